@@ -1,0 +1,330 @@
+/*
+ * oracle.c -- plain, slow, obviously-correct CPU definition of the tumour
+ * database query of Ezhov et al., "A for-loop is all you need" (2022).
+ *
+ * THIS IS TEST INFRASTRUCTURE.  Only the test-suite, the smoke check and the
+ * CPU-baseline leg of the benchmark may load it.  The CUDA library never
+ * links it, and it shares no code, header or table with the CUDA path.
+ *
+ * What it computes (the paper's Section 2.3, "Query to a database of
+ * synthetic tumors", and the "Baseline for-loop search" paragraph):
+ *
+ *   * each database volume u is thresholded at u_T1Gd and u_FLAIR, giving two
+ *     binary segmentations per entry;  a voxel is in the mask when
+ *     (float)u(x) >= t  (reading: ">=" compared in binary32);
+ *   * each entry is compared with the patient's two segmentations by the
+ *     Dice coefficient  Dice(A,B) = 2|A n B| / (|A| + |B|);  both masks
+ *     empty counts as identical (Dice = 1);
+ *   * the two Dice values are added and the entry with the largest sum is
+ *     the best match; the score reported here is the mean
+ *     (Dice_T1Gd + Dice_FLAIR) / 2, which orders entries identically because
+ *     the halving is exact in binary64;
+ *   * entries are ranked by (score descending, index ascending) -- the lowest
+ *     index wins a tie -- and the first k are returned.
+ *
+ * Everything is a loop over voxels and entries, in the order the definition
+ * states.  Counts are exact unsigned integers; the score is IEEE binary64,
+ * round-to-nearest:  D_k = (double)(2 I_k) / (double)(P_k + E_k),
+ * S = (D_1 + D_2) * 0.5.
+ *
+ * The half-precision storage path is decoded by this file's own IEEE
+ * binary16 decoder (sign, 5-bit exponent with bias 15, 10-bit fraction,
+ * subnormals, infinities, NaN), never by a library conversion.
+ *
+ * The embedding prefilter (low-dimensional retrieval, Section 2.3 "Autoencoders"
+ * and "naive downsampling": L2 between compressed representations, combined as
+ * L2_T1Gd + L2_FLAIR, lowest wins) is defined here as the f x f x f block mean
+ * of each binary mask and the Euclidean distance between those block means,
+ * computed in binary64.
+ *
+ * The nearest-neighbour downsampling of Section 2.3 (an order-0 spline
+ * resampling to 64^3 or 32^3) is out[i] = in[f*i] along each axis.
+ *
+ * Volume layout everywhere: [nz][ny][nx], x fastest; voxel linear index
+ * i = x + nx*(y + ny*z).
+ *
+ * Parity pins (tests/test_oracle_*.py): hand-worked 2x2x2 cases, Dice(A,A)=1,
+ * disjoint masks give 0, symmetry, the Jaccard identity D = 2J/(1+J) computed
+ * through Python sets, exact rationals for the score, planted duplicates for
+ * the order, all 65,536 binary16 patterns against numpy's decoder, and
+ * single-voxel volumes for the block-mean layout.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------ */
+/* IEEE 754 binary16 -> binary64, from the format's definition.         */
+/* ------------------------------------------------------------------ */
+double oracle_f16_to_f64(uint16_t h)
+{
+    int sign = (h >> 15) & 1;
+    int expo = (h >> 10) & 0x1F;
+    int frac = h & 0x3FF;
+    double mag;
+    if (expo == 0) {
+        mag = ldexp((double)frac, -24);               /* subnormal: frac * 2^-14 * 2^-10 */
+    } else if (expo == 31) {
+        mag = (frac == 0) ? INFINITY : NAN;
+    } else {
+        mag = ldexp((double)(1024 + frac), expo - 25); /* (1 + frac/1024) * 2^(expo-15) */
+    }
+    return sign ? -mag : mag;
+}
+
+/* Membership of one voxel in a thresholded segmentation (Section 2.3). */
+static int in_mask_f32(float c, float t) { return c >= t; }
+static int in_mask_f16(uint16_t h, float t)
+{
+    /* the binary16 value is exact in binary32, so comparing in binary64 is
+       the same as comparing in binary32 */
+    return oracle_f16_to_f64(h) >= (double)t;
+}
+
+/* Dice coefficient from exact counts; both masks empty -> 1. */
+double oracle_dice(uint32_t inter, uint32_t size_a, uint32_t size_b)
+{
+    uint32_t denom = size_a + size_b;
+    if (denom == 0) return 1.0;
+    return (double)(2u * inter) / (double)denom;
+}
+
+/* Combined score: mean of Dice_T1Gd and Dice_FLAIR. */
+double oracle_score(uint32_t i1, uint32_t i2, uint32_t e1, uint32_t e2,
+                    uint32_t p1, uint32_t p2)
+{
+    double d1 = oracle_dice(i1, p1, e1);
+    double d2 = oracle_dice(i2, p2, e2);
+    return (d1 + d2) * 0.5;
+}
+
+/* ------------------------------------------------------------------ */
+/* Patient segmentations as byte masks [2][v] (0/1).                    */
+/* ------------------------------------------------------------------ */
+void oracle_threshold_f32(const float* vol, int64_t v, float t1, float t2,
+                          uint8_t* mask /* [2][v] */)
+{
+    for (int64_t x = 0; x < v; ++x) {
+        mask[x] = (uint8_t)in_mask_f32(vol[x], t1);
+        mask[v + x] = (uint8_t)in_mask_f32(vol[x], t2);
+    }
+}
+
+void oracle_threshold_f16(const uint16_t* vol, int64_t v, float t1, float t2,
+                          uint8_t* mask /* [2][v] */)
+{
+    for (int64_t x = 0; x < v; ++x) {
+        mask[x] = (uint8_t)in_mask_f16(vol[x], t1);
+        mask[v + x] = (uint8_t)in_mask_f16(vol[x], t2);
+    }
+}
+
+/* Unpack the library's bit-plane format into byte masks: word w, bit b of a
+   plane holds voxel 32*w + b.  planes is [2][words]. */
+void oracle_unpack_planes(const uint32_t* planes, int64_t words, int64_t v,
+                          uint8_t* mask /* [2][v] */)
+{
+    for (int k = 0; k < 2; ++k)
+        for (int64_t x = 0; x < v; ++x)
+            mask[k * v + x] = (uint8_t)((planes[k * words + x / 32] >> (x % 32)) & 1u);
+}
+
+/* ------------------------------------------------------------------ */
+/* Per-entry counts: out[e] = {I1, I2, E1, E2}.                          */
+/* The patient is given as its byte masks [2][v]; P_k is their sum.       */
+/* ------------------------------------------------------------------ */
+static void patient_sizes(const uint8_t* pmask, int64_t v, uint32_t* pcount)
+{
+    pcount[0] = pcount[1] = 0;
+    for (int64_t x = 0; x < v; ++x) {
+        pcount[0] += pmask[x];
+        pcount[1] += pmask[v + x];
+    }
+}
+
+int oracle_counts_f32(const float* db, int64_t n, int64_t v, const uint8_t* pmask,
+                      float t1, float t2, int nthreads,
+                      uint32_t* out /* [n][4] */, uint32_t* pcount /* [2] */)
+{
+    patient_sizes(pmask, v, pcount);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t e = 0; e < n; ++e) {
+        const float* c = db + e * v;
+        uint32_t i1 = 0, i2 = 0, e1 = 0, e2 = 0;
+        for (int64_t x = 0; x < v; ++x) {
+            int m1 = in_mask_f32(c[x], t1);
+            int m2 = in_mask_f32(c[x], t2);
+            e1 += m1;
+            e2 += m2;
+            i1 += m1 & pmask[x];
+            i2 += m2 & pmask[v + x];
+        }
+        out[4 * e + 0] = i1;
+        out[4 * e + 1] = i2;
+        out[4 * e + 2] = e1;
+        out[4 * e + 3] = e2;
+    }
+    (void)nthreads;
+    return 0;
+}
+
+int oracle_counts_f16(const uint16_t* db, int64_t n, int64_t v, const uint8_t* pmask,
+                      float t1, float t2, int nthreads,
+                      uint32_t* out /* [n][4] */, uint32_t* pcount /* [2] */)
+{
+    patient_sizes(pmask, v, pcount);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t e = 0; e < n; ++e) {
+        const uint16_t* c = db + e * v;
+        uint32_t i1 = 0, i2 = 0, e1 = 0, e2 = 0;
+        for (int64_t x = 0; x < v; ++x) {
+            int m1 = in_mask_f16(c[x], t1);
+            int m2 = in_mask_f16(c[x], t2);
+            e1 += m1;
+            e2 += m2;
+            i1 += m1 & pmask[x];
+            i2 += m2 & pmask[v + x];
+        }
+        out[4 * e + 0] = i1;
+        out[4 * e + 1] = i2;
+        out[4 * e + 2] = e1;
+        out[4 * e + 3] = e2;
+    }
+    (void)nthreads;
+    return 0;
+}
+
+/* Counts against database entries given directly as byte masks [n][2][v]
+   (used for the downsampled loop and for masks built by other means). */
+int oracle_counts_masks(const uint8_t* dbmask, int64_t n, int64_t v, const uint8_t* pmask,
+                        int nthreads, uint32_t* out /* [n][4] */, uint32_t* pcount)
+{
+    patient_sizes(pmask, v, pcount);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t e = 0; e < n; ++e) {
+        const uint8_t* m = dbmask + e * 2 * v;
+        uint32_t i1 = 0, i2 = 0, e1 = 0, e2 = 0;
+        for (int64_t x = 0; x < v; ++x) {
+            e1 += m[x];
+            e2 += m[v + x];
+            i1 += m[x] & pmask[x];
+            i2 += m[v + x] & pmask[v + x];
+        }
+        out[4 * e + 0] = i1;
+        out[4 * e + 1] = i2;
+        out[4 * e + 2] = e1;
+        out[4 * e + 3] = e2;
+    }
+    (void)nthreads;
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Ranking: (score descending, index ascending), first k.               */
+/* ------------------------------------------------------------------ */
+typedef struct { double score; int64_t index; } ranked;
+
+static int ranked_cmp(const void* pa, const void* pb)
+{
+    const ranked* a = (const ranked*)pa;
+    const ranked* b = (const ranked*)pb;
+    if (a->score > b->score) return -1;
+    if (a->score < b->score) return 1;
+    if (a->index < b->index) return -1;
+    if (a->index > b->index) return 1;
+    return 0;
+}
+
+/* scores[n] -> out_index[k], out_score[k].  Returns 0, or -1 if k > n. */
+int oracle_rank(const double* scores, int64_t n, int64_t k,
+                int64_t* out_index, double* out_score)
+{
+    if (k > n || k < 0) return -1;
+    ranked* r = (ranked*)malloc(sizeof(ranked) * (size_t)(n > 0 ? n : 1));
+    if (!r) return -2;
+    for (int64_t e = 0; e < n; ++e) { r[e].score = scores[e]; r[e].index = e; }
+    qsort(r, (size_t)n, sizeof(ranked), ranked_cmp);
+    for (int64_t j = 0; j < k; ++j) { out_index[j] = r[j].index; out_score[j] = r[j].score; }
+    free(r);
+    return 0;
+}
+
+/* Scores for all entries from their counts. */
+void oracle_scores(const uint32_t* counts /* [n][4] */, int64_t n, const uint32_t* pcount,
+                   double* scores /* [n] */)
+{
+    for (int64_t e = 0; e < n; ++e)
+        scores[e] = oracle_score(counts[4 * e + 0], counts[4 * e + 1],
+                                 counts[4 * e + 2], counts[4 * e + 3],
+                                 pcount[0], pcount[1]);
+}
+
+/* ------------------------------------------------------------------ */
+/* Low-dimensional representations.                                     */
+/* ------------------------------------------------------------------ */
+
+/* Block mean of a byte mask over f x f x f blocks (nx, ny, nz multiples of f):
+   out[bx + (nx/f)*(by + (ny/f)*bz)] = (1/f^3) * #{voxels set in the block}. */
+int oracle_block_mean(const uint8_t* mask, int nx, int ny, int nz, int f, double* out)
+{
+    if (f <= 0 || nx % f || ny % f || nz % f) return -1;
+    int bx_n = nx / f, by_n = ny / f, bz_n = nz / f;
+    for (int bz = 0; bz < bz_n; ++bz)
+        for (int by = 0; by < by_n; ++by)
+            for (int bx = 0; bx < bx_n; ++bx) {
+                int64_t count = 0;
+                for (int z = bz * f; z < (bz + 1) * f; ++z)
+                    for (int y = by * f; y < (by + 1) * f; ++y)
+                        for (int x = bx * f; x < (bx + 1) * f; ++x)
+                            count += mask[(int64_t)x + (int64_t)nx * ((int64_t)y + (int64_t)ny * z)];
+                out[bx + bx_n * (by + by_n * bz)] = (double)count / ((double)f * f * f);
+            }
+    return 0;
+}
+
+/* Euclidean distance between two vectors of length d, in binary64. */
+double oracle_l2(const double* a, const double* b, int64_t d)
+{
+    double s = 0.0;
+    for (int64_t j = 0; j < d; ++j) {
+        double diff = a[j] - b[j];
+        s += diff * diff;
+    }
+    return sqrt(s);
+}
+
+/* Nearest-neighbour (order-0 spline) downsampling by integer factor f:
+   out[x + (nx/f)*(y + (ny/f)*z)] = in[f*x + nx*(f*y + ny*f*z)]. */
+int oracle_downsample_nn_u8(const uint8_t* in, int nx, int ny, int nz, int f, uint8_t* out)
+{
+    if (f <= 0 || nx % f || ny % f || nz % f) return -1;
+    int ox = nx / f, oy = ny / f, oz = nz / f;
+    for (int z = 0; z < oz; ++z)
+        for (int y = 0; y < oy; ++y)
+            for (int x = 0; x < ox; ++x)
+                out[x + (int64_t)ox * (y + (int64_t)oy * z)] =
+                    in[(int64_t)f * x + (int64_t)nx * ((int64_t)f * y + (int64_t)ny * ((int64_t)f * z))];
+    return 0;
+}
+
+int oracle_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
