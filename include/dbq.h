@@ -1,0 +1,203 @@
+/*
+ * dbq.h -- C ABI of the GB300 tumour-database query library (libdbq.so).
+ *
+ * The library implements the database query of Ezhov et al., "A for-loop is
+ * all you need" (2022): every simulated tumour concentration volume of a
+ * database is thresholded at u_T1Gd and u_FLAIR (Section 2.3, "Query to a
+ * database of synthetic tumors"), each entry's two segmentations are compared
+ * with the patient's two segmentations by the Dice coefficient (same
+ * section), the two Dice values are combined by addition (reported as their
+ * mean, which orders entries identically), and the best match -- the
+ * arg-max -- and the top-k entries are returned together with their model
+ * parameters theta (Section 3, "Data").  The brute-force loop over the whole
+ * database is the paper's "baseline for-loop search" (Section 2.3).
+ *
+ * Definitions used by every call:
+ *   voxel order   volumes are [nz][ny][nx], x fastest: i = x + nx*(y + ny*z).
+ *   mask          m_k(i) = [ (float)c(i) >= t_k ],  k = 1 (T1Gd), 2 (FLAIR).
+ *   bit planes    plane k of a volume is an array of uint32 words; bit b of
+ *                 word w is voxel 32*w + b.  Bits past the last voxel are 0.
+ *   counts        I_k = |P_k n E_k|, E_k = |E_k|, P_k = |P_k| (patient).
+ *   Dice          D_k = 2 I_k / (P_k + E_k) in IEEE binary64, round to
+ *                 nearest;  D_k = 1 when P_k + E_k = 0 (both masks empty).
+ *   score         S = (D_1 + D_2) * 0.5 in binary64.
+ *   order         entries are ranked by (S descending, index ascending):
+ *                 of two equal scores the lower database index ranks first.
+ *
+ * Conventions:
+ *   * Every call returns a dbq_status; on failure db_last_error() returns a
+ *     thread-local message and no output has been written.
+ *   * "host or device" pointers are classified with cudaPointerGetAttributes;
+ *     host memory may be pageable or pinned.
+ *   * `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     whose outputs are host memory return only after their work is complete.
+ *     The *_async calls only enqueue work on `stream`.
+ *   * A handle is thread-safe (an internal mutex serialises calls), but all
+ *     work of one handle shares one query workspace in device memory, so
+ *     asynchronous calls on one handle must not overlap on the GPU: issue them
+ *     on one stream, or synchronise between streams.
+ *   * The library owns all database device memory and frees it in
+ *     db_destroy(); the caller owns every buffer it passes in.
+ */
+#ifndef DBQ_H
+#define DBQ_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dbq_db dbq_db;
+
+/* Status codes. */
+enum dbq_status {
+    DBQ_OK = 0,
+    DBQ_EINVAL = -1,   /* bad argument: null pointer, bad size, bad threshold  */
+    DBQ_ENOMEM = -2,   /* device or host allocation failed                     */
+    DBQ_ESTATE = -3,   /* call not valid in the handle's state (e.g. unbuilt)  */
+    DBQ_ECUDA = -4,    /* a CUDA runtime call or a kernel launch failed         */
+    DBQ_ETIMEOUT = -5, /* reserved: a bounded device wait gave up               */
+    DBQ_ERANGE = -6    /* k or an index outside [0, N]                          */
+};
+
+/* Element kinds of volumes passed in. */
+enum dbq_kind {
+    DBQ_F32 = 0,   /* float32 concentrations [V]                               */
+    DBQ_F16 = 1,   /* IEEE binary16 concentrations [V] (uint16 bit patterns)   */
+    DBQ_BITS = 2   /* two bit planes [2][ceil(V/32)] uint32 (patients only)    */
+};
+
+/* Database storage. */
+enum dbq_storage {
+    DBQ_STORE_BITS = 0, /* masks thresholded at build time, 1 bit per voxel per
+                           threshold; queries use the build thresholds       */
+    DBQ_STORE_F16 = 1   /* binary16 concentrations; each query thresholds the
+                           database at its own (t1, t2)                      */
+};
+
+/* One ranked result.  p1/p2 are the patient's mask sizes. */
+typedef struct dbq_hit {
+    int64_t index;     /* database entry                                      */
+    double score;      /* (Dice_T1Gd + Dice_FLAIR) / 2                         */
+    uint32_t i1, i2;   /* |P_1 n E_1|, |P_2 n E_2|                              */
+    uint32_t e1, e2;   /* |E_1|, |E_2| of the entry                             */
+    uint32_t p1, p2;   /* |P_1|, |P_2| of the patient                           */
+} dbq_hit;
+
+/*
+ * db_create -- make an empty database of `capacity` entries on the current
+ * CUDA device.
+ *   nx, ny, nz   grid of every volume (each >= 1; V = nx*ny*nz < 2^31).
+ *   capacity     number of entries N (>= 1); all are allocated up front:
+ *                BITS storage 2*ceil4(ceil(V/32))*4 bytes per entry,
+ *                F16 storage 2*V bytes per entry.
+ *   storage      DBQ_STORE_BITS or DBQ_STORE_F16.
+ *   t1, t2       BITS storage: the T1Gd and FLAIR thresholds the masks are
+ *                built with (Section 2.3 uses 0.6 and 0.2); each must be a
+ *                finite number in (0, 1].  F16 storage: ignored.
+ *   n_params     doubles of theta kept per entry (0..64), returned with hits.
+ *   flags        0 (reserved for later options).
+ * Returns DBQ_OK and *out, or DBQ_EINVAL / DBQ_ENOMEM / DBQ_ECUDA.
+ */
+int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storage,
+              float t1, float t2, int n_params, uint32_t flags);
+
+/*
+ * db_load_volumes -- put entries [first, first+count) into the database.
+ *   vols     [count][V] DBQ_F32 or DBQ_F16 volumes, host or device memory.
+ *            BITS storage thresholds them at (t1, t2) into bit planes and
+ *            the per-entry mask sizes |E_1|, |E_2| (the build step of the
+ *            thresholding in Section 2.3); no concentration is kept.
+ *            F16 storage keeps binary16 values (float32 input is rounded to
+ *            nearest-even).
+ *   params   host [count][n_params] doubles (theta), or NULL (zeros).
+ * Entries may be loaded in any order and reloaded.  Loading clears the built
+ * state; call db_build_masks() again before querying.
+ */
+int db_load_volumes(dbq_db* db, int64_t first, int64_t count, const void* vols, int kind,
+                    const double* params, void* stream);
+
+/*
+ * db_build_masks -- finish the build: check that every entry in
+ * [0, capacity) has been loaded and make the database queryable.  The masks
+ * themselves are written as volumes are loaded, so this call reads no
+ * volume.  Returns DBQ_ESTATE if an entry is missing.
+ */
+int db_build_masks(dbq_db* db, void* stream);
+
+/*
+ * db_query -- the brute-force query: score the patient against every entry
+ * and return the k best under the order above.
+ *   patient  host or device; kind DBQ_F32 / DBQ_F16 volume [V] (thresholded
+ *            here at (t1, t2)), or DBQ_BITS planes [2][ceil(V/32)] (bits
+ *            past voxel V-1 are ignored).
+ *   t1, t2   BITS storage: must equal the build thresholds, or be NaN to
+ *            mean "the build thresholds".  F16 storage: the thresholds
+ *            applied to the database and to a volume patient, in (0, 1].
+ *   k        1 <= k <= min(N, 1024); DBQ_ERANGE otherwise.
+ *   hits     host [k], written in rank order.
+ *   params   host [k][n_params] theta of the hits, or NULL.
+ * Returns after the results are in host memory.
+ */
+int db_query(dbq_db* db, const void* patient, int kind, float t1, float t2, int k,
+             dbq_hit* hits, double* params, void* stream);
+
+/*
+ * db_query_async -- as db_query, but the patient must be device memory and
+ * the k hits are written to device memory `hits_dev` [k]; the work is only
+ * enqueued on `stream` (no host synchronisation, no host copies), so the
+ * call can be captured in a CUDA graph.
+ */
+int db_query_async(dbq_db* db, const void* patient_dev, int kind, float t1, float t2,
+                   int k, dbq_hit* hits_dev, void* stream);
+
+/*
+ * db_prepare_patient / db_query_prepared -- the two steps of db_query_async
+ * issued separately: the first thresholds (or imports) a device-memory
+ * patient into the handle's workspace (the patient's segmentations, Section
+ * 2.3), the second runs the scan, scoring and top-k selection against that
+ * prepared patient and writes `k` hits to device memory.  Both only enqueue
+ * work on `stream`.  db_query_prepared returns DBQ_ESTATE if no patient has
+ * been prepared since the handle was created.
+ */
+int db_prepare_patient(dbq_db* db, const void* patient_dev, int kind, float t1, float t2,
+                       void* stream);
+int db_query_prepared(dbq_db* db, int k, dbq_hit* hits_dev, void* stream);
+
+/*
+ * db_scan_counts -- the per-entry counts of one patient, for every entry:
+ * counts [N][4] = (I_1, I_2, E_1, E_2), host or device memory, plus the
+ * patient's (P_1, P_2) in pcount [2] (host or device).  Same patient and
+ * threshold rules as db_query.  Returns after the counts are written.
+ */
+int db_scan_counts(dbq_db* db, const void* patient, int kind, float t1, float t2,
+                   uint32_t* counts, uint32_t* pcount, void* stream);
+
+/*
+ * db_get_masks -- copy the packed planes of entries [first, first+count) to
+ * `planes` [count][2][words] (host or device) and their mask sizes to
+ * `sizes` [count][2] (host or device, or NULL).  BITS storage only.
+ * `words` = ceil(V/32); see db_info().
+ */
+int db_get_masks(dbq_db* db, int64_t first, int64_t count, uint32_t* planes,
+                 uint32_t* sizes, void* stream);
+
+/*
+ * db_info -- sizes of a handle: out[0] = N, out[1] = V, out[2] = words per
+ * plane ceil(V/32), out[3] = padded words per plane, out[4] = storage,
+ * out[5] = built (0/1), out[6] = n_params, out[7] = device bytes held.
+ */
+int db_info(const dbq_db* db, int64_t out[8]);
+
+/* db_destroy -- free everything the handle owns.  NULL is accepted. */
+int db_destroy(dbq_db* db);
+
+/* Last error message of the calling thread ("" if none). */
+const char* db_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DBQ_H */

@@ -1,0 +1,586 @@
+// api.cu -- the C ABI of libdbq (declared and documented in include/dbq.h).
+//
+// Host side only: argument checks, device memory of the database and the
+// query workspace, staging of host inputs, and the launches of the kernels
+// in pack.cu and scan_packed.cu (and, for half-precision storage,
+// scan_f16.cu).  Every step of a query runs in those kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "dbq.h"
+#include "kernels.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char* fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_fail(cudaError_t err, const char* what)
+{
+    return fail(DBQ_ECUDA, "%s: %s", what, cudaGetErrorString(err));
+}
+
+#define DBQ_CUDA(call)                                               \
+    do {                                                             \
+        cudaError_t err_ = (call);                                   \
+        if (err_ != cudaSuccess) return cuda_fail(err_, #call);      \
+    } while (0)
+
+// Keeps the caller's current device unchanged across a call.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = (prev == dev) || (cudaSetDevice(dev) == cudaSuccess);
+    }
+    ~DeviceGuard()
+    {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+bool threshold_ok(float t) { return std::isfinite(t) && t > 0.0f && t <= 1.0f; }
+
+constexpr int kMaxK = 1024;
+constexpr size_t kStageBytes = size_t(256) << 20;   // host-input staging chunk
+
+}  // namespace
+
+struct dbq_db {
+    std::mutex mu;
+    int device = 0;
+    int nx = 0, ny = 0, nz = 0;
+    int64_t v = 0, words = 0, wp = 0;
+    int wp4 = 0;
+    int64_t n = 0;
+    int storage = DBQ_STORE_BITS;
+    float t1 = 0.f, t2 = 0.f;
+    int n_params = 0;
+    uint32_t flags = 0;
+    // database
+    uint32_t* planes = nullptr;     // [n][2][wp]
+    uint32_t* ecount = nullptr;     // [n][2]
+    uint16_t* vols16 = nullptr;     // [n][v] (F16 storage)
+    std::vector<double> params;     // [n][n_params]
+    std::vector<uint8_t> loaded;
+    int64_t n_loaded = 0;
+    bool built = false;
+    // query workspace
+    void* stage = nullptr;          // device staging for host inputs
+    size_t stage_bytes = 0;
+    uint32_t* pplanes = nullptr;    // [2][wp] patient planes
+    uint32_t* pcount = nullptr;     // [4] patient sizes (2 used)
+    dbq::Cand* cand = nullptr;      // [grid][kMaxK]
+    unsigned int* ticket = nullptr;
+    dbq::Hit* hits_dev = nullptr;   // [kMaxK]
+    dbq::Hit* hits_host = nullptr;  // pinned [kMaxK]
+    uint32_t* counts_dev = nullptr; // [n][4], allocated on first db_scan_counts
+    bool prepared = false;          // a patient sits in pplanes/pcount
+    float prep_t1 = 0.f, prep_t2 = 0.f;
+    int grid = 1;
+    int chunk4 = 1, nchunks = 1;
+    size_t bytes_held = 0;
+
+    ~dbq_db()
+    {
+        cudaFree(planes);
+        cudaFree(ecount);
+        cudaFree(vols16);
+        cudaFree(stage);
+        cudaFree(pplanes);
+        cudaFree(pcount);
+        cudaFree(cand);
+        cudaFree(ticket);
+        cudaFree(hits_dev);
+        cudaFreeHost(hits_host);
+        cudaFree(counts_dev);
+    }
+};
+
+namespace {
+
+template <typename T>
+int dev_alloc(dbq_db* db, T** p, size_t bytes, const char* what)
+{
+    cudaError_t err = cudaMalloc(reinterpret_cast<void**>(p), bytes ? bytes : 16);
+    if (err != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(DBQ_ENOMEM, "cudaMalloc of %zu bytes for %s failed: %s", bytes, what,
+                    cudaGetErrorString(err));
+    }
+    db->bytes_held += bytes;
+    return DBQ_OK;
+}
+
+int ensure_stage(dbq_db* db, size_t bytes)
+{
+    if (db->stage_bytes >= bytes) return DBQ_OK;
+    cudaFree(db->stage);
+    db->bytes_held -= db->stage_bytes;
+    db->stage = nullptr;
+    db->stage_bytes = 0;
+    int rc = dev_alloc(db, &db->stage, bytes, "input staging");
+    if (rc == DBQ_OK) db->stage_bytes = bytes;
+    return rc;
+}
+
+// Bring a patient into db->pplanes / db->pcount (device), thresholding a
+// volume at (t1, t2) or importing caller bit planes.
+int prepare_patient(dbq_db* db, const void* patient, int kind, float t1, float t2,
+                    cudaStream_t s)
+{
+    const bool on_dev = is_device_ptr(patient);
+    size_t bytes;
+    if (kind == DBQ_BITS)
+        bytes = (size_t)2 * db->words * sizeof(uint32_t);
+    else if (kind == DBQ_F32)
+        bytes = (size_t)db->v * sizeof(float);
+    else if (kind == DBQ_F16)
+        bytes = (size_t)db->v * sizeof(uint16_t);
+    else
+        return fail(DBQ_EINVAL, "unknown patient kind %d", kind);
+    const void* src = patient;
+    if (!on_dev) {
+        int rc = ensure_stage(db, bytes);
+        if (rc) return rc;
+        DBQ_CUDA(cudaMemcpyAsync(db->stage, patient, bytes, cudaMemcpyHostToDevice, s));
+        src = db->stage;
+    }
+    DBQ_CUDA(cudaMemsetAsync(db->pcount, 0, 4 * sizeof(uint32_t), s));
+    cudaError_t err;
+    if (kind == DBQ_BITS)
+        err = dbq::launch_import_bits(static_cast<const uint32_t*>(src), db->words, db->v, db->wp,
+                                      db->pplanes, db->pcount, s);
+    else
+        err = dbq::launch_pack(src, kind == DBQ_F16, 1, db->v, db->wp, t1, t2, db->pplanes,
+                               db->pcount, s);
+    if (err != cudaSuccess) return cuda_fail(err, "patient packing");
+    db->prepared = true;
+    db->prep_t1 = t1;
+    db->prep_t2 = t2;
+    return DBQ_OK;
+}
+
+int check_query_args(dbq_db* db, int kind, float* t1, float* t2, int k)
+{
+    if (!db->built) return fail(DBQ_ESTATE, "database not built (call db_build_masks)");
+    if (kind != DBQ_F32 && kind != DBQ_F16 && kind != DBQ_BITS)
+        return fail(DBQ_EINVAL, "unknown patient kind %d", kind);
+    if (db->storage == DBQ_STORE_BITS) {
+        if (std::isnan(*t1)) *t1 = db->t1;
+        if (std::isnan(*t2)) *t2 = db->t2;
+        if (*t1 != db->t1 || *t2 != db->t2)
+            return fail(DBQ_EINVAL,
+                        "thresholds (%g, %g) differ from the build thresholds (%g, %g) of a "
+                        "bit-packed database",
+                        (double)*t1, (double)*t2, (double)db->t1, (double)db->t2);
+    } else {
+        if (!threshold_ok(*t1) || !threshold_ok(*t2))
+            return fail(DBQ_EINVAL, "thresholds must be finite and in (0, 1]");
+    }
+    if (k < 1) return fail(DBQ_ERANGE, "k = %d must be >= 1", k);
+    if (k > db->n || k > kMaxK)
+        return fail(DBQ_ERANGE, "k = %d outside [1, min(N=%lld, %d)]", k, (long long)db->n,
+                    kMaxK);
+    return DBQ_OK;
+}
+
+int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaStream_t s)
+{
+    if (db->storage == DBQ_STORE_BITS) {
+        dbq::ScanPackedArgs a;
+        a.planes = reinterpret_cast<const uint4*>(db->planes);
+        a.ecount = db->ecount;
+        a.patient = reinterpret_cast<const uint4*>(db->pplanes);
+        a.pcount = db->pcount;
+        a.n = db->n;
+        a.wp4 = db->wp4;
+        a.chunk4 = db->chunk4;
+        a.nchunks = db->nchunks;
+        a.k = k;
+        a.cand = db->cand;
+        a.ticket = db->ticket;
+        a.hits = hits;
+        a.counts_out = counts_out;
+        cudaError_t err = dbq::launch_scan_packed(a, db->grid, s);
+        if (err != cudaSuccess) return cuda_fail(err, "scan_packed launch");
+        return DBQ_OK;
+    }
+    return fail(DBQ_ESTATE, "half-precision storage query is not available in this build");
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* db_last_error(void) { return g_last_error.c_str(); }
+
+int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storage, float t1,
+              float t2, int n_params, uint32_t flags)
+{
+    if (!out) return fail(DBQ_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(DBQ_EINVAL, "grid dimensions must be >= 1");
+    const int64_t v = (int64_t)nx * ny * nz;
+    if (v >= (int64_t(1) << 31)) return fail(DBQ_EINVAL, "volume of %lld voxels too large",
+                                             (long long)v);
+    if (capacity < 1) return fail(DBQ_EINVAL, "capacity must be >= 1");
+    if (storage != DBQ_STORE_BITS && storage != DBQ_STORE_F16)
+        return fail(DBQ_EINVAL, "unknown storage %d", storage);
+    if (storage == DBQ_STORE_BITS && (!threshold_ok(t1) || !threshold_ok(t2)))
+        return fail(DBQ_EINVAL, "build thresholds must be finite and in (0, 1]");
+    if (n_params < 0 || n_params > 64) return fail(DBQ_EINVAL, "n_params must be in [0, 64]");
+    if (flags != 0) return fail(DBQ_EINVAL, "unknown flags 0x%x", flags);
+
+    int dev = 0;
+    DBQ_CUDA(cudaGetDevice(&dev));
+    dbq_db* db = new (std::nothrow) dbq_db;
+    if (!db) return fail(DBQ_ENOMEM, "host allocation failed");
+    db->device = dev;
+    db->nx = nx;
+    db->ny = ny;
+    db->nz = nz;
+    db->v = v;
+    db->words = (v + 31) / 32;
+    db->wp = (db->words + 3) / 4 * 4;
+    db->wp4 = (int)(db->wp / 4);
+    db->n = capacity;
+    db->storage = storage;
+    db->t1 = t1;
+    db->t2 = t2;
+    db->n_params = n_params;
+    db->flags = flags;
+    try {
+        db->params.assign((size_t)capacity * n_params, 0.0);
+        db->loaded.assign((size_t)capacity, 0);
+    } catch (...) {
+        delete db;
+        return fail(DBQ_ENOMEM, "host allocation of per-entry metadata failed");
+    }
+    int rc = DBQ_OK;
+    if (storage == DBQ_STORE_BITS) {
+        rc = dev_alloc(db, &db->planes, (size_t)capacity * 2 * db->wp * sizeof(uint32_t),
+                       "bit planes");
+        if (!rc)
+            rc = dev_alloc(db, &db->ecount, (size_t)capacity * 2 * sizeof(uint32_t),
+                           "mask sizes");
+    } else {
+        rc = dev_alloc(db, &db->vols16, (size_t)capacity * v * sizeof(uint16_t),
+                       "binary16 volumes");
+    }
+    db->grid = dbq::scan_packed_grid(dev);
+    dbq::scan_packed_chunking(db->wp4, &db->chunk4, &db->nchunks);
+    if (!rc) rc = dev_alloc(db, &db->pplanes, (size_t)2 * db->wp * sizeof(uint32_t), "patient");
+    if (!rc) rc = dev_alloc(db, &db->pcount, 4 * sizeof(uint32_t), "patient sizes");
+    if (!rc)
+        rc = dev_alloc(db, &db->cand, (size_t)db->grid * kMaxK * sizeof(dbq::Cand),
+                       "candidate lists");
+    if (!rc) rc = dev_alloc(db, &db->ticket, sizeof(unsigned int), "ticket");
+    if (!rc) rc = dev_alloc(db, &db->hits_dev, (size_t)kMaxK * sizeof(dbq::Hit), "hits");
+    if (!rc) {
+        cudaError_t err = cudaMallocHost(reinterpret_cast<void**>(&db->hits_host),
+                                         (size_t)kMaxK * sizeof(dbq::Hit));
+        if (err != cudaSuccess) {
+            cudaGetLastError();
+            db->hits_host = nullptr;
+            rc = fail(DBQ_ENOMEM, "pinned host allocation failed");
+        }
+    }
+    if (!rc) {
+        cudaError_t err = cudaMemset(db->ticket, 0, sizeof(unsigned int));
+        if (err == cudaSuccess && db->ecount)
+            err = cudaMemset(db->ecount, 0, (size_t)capacity * 2 * sizeof(uint32_t));
+        if (err == cudaSuccess) err = cudaDeviceSynchronize();
+        if (err != cudaSuccess) rc = cuda_fail(err, "workspace initialisation");
+    }
+    if (rc) {
+        delete db;
+        return rc;
+    }
+    *out = db;
+    return DBQ_OK;
+}
+
+int db_load_volumes(dbq_db* db, int64_t first, int64_t count, const void* vols, int kind,
+                    const double* params, void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (count == 0) return DBQ_OK;
+    if (!vols) return fail(DBQ_EINVAL, "vols is NULL");
+    if (first < 0 || count < 0 || first + count > db->n)
+        return fail(DBQ_ERANGE, "entries [%lld, %lld) outside [0, %lld)", (long long)first,
+                    (long long)(first + count), (long long)db->n);
+    if (kind != DBQ_F32 && kind != DBQ_F16)
+        return fail(DBQ_EINVAL, "volumes must be DBQ_F32 or DBQ_F16");
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t esz = kind == DBQ_F16 ? 2 : 4;
+    const size_t vol_bytes = (size_t)db->v * esz;
+    const bool on_dev = is_device_ptr(vols);
+    int64_t per_chunk = count;
+    if (!on_dev) {
+        per_chunk = (int64_t)(kStageBytes / vol_bytes);
+        if (per_chunk < 1) per_chunk = 1;
+        if (per_chunk > count) per_chunk = count;
+        int rc = ensure_stage(db, (size_t)per_chunk * vol_bytes);
+        if (rc) return rc;
+    }
+    db->built = false;
+    for (int64_t c0 = 0; c0 < count; c0 += per_chunk) {
+        const int64_t cn = (count - c0) < per_chunk ? (count - c0) : per_chunk;
+        const char* src = static_cast<const char*>(vols) + (size_t)c0 * vol_bytes;
+        if (!on_dev) {
+            DBQ_CUDA(cudaMemcpyAsync(db->stage, src, (size_t)cn * vol_bytes,
+                                     cudaMemcpyHostToDevice, s));
+            src = static_cast<const char*>(db->stage);
+        }
+        const int64_t e0 = first + c0;
+        if (db->storage == DBQ_STORE_BITS) {
+            DBQ_CUDA(cudaMemsetAsync(db->ecount + 2 * e0, 0, (size_t)cn * 2 * sizeof(uint32_t),
+                                     s));
+            cudaError_t err = dbq::launch_pack(src, kind == DBQ_F16, cn, db->v, db->wp, db->t1,
+                                               db->t2, db->planes + e0 * 2 * db->wp,
+                                               db->ecount + 2 * e0, s);
+            if (err != cudaSuccess) return cuda_fail(err, "pack launch");
+        } else {
+            uint16_t* dst = db->vols16 + e0 * db->v;
+            if (kind == DBQ_F16) {
+                DBQ_CUDA(cudaMemcpyAsync(dst, src, (size_t)cn * vol_bytes,
+                                         cudaMemcpyDeviceToDevice, s));
+            } else {
+                cudaError_t err = dbq::launch_to_f16(reinterpret_cast<const float*>(src),
+                                                     cn * db->v, dst, s);
+                if (err != cudaSuccess) return cuda_fail(err, "binary16 conversion launch");
+            }
+        }
+    }
+    if (!on_dev) DBQ_CUDA(cudaStreamSynchronize(s));   // the caller may reuse its buffer
+    for (int64_t e = first; e < first + count; ++e) {
+        if (!db->loaded[e]) {
+            db->loaded[e] = 1;
+            ++db->n_loaded;
+        }
+        if (db->n_params) {
+            double* dst = &db->params[(size_t)e * db->n_params];
+            if (params)
+                std::memcpy(dst, params + (size_t)(e - first) * db->n_params,
+                            sizeof(double) * db->n_params);
+            else
+                std::memset(dst, 0, sizeof(double) * db->n_params);
+        }
+    }
+    return DBQ_OK;
+}
+
+int db_build_masks(dbq_db* db, void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (db->n_loaded != db->n)
+        return fail(DBQ_ESTATE, "%lld of %lld entries loaded", (long long)db->n_loaded,
+                    (long long)db->n);
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    DBQ_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    db->built = true;
+    return DBQ_OK;
+}
+
+int db_query_async(dbq_db* db, const void* patient_dev, int kind, float t1, float t2, int k,
+                   dbq_hit* hits_dev, void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    if (!patient_dev || !hits_dev) return fail(DBQ_EINVAL, "NULL pointer argument");
+    std::lock_guard<std::mutex> lock(db->mu);
+    int rc = check_query_args(db, kind, &t1, &t2, k);
+    if (rc) return rc;
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    if (!is_device_ptr(patient_dev) || !is_device_ptr(hits_dev))
+        return fail(DBQ_EINVAL, "db_query_async needs device pointers");
+    if (reinterpret_cast<uintptr_t>(hits_dev) % 8)
+        return fail(DBQ_EINVAL, "hits_dev must be 8-byte aligned");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    rc = prepare_patient(db, patient_dev, kind, t1, t2, s);
+    if (rc) return rc;
+    return launch_query(db, k, reinterpret_cast<dbq::Hit*>(hits_dev), nullptr, s);
+}
+
+int db_prepare_patient(dbq_db* db, const void* patient_dev, int kind, float t1, float t2,
+                       void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    if (!patient_dev) return fail(DBQ_EINVAL, "NULL pointer argument");
+    std::lock_guard<std::mutex> lock(db->mu);
+    int rc = check_query_args(db, kind, &t1, &t2, 1);
+    if (rc) return rc;
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    if (!is_device_ptr(patient_dev))
+        return fail(DBQ_EINVAL, "db_prepare_patient needs a device pointer");
+    return prepare_patient(db, patient_dev, kind, t1, t2, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int db_query_prepared(dbq_db* db, int k, dbq_hit* hits_dev, void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    if (!hits_dev) return fail(DBQ_EINVAL, "NULL pointer argument");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (!db->prepared) return fail(DBQ_ESTATE, "no patient prepared");
+    float t1 = db->prep_t1, t2 = db->prep_t2;
+    int rc = check_query_args(db, DBQ_BITS, &t1, &t2, k);
+    if (rc) return rc;
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    if (!is_device_ptr(hits_dev) || reinterpret_cast<uintptr_t>(hits_dev) % 8)
+        return fail(DBQ_EINVAL, "hits_dev must be 8-byte aligned device memory");
+    return launch_query(db, k, reinterpret_cast<dbq::Hit*>(hits_dev), nullptr,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+int db_query(dbq_db* db, const void* patient, int kind, float t1, float t2, int k,
+             dbq_hit* hits, double* params, void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    if (!patient || !hits) return fail(DBQ_EINVAL, "NULL pointer argument");
+    std::lock_guard<std::mutex> lock(db->mu);
+    int rc = check_query_args(db, kind, &t1, &t2, k);
+    if (rc) return rc;
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    rc = prepare_patient(db, patient, kind, t1, t2, s);
+    if (rc) return rc;
+    rc = launch_query(db, k, db->hits_dev, nullptr, s);
+    if (rc) return rc;
+    DBQ_CUDA(cudaMemcpyAsync(db->hits_host, db->hits_dev, (size_t)k * sizeof(dbq::Hit),
+                             cudaMemcpyDeviceToHost, s));
+    DBQ_CUDA(cudaStreamSynchronize(s));
+    std::memcpy(hits, db->hits_host, (size_t)k * sizeof(dbq_hit));
+    if (params && db->n_params) {
+        for (int j = 0; j < k; ++j) {
+            const int64_t e = hits[j].index;
+            if (e < 0 || e >= db->n) return fail(DBQ_ECUDA, "kernel returned index %lld",
+                                                 (long long)e);
+            std::memcpy(params + (size_t)j * db->n_params, &db->params[(size_t)e * db->n_params],
+                        sizeof(double) * db->n_params);
+        }
+    }
+    return DBQ_OK;
+}
+
+int db_scan_counts(dbq_db* db, const void* patient, int kind, float t1, float t2,
+                   uint32_t* counts, uint32_t* pcount, void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    if (!patient || !counts || !pcount) return fail(DBQ_EINVAL, "NULL pointer argument");
+    std::lock_guard<std::mutex> lock(db->mu);
+    int rc = check_query_args(db, kind, &t1, &t2, 1);
+    if (rc) return rc;
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    rc = prepare_patient(db, patient, kind, t1, t2, s);
+    if (rc) return rc;
+    const bool dev_out = is_device_ptr(counts) && reinterpret_cast<uintptr_t>(counts) % 16 == 0;
+    uint32_t* dst = counts;
+    if (!dev_out) {
+        if (!db->counts_dev) {
+            rc = dev_alloc(db, &db->counts_dev, (size_t)db->n * 4 * sizeof(uint32_t), "counts");
+            if (rc) return rc;
+        }
+        dst = db->counts_dev;
+    }
+    rc = launch_query(db, 1, nullptr, dst, s);
+    if (rc) return rc;
+    if (dst != counts)
+        DBQ_CUDA(cudaMemcpyAsync(counts, dst, (size_t)db->n * 4 * sizeof(uint32_t),
+                                 cudaMemcpyDefault, s));
+    DBQ_CUDA(cudaMemcpyAsync(pcount, db->pcount, 2 * sizeof(uint32_t), cudaMemcpyDefault, s));
+    DBQ_CUDA(cudaStreamSynchronize(s));
+    return DBQ_OK;
+}
+
+int db_get_masks(dbq_db* db, int64_t first, int64_t count, uint32_t* planes, uint32_t* sizes,
+                 void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (db->storage != DBQ_STORE_BITS) return fail(DBQ_ESTATE, "not a bit-packed database");
+    if (first < 0 || count < 0 || first + count > db->n)
+        return fail(DBQ_ERANGE, "entries outside [0, N)");
+    if (count == 0) return DBQ_OK;
+    if (!planes) return fail(DBQ_EINVAL, "planes is NULL");
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // [count*2] rows of `words` words out of rows of `wp` words
+    DBQ_CUDA(cudaMemcpy2DAsync(planes, (size_t)db->words * 4, db->planes + first * 2 * db->wp,
+                               (size_t)db->wp * 4, (size_t)db->words * 4, (size_t)count * 2,
+                               cudaMemcpyDefault, s));
+    if (sizes)
+        DBQ_CUDA(cudaMemcpyAsync(sizes, db->ecount + 2 * first, (size_t)count * 2 * 4,
+                                 cudaMemcpyDefault, s));
+    DBQ_CUDA(cudaStreamSynchronize(s));
+    return DBQ_OK;
+}
+
+int db_info(const dbq_db* db, int64_t out[8])
+{
+    if (!db || !out) return fail(DBQ_EINVAL, "NULL pointer argument");
+    out[0] = db->n;
+    out[1] = db->v;
+    out[2] = db->words;
+    out[3] = db->wp;
+    out[4] = db->storage;
+    out[5] = db->built ? 1 : 0;
+    out[6] = db->n_params;
+    out[7] = (int64_t)db->bytes_held;
+    return DBQ_OK;
+}
+
+int db_destroy(dbq_db* db)
+{
+    if (!db) return DBQ_OK;
+    {
+        DeviceGuard guard(db->device);
+        cudaDeviceSynchronize();
+        delete db;
+    }
+    return DBQ_OK;
+}
+
+}  // extern "C"

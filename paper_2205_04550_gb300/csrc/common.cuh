@@ -1,0 +1,97 @@
+// common.cuh -- device helpers shared by the query kernels of libdbq.
+//
+// Ranking (Section 2.3 of Ezhov et al. 2022: the entry with the largest
+// combined Dice is the best match): a candidate is (score, index, payload)
+// and the order is score descending, then index ascending, so the result
+// does not depend on how CTAs were scheduled.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dbq {
+
+constexpr double kSentinelScore = -1.0;            // below every Dice score (>= 0)
+constexpr int64_t kSentinelIndex = INT64_MAX;
+
+// Device-side copy of dbq_hit (same layout as the C ABI struct).
+struct Hit {
+    int64_t index;
+    double score;
+    uint32_t i1, i2, e1, e2, p1, p2;
+};
+static_assert(sizeof(Hit) == 40, "Hit must match dbq_hit");
+
+// One candidate of a per-CTA list: payload = (I_1 | I_2 << 32).
+struct Cand {
+    double score;
+    int64_t index;
+    uint64_t payload;
+};
+
+__device__ __forceinline__ bool better(double sa, int64_t ia, double sb, int64_t ib)
+{
+    return sa > sb || (sa == sb && ia < ib);
+}
+
+// Streaming 128-bit load: read-only path, no L1 allocation, 256-byte L2
+// prefetch -- the database is read once per query.
+__device__ __forceinline__ uint4 ld_stream(const uint4* p)
+{
+    uint4 r;
+    asm volatile("ld.global.nc.L1::no_allocate.L2::256B.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(r.x), "=r"(r.y), "=r"(r.z), "=r"(r.w)
+                 : "l"(p));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t popc_and4(const uint4& a, const uint4& b)
+{
+    return __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
+}
+
+// Dice from exact counts, IEEE binary64 round-to-nearest; both empty -> 1.
+__device__ __forceinline__ double dice_rn(uint32_t inter, uint32_t a, uint32_t b)
+{
+    const uint32_t den = a + b;
+    if (den == 0u) return 1.0;
+    return __ddiv_rn((double)(2u * inter), (double)den);
+}
+
+__device__ __forceinline__ double score_rn(uint32_t i1, uint32_t i2, uint32_t e1, uint32_t e2,
+                                           uint32_t p1, uint32_t p2)
+{
+    return __dmul_rn(__dadd_rn(dice_rn(i1, p1, e1), dice_rn(i2, p2, e2)), 0.5);
+}
+
+// Block-wide bitonic sort of n (a power of two, <= 2 * blockDim.x * 8)
+// candidates held in shared memory, best first.  All threads must call it.
+__device__ __forceinline__ void bitonic_sort_best_first(double* key, int64_t* idx, uint64_t* pay,
+                                                        int n)
+{
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
+                const int lo = 2 * t - (t & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const bool hi_better = better(key[hi], idx[hi], key[lo], idx[lo]);
+                if (hi_better == up) {
+                    const double k = key[lo]; key[lo] = key[hi]; key[hi] = k;
+                    const int64_t i = idx[lo]; idx[lo] = idx[hi]; idx[hi] = i;
+                    const uint64_t p = pay[lo]; pay[lo] = pay[hi]; pay[hi] = p;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__host__ __device__ __forceinline__ int next_pow2(int x)
+{
+    int p = 1;
+    while (p < x) p <<= 1;
+    return p;
+}
+
+}  // namespace dbq

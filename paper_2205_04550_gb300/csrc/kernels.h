@@ -1,0 +1,51 @@
+// kernels.h -- host-side launchers of the libdbq kernels (internal).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+
+namespace dbq {
+
+// Threshold volumes into bit planes (Section 2.3 thresholding) and count the
+// mask sizes.  vols: [count][v] float32 (src_f16 = 0) or binary16 bits
+// (src_f16 = 1), device.  planes: [count][2][wp] words, ecount: [count][2];
+// ecount must be zeroed by the caller.  Words past ceil(v/32) are written 0.
+cudaError_t launch_pack(const void* vols, int src_f16, int64_t count, int64_t v, int64_t wp,
+                        float t1, float t2, uint32_t* planes, uint32_t* ecount,
+                        cudaStream_t stream);
+
+// Round float32 to binary16, nearest-even (storage conversion of the
+// half-precision database).
+cudaError_t launch_to_f16(const float* src, int64_t n, uint16_t* dst, cudaStream_t stream);
+
+// Copy caller bit planes [2][words] into padded planes [2][wp], clearing bits
+// past voxel v-1, and count them into pcount[2] (zeroed by the caller).
+cudaError_t launch_import_bits(const uint32_t* src, int64_t words, int64_t v, int64_t wp,
+                               uint32_t* planes, uint32_t* pcount, cudaStream_t stream);
+
+// Arguments of the fused exact packed scan.
+struct ScanPackedArgs {
+    const uint4* planes;      // [n][2][wp4] database bit planes
+    const uint32_t* ecount;   // [n][2] |E_1|, |E_2|
+    const uint4* patient;     // [2][wp4] patient bit planes
+    const uint32_t* pcount;   // [2] |P_1|, |P_2|
+    int64_t n;                // entries
+    int wp4;                  // uint4 per plane (padded)
+    int chunk4;               // uint4 per plane per patient chunk held in shared memory
+    int nchunks;              // ceil(wp4 / chunk4)
+    int k;                    // results wanted (1..1024)
+    Cand* cand;               // scratch [gridDim.x][k]
+    unsigned int* ticket;     // scratch counter, 0 between launches
+    Hit* hits;                // [k] output (device), may be null when counts_out is set
+    uint32_t* counts_out;     // [n][4] per-entry (I1, I2, E1, E2), or null
+};
+
+// Grid size (CTAs) the scan uses on this device, and its shared memory bytes.
+int scan_packed_grid(int device);
+size_t scan_packed_smem(int chunk4);
+void scan_packed_chunking(int wp4, int* chunk4, int* nchunks);
+cudaError_t launch_scan_packed(const ScanPackedArgs& a, int grid, cudaStream_t stream);
+
+}  // namespace dbq

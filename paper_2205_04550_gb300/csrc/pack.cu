@@ -1,0 +1,149 @@
+// pack.cu -- thresholding of concentration volumes into bit planes.
+//
+// Section 2.3 of Ezhov et al. (2022): the simulated concentration u is
+// thresholded at u_T1Gd and u_FLAIR to give the two binary segmentations
+// compared with the patient's.  A voxel is in mask k when (float)u >= t_k.
+// Each warp turns 32 consecutive voxels into one 32-bit word per mask with
+// two ballots (bit b of word w = voxel 32w + b) and accumulates the mask
+// sizes |E_1|, |E_2| with popcounts.
+#include <cuda_fp16.h>
+
+#include "kernels.h"
+
+namespace dbq {
+namespace {
+
+constexpr int kPackThreads = 256;
+constexpr int kPackUnroll = 4;   // words per warp per iteration (loads in flight)
+
+template <bool kHalf>
+__device__ __forceinline__ float load_value(const void* base, int64_t i)
+{
+    if (kHalf) {
+        const unsigned short h = __ldg(reinterpret_cast<const unsigned short*>(base) + i);
+        return __half2float(__ushort_as_half(h));
+    }
+    return __ldg(reinterpret_cast<const float*>(base) + i);
+}
+
+template <bool kHalf>
+__global__ void __launch_bounds__(kPackThreads)
+pack_kernel(const void* __restrict__ vols, int64_t v, int64_t wp, float t1, float t2,
+            uint32_t* __restrict__ planes, uint32_t* __restrict__ ecount, int64_t e_base)
+{
+    const int64_t e = e_base + blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * kPackThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kPackThreads) >> 5;
+    const char* src = reinterpret_cast<const char*>(vols) + e * v * (kHalf ? 2 : 4);
+    uint32_t* p1 = planes + e * 2 * wp;
+    uint32_t* p2 = p1 + wp;
+    uint32_t c1 = 0, c2 = 0;
+    for (int64_t w0 = warp * kPackUnroll; w0 < wp; w0 += nwarps * kPackUnroll) {
+        float val[kPackUnroll];
+#pragma unroll
+        for (int u = 0; u < kPackUnroll; ++u) {
+            const int64_t x = (w0 + u) * 32 + lane;
+            val[u] = (x < v) ? load_value<kHalf>(src, x) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kPackUnroll; ++u) {
+            const int64_t w = w0 + u;
+            const int64_t x = w * 32 + lane;
+            const bool in = x < v;
+            const uint32_t b1 = __ballot_sync(0xffffffffu, in && val[u] >= t1);
+            const uint32_t b2 = __ballot_sync(0xffffffffu, in && val[u] >= t2);
+            if (lane == 0 && w < wp) {
+                p1[w] = b1;
+                p2[w] = b2;
+                c1 += __popc(b1);
+                c2 += __popc(b2);
+            }
+        }
+    }
+    if (lane == 0 && (c1 | c2)) {
+        atomicAdd(&ecount[2 * e], c1);
+        atomicAdd(&ecount[2 * e + 1], c2);
+    }
+}
+
+__global__ void import_bits_kernel(const uint32_t* __restrict__ src, int64_t words, int64_t v,
+                                   int64_t wp, uint32_t* __restrict__ planes,
+                                   uint32_t* __restrict__ pcount)
+{
+    const int k = blockIdx.y;
+    uint32_t c = 0;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < wp;
+         w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t word = 0;
+        if (w < words) {
+            word = src[k * words + w];
+            const int64_t first = w * 32;
+            if (first + 32 > v) {
+                const int64_t keep = v - first;          // 0 < keep < 32 here
+                word &= (keep <= 0) ? 0u : ((1u << keep) - 1u);
+            }
+        }
+        planes[k * wp + w] = word;
+        c += __popc(word);
+    }
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(&pcount[k], c);
+}
+
+__global__ void to_f16_kernel(const float* __restrict__ src, int64_t n,
+                              unsigned short* __restrict__ dst)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = __half_as_ushort(__float2half_rn(src[i]));
+}
+
+}  // namespace
+
+cudaError_t launch_to_f16(const float* src, int64_t n, uint16_t* dst, cudaStream_t stream)
+{
+    if (n <= 0) return cudaSuccess;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    to_f16_kernel<<<(unsigned)blocks, 256, 0, stream>>>(src, n,
+                                                        reinterpret_cast<unsigned short*>(dst));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const void* vols, int src_f16, int64_t count, int64_t v, int64_t wp,
+                        float t1, float t2, uint32_t* planes, uint32_t* ecount,
+                        cudaStream_t stream)
+{
+    if (count <= 0) return cudaSuccess;
+    const int64_t warps_needed = (wp + kPackUnroll - 1) / kPackUnroll;
+    int64_t bx = (warps_needed * 32 + kPackThreads - 1) / kPackThreads;
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    for (int64_t e0 = 0; e0 < count; e0 += 65535) {
+        const int64_t ce = (count - e0) < 65535 ? (count - e0) : 65535;
+        dim3 grid((unsigned)bx, (unsigned)ce);
+        if (src_f16)
+            pack_kernel<true><<<grid, kPackThreads, 0, stream>>>(vols, v, wp, t1, t2, planes,
+                                                                 ecount, e0);
+        else
+            pack_kernel<false><<<grid, kPackThreads, 0, stream>>>(vols, v, wp, t1, t2, planes,
+                                                                  ecount, e0);
+        const cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_import_bits(const uint32_t* src, int64_t words, int64_t v, int64_t wp,
+                               uint32_t* planes, uint32_t* pcount, cudaStream_t stream)
+{
+    int64_t bx = (wp + 255) / 256;
+    if (bx > 256) bx = 256;
+    if (bx < 1) bx = 1;
+    import_bits_kernel<<<dim3((unsigned)bx, 2), 256, 0, stream>>>(src, words, v, wp, planes,
+                                                                   pcount);
+    return cudaGetLastError();
+}
+
+}  // namespace dbq

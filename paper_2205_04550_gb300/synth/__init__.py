@@ -255,28 +255,56 @@ def _load():
         return _lib
 
 
+class DeviceGenerator:
+    """Parameters of a range of entries computed once on the host (binary64)
+    and uploaded; ``fill`` generates any sub-range of their volumes on the GPU."""
+
+    def __init__(self, shape, seed: int, entries, device="cuda"):
+        import torch
+        self.shape = tuple(int(s) for s in shape)
+        self.entries = np.asarray(entries, dtype=np.uint64).reshape(-1)
+        self.theta = entry_params(self.shape, seed, self.entries)
+        keys = noise_keys(stream_keys(seed, self.entries))
+        self.device = torch.device(device)
+        self._theta = torch.from_numpy(self.theta.astype(np.float32)).to(self.device)
+        self._keys = torch.from_numpy(keys.view(np.int64)).to(self.device)
+        self._xr = torch.from_numpy(brain_xrange_cached(self.shape)).to(self.device)
+
+    def __len__(self):
+        return self.entries.shape[0]
+
+    def fill(self, first: int, count: int, out):
+        """Write volumes of entries [first, first+count) of this generator into
+        ``out`` (contiguous float32 or float16 CUDA tensor) on the current stream."""
+        import torch
+        nx, ny, nz = self.shape
+        if first < 0 or count < 0 or first + count > len(self):
+            raise IndexError("entry range outside the generator")
+        if not out.is_contiguous() or out.numel() < count * nx * ny * nz:
+            raise ValueError("bad output tensor")
+        if out.dtype not in (torch.float32, torch.float16):
+            raise ValueError("output must be float32 or float16")
+        stream = torch.cuda.current_stream(out.device).cuda_stream
+        rc = _load().synth_generate(self._theta.data_ptr() + first * 8 * 4,
+                                    self._keys.data_ptr() + first * 8, self._xr.data_ptr(),
+                                    nx, ny, nz, count, 1 if out.dtype == torch.float16 else 0,
+                                    out.data_ptr(), stream)
+        if rc != 0:
+            raise RuntimeError(f"synth_generate failed: {rc}")
+        return out
+
+
 def generate_device(shape, seed: int, entries, dtype="float32", out=None, device="cuda"):
     """Volumes for ``entries`` generated on the GPU -> (torch tensor
     [n, nz, ny, nx] on ``device``, theta float64 numpy [n, 8]).
 
     ``out`` may be a preallocated contiguous tensor of the right size."""
     import torch
-    entries = np.asarray(entries, dtype=np.uint64).reshape(-1)
-    n = entries.shape[0]
-    theta = entry_params(shape, seed, entries)
-    keys = noise_keys(stream_keys(seed, entries))
-    nx, ny, nz = shape
+    gen = DeviceGenerator(shape, seed, entries, device if out is None else out.device)
+    nx, ny, nz = gen.shape
+    n = len(gen)
     tdt = torch.float16 if dtype in ("float16", np.float16, torch.float16) else torch.float32
     if out is None:
         out = torch.empty((n, nz, ny, nx), dtype=tdt, device=device)
-    if out.dtype != tdt or not out.is_contiguous() or out.numel() < n * nx * ny * nz:
-        raise ValueError("bad output tensor")
-    th = torch.from_numpy(theta.astype(np.float32)).to(out.device)
-    ky = torch.from_numpy(keys.view(np.int64)).to(out.device)
-    xr = torch.from_numpy(brain_xrange_cached(shape)).to(out.device)
-    stream = torch.cuda.current_stream(out.device).cuda_stream
-    rc = _load().synth_generate(th.data_ptr(), ky.data_ptr(), xr.data_ptr(), nx, ny, nz,
-                                n, 1 if tdt == torch.float16 else 0, out.data_ptr(), stream)
-    if rc != 0:
-        raise RuntimeError(f"synth_generate failed: {rc}")
-    return out, theta
+    gen.fill(0, n, out)
+    return out, gen.theta

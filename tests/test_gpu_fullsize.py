@@ -1,0 +1,94 @@
+"""Parity at the full workload sizes, in the launch configuration the
+benchmark times.
+
+* 1,024 entries at 64^3 (float32 surrogate volumes, t = 0.6 / 0.25, top-10):
+  the oracle runs over the whole database; every count, the scores and the
+  top-10 must match exactly.
+* 50,000 entries at 128^3 bit-packed (top-64): the oracle recomputes the
+  counts of a seeded sample of entries and of every returned hit from the
+  same volumes, and ranks the GPU's per-entry counts with its own scoring --
+  the GPU top-64 must equal that ranking exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_04550_gb300 import DBQ_STORE_BITS, Database, synth
+from tests._gpu_helpers import assert_hits_equal
+
+pytestmark = pytest.mark.gpu
+
+T1, T2 = np.float32(0.6), np.float32(0.25)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    from paper_2205_04550_gb300 import build
+    build.build()
+    return _t
+
+
+def _build_db_on_device(torch, shape, n, chunk, n_params=8):
+    db = Database(shape, n, DBQ_STORE_BITS, T1, T2, n_params)
+    nx, ny, nz = shape
+    gen = synth.DeviceGenerator(shape, synth.DB_SEED, np.arange(n))
+    buf = torch.empty((chunk, nz, ny, nx), dtype=torch.float32, device="cuda")
+    for c0 in range(0, n, chunk):
+        cn = min(chunk, n - c0)
+        gen.fill(c0, cn, buf)
+        db.load(c0, buf[:cn], params=gen.theta[c0:c0 + cn])
+    db.build()
+    torch.cuda.synchronize()
+    return db
+
+
+def test_exact_query_1024_entries_64cube_full_oracle(torch):
+    shape = (64, 64, 64)
+    n, k = 1024, 10
+    vols_dev, theta = synth.generate_device(shape, synth.DB_SEED, np.arange(n))
+    vols = vols_dev.cpu().numpy()
+    pat, _ = synth.patients_np(shape, [1])
+    ref = oracle.query(vols, pat[0], T1, T2, k)
+    with Database(shape, n, DBQ_STORE_BITS, T1, T2, 8) as db:
+        db.load(0, vols_dev, params=theta)
+        db.build()
+        hits, params = db.query(pat[0], k)
+        assert_hits_equal(hits, ref, k)
+        np.testing.assert_array_equal(params, theta[ref["index"]])
+        counts, pcount = db.scan_counts(pat[0])
+        np.testing.assert_array_equal(counts, ref["all_counts"])
+        np.testing.assert_array_equal(pcount, ref["pcount"])
+
+
+def test_exact_query_50000_entries_128cube_sampled(torch):
+    shape = (128, 128, 128)
+    n, k = 50_000, 64
+    db = _build_db_on_device(torch, shape, n, chunk=8)
+    try:
+        pat, _ = synth.patients_np(shape, [1])
+        patient = pat[0]
+        hits, params = db.query(patient, k)
+        counts, pcount = db.scan_counts(patient)
+        pmask = oracle.threshold(patient, T1, T2)
+        np.testing.assert_array_equal(pcount, pmask.sum(axis=1))
+        # the ranking of the GPU's counts by the oracle's scoring and order
+        sc = oracle.scores(counts, pcount)
+        idx, val = oracle.rank(sc, k)
+        np.testing.assert_array_equal(hits["index"], idx)
+        np.testing.assert_array_equal(hits["score"].view(np.uint64), val.view(np.uint64))
+        # the counts themselves, recomputed by the oracle from the volumes
+        rng = np.random.default_rng(20220510)
+        sample = np.unique(np.concatenate([rng.choice(n, 48, replace=False), idx,
+                                           [0, n - 1]]))
+        vols_dev, _ = synth.generate_device(shape, synth.DB_SEED, sample)
+        vols = vols_dev.cpu().numpy()
+        ref_counts, ref_p = oracle.counts(vols, pmask, T1, T2)
+        np.testing.assert_array_equal(counts[sample], ref_counts)
+        np.testing.assert_array_equal(pcount, ref_p)
+        hit_counts = np.stack([hits[f] for f in ("i1", "i2", "e1", "e2")], axis=1)
+        np.testing.assert_array_equal(hit_counts, counts[idx])
+        theta = synth.entry_params(shape, synth.DB_SEED, idx)
+        np.testing.assert_array_equal(params, theta)
+    finally:
+        db.close()
