@@ -33,6 +33,15 @@ sys.path.insert(0, ROOT)
 WORKLOADS = {
     "exact_packed_50k_128": dict(shape=(128, 128, 128), n=50_000, k=64, t1=0.6, t2=0.25,
                                  desc="50,000 x 128^3 bit-packed, t=(0.6,0.25), top-64"),
+    "exact_packed_2k_128": dict(shape=(128, 128, 128), n=2000, k=64, t1=0.6, t2=0.25,
+                                desc="2,000 x 128^3 bit-packed (1.05 GB, profiling size), "
+                                     "t=(0.6,0.25), top-64"),
+    "f16_100k_64": dict(shape=(64, 64, 64), n=100_000, k=16, t1=0.6, t2=0.25, storage="f16",
+                        desc="100,000 x 64^3 binary16 (52.4 GB), per-query thresholds "
+                             "t1~U(0.5,0.8), t2~U(0.15,0.35), top-16"),
+    "f16_4k_64": dict(shape=(64, 64, 64), n=4000, k=16, t1=0.6, t2=0.25, storage="f16",
+                      desc="4,000 x 64^3 binary16 (2.1 GB, profiling size), per-query "
+                           "thresholds, top-16"),
     "exact_packed_1k_64": dict(shape=(64, 64, 64), n=1024, k=10, t1=0.6, t2=0.25,
                                desc="1,024 x 64^3 bit-packed, t=(0.6,0.25), top-10"),
 }
@@ -124,29 +133,48 @@ class ClockSampler:
 
 def build_database(torch, wl, chunk: int = 8):
     """Generate the surrogate database on the GPU in L2-sized chunks and
-    threshold/pack each chunk as it is made (not timed)."""
-    from paper_2205_04550_gb300 import DBQ_STORE_BITS, Database, synth
+    load each chunk as it is made (thresholded and packed for bit-packed
+    storage, rounded to binary16 for half storage); not timed."""
+    from paper_2205_04550_gb300 import DBQ_STORE_BITS, DBQ_STORE_F16, Database, _dbq, synth
     shape, n = wl["shape"], wl["n"]
     nx, ny, nz = shape
+    f16 = wl.get("storage") == "f16"
     gen = synth.DeviceGenerator(shape, synth.DB_SEED, np.arange(n))
-    db = Database(shape, n, DBQ_STORE_BITS, wl["t1"], wl["t2"], synth.N_PARAMS)
-    buf = torch.empty((chunk, nz, ny, nx), dtype=torch.float32, device="cuda")
+    db = Database(shape, n, DBQ_STORE_F16 if f16 else DBQ_STORE_BITS, wl["t1"], wl["t2"],
+                  synth.N_PARAMS)
+    if f16:
+        chunk *= 8
+    buf = torch.empty((chunk, nz, ny, nx), dtype=torch.float16 if f16 else torch.float32,
+                      device="cuda")
     for c0 in range(0, n, chunk):
         cn = min(chunk, n - c0)
         gen.fill(c0, cn, buf)
-        db.load(c0, buf[:cn], params=gen.theta[c0:c0 + cn])
+        _dbq.db_load_volumes(db.handle, c0, cn, buf, kind=_dbq.DBQ_F16 if f16 else _dbq.DBQ_F32,
+                             params=gen.theta[c0:c0 + cn])
     db.build()
     torch.cuda.synchronize()
     return db
 
 
+def query_thresholds(wl, q: int):
+    """Per-query thresholds: fixed build thresholds for bit-packed storage;
+    t1 ~ U(0.5, 0.8), t2 ~ U(0.15, 0.35) seeded by the query for binary16."""
+    if wl.get("storage") != "f16":
+        return float("nan"), float("nan")
+    rng = np.random.default_rng(1000 + q)
+    return float(np.float32(rng.uniform(0.5, 0.8))), float(np.float32(rng.uniform(0.15, 0.35)))
+
+
 def algorithmic_bytes(wl) -> int:
-    """Bytes the exact scan must move per query: both bit planes of every
-    entry (ceil(V/32) words each), the entry's two mask sizes, and the
-    patient's two planes."""
+    """Bytes the exact scan must move per query.  Bit-packed: both bit planes
+    of every entry (ceil(V/32) words each) and its two mask sizes.  binary16:
+    every entry's V half values.  Plus the patient's two planes."""
     nx, ny, nz = wl["shape"]
-    words = (nx * ny * nz + 31) // 32
+    v = nx * ny * nz
+    words = (v + 31) // 32
     n = wl["n"]
+    if wl.get("storage") == "f16":
+        return n * 2 * v + 2 * words * 4
     return n * (2 * words * 4 + 2 * 4) + 2 * words * 4
 
 
@@ -154,17 +182,21 @@ def _oracle_sample(wl, sample_entries: int):
     import oracle
     from paper_2205_04550_gb300 import synth
     shape = wl["shape"]
-    vols, _ = synth.generate_np(shape, synth.DB_SEED, np.arange(sample_entries))
-    pat, _ = synth.patients_np(shape, [1])
-    pmask = oracle.threshold(pat[0], wl["t1"], wl["t2"])
-    return vols, pmask
+    f16 = wl.get("storage") == "f16"
+    dt = np.float16 if f16 else np.float32
+    vols, _ = synth.generate_np(shape, synth.DB_SEED, np.arange(sample_entries), dtype=dt)
+    pat, _ = synth.patients_np(shape, [1], dtype=dt)
+    t1, t2 = query_thresholds(wl, 0) if f16 else (wl["t1"], wl["t2"])
+    pmask = oracle.threshold(pat[0], t1, t2)
+    return vols, pmask, t1, t2
 
 
-def _oracle_pass(wl, vols, pmask, nthreads: int = 0):
+def _oracle_pass(wl, sample, nthreads: int = 0):
     """One pass of the oracle's query over the sample: threshold, count,
     score and rank every sampled entry."""
     import oracle
-    cnt, pc = oracle.counts(vols, pmask, wl["t1"], wl["t2"], nthreads)
+    vols, pmask, t1, t2 = sample
+    cnt, pc = oracle.counts(vols, pmask, t1, t2, nthreads)
     sc = oracle.scores(cnt, pc)
     oracle.rank(sc, min(wl["k"], vols.shape[0]))
 
@@ -172,10 +204,10 @@ def _oracle_pass(wl, vols, pmask, nthreads: int = 0):
 def cpu_baseline(wl, sample_entries: int, min_seconds: float, nthreads: int = 0):
     """The oracle as it stands on a bounded sample of the workload's entries."""
     import oracle
-    vols, pmask = _oracle_sample(wl, sample_entries)
+    sample = _oracle_sample(wl, sample_entries)
     reps, t0 = 0, time.perf_counter()
     while True:
-        _oracle_pass(wl, vols, pmask, nthreads)
+        _oracle_pass(wl, sample, nthreads)
         reps += 1
         el = time.perf_counter() - t0
         if el >= min_seconds:
@@ -184,7 +216,8 @@ def cpu_baseline(wl, sample_entries: int, min_seconds: float, nthreads: int = 0)
     cores = nthreads if nthreads > 0 else oracle.num_threads()
     shape = wl["shape"]
     return {"value": rate, "unit": "entries/s", "cores": cores, "kind": "oracle",
-            "sample": f"{sample_entries} of {wl['n']:,} entries ({shape[0]}^3 float32, same "
+            "sample": f"{sample_entries} of {wl['n']:,} entries ({shape[0]}^3 "
+                      f"{'binary16' if wl.get('storage') == 'f16' else 'float32'}, same "
                       f"generator), queried {reps}x in {el:.1f} s (threshold, count, score, "
                       f"rank)",
             "host_cpus": os.cpu_count()}
@@ -198,22 +231,23 @@ def run_reference(args, wl):
     if rank != 0:
         return 0
     sample = args.cpu_sample
-    vols, pmask = _oracle_sample(wl, sample)
+    smp = _oracle_sample(wl, sample)
     t0 = time.perf_counter()
     for _ in range(max(1, args.warmup)):
-        _oracle_pass(wl, vols, pmask)
+        _oracle_pass(wl, smp)
     rate = max(1, args.warmup) * sample / (time.perf_counter() - t0)
     reps = max(1, int(round(0.2 * rate / sample)))
     t0 = time.perf_counter()
     for _ in range(args.steps):
         for _ in range(reps):
-            _oracle_pass(wl, vols, pmask)
+            _oracle_pass(wl, smp)
     t = time.perf_counter() - t0
     per_step = reps * sample
     value = args.steps * per_step / t
     cores = oracle.num_threads()
     desc = (f"{per_step} entry scores per step ({reps} passes over {sample} of {wl['n']:,} "
-            f"entries, {wl['shape'][0]}^3 float32)")
+            f"entries, {wl['shape'][0]}^3 "
+            f"{'binary16' if wl.get('storage') == 'f16' else 'float32'})")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "entries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
@@ -257,15 +291,21 @@ def main(argv=None):
     db = build_database(torch, wl)
     k = wl["k"]
     shape = wl["shape"]
-    pats, _ = synth.patients_np(shape, [1, 2, 3, 4])
-    pats_dev = torch.from_numpy(pats).cuda()
+    f16 = wl.get("storage") == "f16"
+    pats, _ = synth.patients_np(shape, [1, 2, 3, 4], dtype=np.float16 if f16 else np.float32)
+    if f16:
+        pats = pats.view(np.uint16)
+    pats_dev = torch.from_numpy(pats.view(np.int16) if f16 else pats).cuda()
+    thr = [query_thresholds(wl, q) for q in range(4)]
     hits_dev = torch.zeros((k, 40), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     h = db.handle
 
     def step(i, ev=None):
         p = pats_dev[i % 4]
-        _dbq.db_prepare_patient(h, p, stream=stream)
+        t1, t2 = thr[i % 4]
+        _dbq.db_prepare_patient(h, p, t1, t2, kind=_dbq.DBQ_F16 if f16 else _dbq.DBQ_F32,
+                                stream=stream)
         if ev is not None:
             ev[0].record(stream)
         _dbq.db_query_prepared(h, k, hits_dev, stream=stream)
@@ -307,18 +347,18 @@ def main(argv=None):
     value = world * args.steps * n_entries / elapsed
 
     # end to end through db_query: pinned host patient in, host hits out
-    pinned = torch.from_numpy(pats).pin_memory()
-    pin_np = pinned.numpy()
+    pinned = torch.from_numpy(pats.view(np.int16) if f16 else pats).pin_memory()
+    pin_np = pinned.numpy().view(np.uint16) if f16 else pinned.numpy()
     e2e_steps = max(10, args.steps // 3)
     for i in range(3):
-        db.query(pin_np[i % 4], k)
+        db.query(pin_np[i % 4], k, *thr[i % 4])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     e0 = time.perf_counter()
     w0 = time.time()
     for i in range(e2e_steps):
-        db.query(pin_np[i % 4], k)
+        db.query(pin_np[i % 4], k, *thr[i % 4])
     torch.cuda.synchronize()
     e_el = time.perf_counter() - e0
     w1 = time.time()
@@ -337,16 +377,19 @@ def main(argv=None):
         "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16" if f16 else "u32",
+        "data": "synthetic",
         "config": {"workload": args.workload, "desc": wl["desc"], "entries": n_entries,
                    "grid": list(shape), "k": k, "thresholds": [wl["t1"], wl["t2"]],
-                   "l2": "inputs larger than L2 (26.2 GB packed DB vs 129 MB L2); no flush",
+                   "l2": f"inputs larger than L2 ({algorithmic_bytes(wl) / 1e9:.2f} GB DB "
+                         "vs 129 MB L2); no flush",
                    "parallelism": "replicas" if world > 1 else "single-gpu",
                    "voxels_per_s": value * shape[0] * shape[1] * shape[2]},
         "e2e": {"value": e2e_value, "unit": "entries/s",
                 "h2d_bytes_per_step": int(pats[0].nbytes), "d2h_bytes_per_step": k * 40},
         "gpu_launches": 2 * args.steps,   # per step: patient pack + fused scan
-        "roofline": {"bound": "hbm", "kernel": "scan_packed_kernel", "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": "scan_f16_kernel" if f16 else "scan_packed_kernel",
+                     "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": None,
                      "algorithmic_bytes_per_launch": alg,

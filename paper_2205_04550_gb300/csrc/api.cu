@@ -90,7 +90,9 @@ struct dbq_db {
     // database
     uint32_t* planes = nullptr;     // [n][2][wp]
     uint32_t* ecount = nullptr;     // [n][2]
-    uint16_t* vols16 = nullptr;     // [n][v] (F16 storage)
+    uint16_t* vols16 = nullptr;     // [n][vp] (F16 storage, rows padded with zeros)
+    int64_t vp = 0;                 // F16 row length: V rounded up to 1024
+    int blocks = 0;                 // F16: 1024-voxel blocks per row
     std::vector<double> params;     // [n][n_params]
     std::vector<uint8_t> loaded;
     int64_t n_loaded = 0;
@@ -237,7 +239,26 @@ int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaSt
         if (err != cudaSuccess) return cuda_fail(err, "scan_packed launch");
         return DBQ_OK;
     }
-    return fail(DBQ_ESTATE, "half-precision storage query is not available in this build");
+    dbq::ScanF16Args a;
+    a.vols = reinterpret_cast<const uint4*>(db->vols16);
+    a.patient = db->pplanes;
+    a.pcount = db->pcount;
+    a.n = db->n;
+    a.blocks = db->blocks;
+    a.wp = (int)db->wp;
+    dbq::scan_f16_chunking(db->blocks, &a.chunk_blocks, &a.nchunks);
+    a.k = k;
+    const uint32_t th1 = dbq::f16_threshold_bits(db->prep_t1);
+    const uint32_t th2 = dbq::f16_threshold_bits(db->prep_t2);
+    a.th1x2 = th1 | (th1 << 16);
+    a.th2x2 = th2 | (th2 << 16);
+    a.cand = db->cand;
+    a.ticket = db->ticket;
+    a.hits = hits;
+    a.counts_out = counts_out;
+    cudaError_t err = dbq::launch_scan_f16(a, db->grid, s);
+    if (err != cudaSuccess) return cuda_fail(err, "scan_f16 launch");
+    return DBQ_OK;
 }
 
 }  // namespace
@@ -273,7 +294,13 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
     db->nz = nz;
     db->v = v;
     db->words = (v + 31) / 32;
-    db->wp = (db->words + 3) / 4 * 4;
+    if (storage == DBQ_STORE_F16) {
+        db->blocks = (int)((v + 1023) / 1024);
+        db->vp = (int64_t)db->blocks * 1024;
+        db->wp = (int64_t)db->blocks * 32;     // patient planes cover whole blocks
+    } else {
+        db->wp = (db->words + 3) / 4 * 4;
+    }
     db->wp4 = (int)(db->wp / 4);
     db->n = capacity;
     db->storage = storage;
@@ -296,7 +323,7 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
             rc = dev_alloc(db, &db->ecount, (size_t)capacity * 2 * sizeof(uint32_t),
                            "mask sizes");
     } else {
-        rc = dev_alloc(db, &db->vols16, (size_t)capacity * v * sizeof(uint16_t),
+        rc = dev_alloc(db, &db->vols16, (size_t)capacity * db->vp * sizeof(uint16_t),
                        "binary16 volumes");
     }
     db->grid = dbq::scan_packed_grid(dev);
@@ -321,6 +348,8 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
         cudaError_t err = cudaMemset(db->ticket, 0, sizeof(unsigned int));
         if (err == cudaSuccess && db->ecount)
             err = cudaMemset(db->ecount, 0, (size_t)capacity * 2 * sizeof(uint32_t));
+        if (err == cudaSuccess && db->vols16)   // zero padding never reaches a threshold
+            err = cudaMemset(db->vols16, 0, (size_t)capacity * db->vp * sizeof(uint16_t));
         if (err == cudaSuccess) err = cudaDeviceSynchronize();
         if (err != cudaSuccess) rc = cuda_fail(err, "workspace initialisation");
     }
@@ -376,15 +405,10 @@ int db_load_volumes(dbq_db* db, int64_t first, int64_t count, const void* vols, 
                                                db->ecount + 2 * e0, s);
             if (err != cudaSuccess) return cuda_fail(err, "pack launch");
         } else {
-            uint16_t* dst = db->vols16 + e0 * db->v;
-            if (kind == DBQ_F16) {
-                DBQ_CUDA(cudaMemcpyAsync(dst, src, (size_t)cn * vol_bytes,
-                                         cudaMemcpyDeviceToDevice, s));
-            } else {
-                cudaError_t err = dbq::launch_to_f16(reinterpret_cast<const float*>(src),
-                                                     cn * db->v, dst, s);
-                if (err != cudaSuccess) return cuda_fail(err, "binary16 conversion launch");
-            }
+            uint16_t* dst = db->vols16 + e0 * db->vp;
+            cudaError_t err = dbq::launch_rows_to_f16(src, kind == DBQ_F16, cn, db->v, db->vp,
+                                                      dst, s);
+            if (err != cudaSuccess) return cuda_fail(err, "binary16 storage launch");
         }
     }
     if (!on_dev) DBQ_CUDA(cudaStreamSynchronize(s));   // the caller may reuse its buffer

@@ -22,11 +22,12 @@ struct Hit {
 };
 static_assert(sizeof(Hit) == 40, "Hit must match dbq_hit");
 
-// One candidate of a per-CTA list: payload = (I_1 | I_2 << 32).
+// One candidate of a per-CTA list; pay0/pay1 carry the entry's counts.
 struct Cand {
     double score;
     int64_t index;
-    uint64_t payload;
+    uint64_t pay0;
+    uint64_t pay1;
 };
 
 __device__ __forceinline__ bool better(double sa, int64_t ia, double sb, int64_t ib)
@@ -62,29 +63,6 @@ __device__ __forceinline__ double score_rn(uint32_t i1, uint32_t i2, uint32_t e1
                                            uint32_t p1, uint32_t p2)
 {
     return __dmul_rn(__dadd_rn(dice_rn(i1, p1, e1), dice_rn(i2, p2, e2)), 0.5);
-}
-
-// Block-wide bitonic sort of n (a power of two, <= 2 * blockDim.x * 8)
-// candidates held in shared memory, best first.  All threads must call it.
-__device__ __forceinline__ void bitonic_sort_best_first(double* key, int64_t* idx, uint64_t* pay,
-                                                        int n)
-{
-    for (int size = 2; size <= n; size <<= 1) {
-        for (int stride = size >> 1; stride > 0; stride >>= 1) {
-            for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
-                const int lo = 2 * t - (t & (stride - 1));
-                const int hi = lo + stride;
-                const bool up = (lo & size) == 0;
-                const bool hi_better = better(key[hi], idx[hi], key[lo], idx[lo]);
-                if (hi_better == up) {
-                    const double k = key[lo]; key[lo] = key[hi]; key[hi] = k;
-                    const int64_t i = idx[lo]; idx[lo] = idx[hi]; idx[hi] = i;
-                    const uint64_t p = pay[lo]; pay[lo] = pay[hi]; pay[hi] = p;
-                }
-            }
-            __syncthreads();
-        }
-    }
 }
 
 __host__ __device__ __forceinline__ int next_pow2(int x)

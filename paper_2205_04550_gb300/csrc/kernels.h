@@ -48,4 +48,33 @@ size_t scan_packed_smem(int chunk4);
 void scan_packed_chunking(int wp4, int* chunk4, int* nchunks);
 cudaError_t launch_scan_packed(const ScanPackedArgs& a, int grid, cudaStream_t stream);
 
+// Arguments of the fused half-precision scan (per-query thresholds).
+struct ScanF16Args {
+    const uint4* vols;        // [n][blocks * 128] binary16 rows, 1024 voxels per block
+    const uint32_t* patient;  // [2][wp] patient bit planes, wp = blocks * 32 words
+    const uint32_t* pcount;   // [2] |P_1|, |P_2|
+    int64_t n;                // entries
+    int blocks;               // 1024-voxel blocks per entry row
+    int wp;                   // words per patient plane (= blocks * 32)
+    int chunk_blocks;         // blocks per patient chunk held in shared memory
+    int nchunks;              // ceil(blocks / chunk_blocks)
+    int k;                    // results wanted (1..1024)
+    uint32_t th1x2, th2x2;    // smallest binary16 >= t_k, in both halves
+    Cand* cand;               // scratch [gridDim.x][k]
+    unsigned int* ticket;     // scratch counter, 0 between launches
+    Hit* hits;                // [k] output, or null when only counts_out is wanted
+    uint32_t* counts_out;     // [n][4] per-entry (I1, I2, E1, E2), or null
+};
+
+void scan_f16_chunking(int blocks, int* chunk_blocks, int* nchunks);
+size_t scan_f16_smem(int chunk_blocks);
+// Smallest binary16 bit pattern whose value is >= t (0 < t <= 1).
+uint16_t f16_threshold_bits(float t);
+cudaError_t launch_scan_f16(const ScanF16Args& a, int grid, cudaStream_t stream);
+
+// Copy `count` rows of `v` binary16 values (or float32 values rounded to
+// nearest-even) into rows of `pitch` halves; the padding is left untouched.
+cudaError_t launch_rows_to_f16(const void* src, int src_f16, int64_t count, int64_t v,
+                               int64_t pitch, uint16_t* dst, cudaStream_t stream);
+
 }  // namespace dbq

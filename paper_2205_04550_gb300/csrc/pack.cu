@@ -99,7 +99,42 @@ __global__ void to_f16_kernel(const float* __restrict__ src, int64_t n,
         dst[i] = __half_as_ushort(__float2half_rn(src[i]));
 }
 
+template <bool kSrcHalf>
+__global__ void rows_to_f16_kernel(const void* __restrict__ src, int64_t v, int64_t pitch,
+                                   unsigned short* __restrict__ dst, int64_t row_base)
+{
+    const int64_t row = row_base + blockIdx.y;
+    unsigned short* d = dst + row * pitch;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < v;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (kSrcHalf)
+            d[i] = reinterpret_cast<const unsigned short*>(src)[row * v + i];
+        else
+            d[i] = __half_as_ushort(__float2half_rn(reinterpret_cast<const float*>(src)[row * v + i]));
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_rows_to_f16(const void* src, int src_f16, int64_t count, int64_t v,
+                               int64_t pitch, uint16_t* dst, cudaStream_t stream)
+{
+    int64_t bx = (v + 255) / 256;
+    if (bx > 1024) bx = 1024;
+    if (bx < 1) bx = 1;
+    unsigned short* d = reinterpret_cast<unsigned short*>(dst);
+    for (int64_t r0 = 0; r0 < count; r0 += 65535) {
+        const int64_t rc = (count - r0) < 65535 ? (count - r0) : 65535;
+        dim3 grid((unsigned)bx, (unsigned)rc);
+        if (src_f16)
+            rows_to_f16_kernel<true><<<grid, 256, 0, stream>>>(src, v, pitch, d, r0);
+        else
+            rows_to_f16_kernel<false><<<grid, 256, 0, stream>>>(src, v, pitch, d, r0);
+        const cudaError_t err = cudaGetLastError();
+        if (err != cudaSuccess) return err;
+    }
+    return cudaSuccess;
+}
 
 cudaError_t launch_to_f16(const float* src, int64_t n, uint16_t* dst, cudaStream_t stream)
 {

@@ -10,128 +10,66 @@
 //
 // GB300 mapping (one CTA of 1024 threads per SM, persistent):
 //   * CTA b owns the contiguous entry range [b*N/G, (b+1)*N/G).
-//   * The patient's planes are split into chunks of at most 2 x 64 KiB that
-//     live in shared memory; for each chunk the CTA streams the matching
-//     words of each of its entries from HBM with 128-bit no-L1-allocate
-//     loads (every database byte is read exactly once per query), ANDs them
-//     with the shared-memory copy, POPCs, reduces across the warp with
-//     redux.sync and adds the warp's sum into a per-entry shared counter.
+//   * The patient's planes are split into chunks of 2 x 32 KiB.  Within a
+//     chunk, thread t always handles the same two 16-byte positions of each
+//     plane, so it holds the patient's words for them in registers; it then
+//     streams those positions of each of its entries from HBM with 128-bit
+//     no-L1-allocate loads (every database byte is read exactly once per
+//     query, two entries in flight), ANDs, POPCs, reduces across the warp
+//     with redux.sync and adds the warp's sum into a per-entry shared
+//     counter.
 //   * When every chunk of a group of entries is done the CTA knows their
 //     exact I_1, I_2, computes the binary64 scores and keeps a running
 //     top-k in shared memory (bitonic sort, order: score desc, index asc).
 //   * Each CTA writes its list to scratch; the last CTA to finish (atomic
 //     ticket, no spinning) merges all lists and writes the k hits.
 #include "kernels.h"
+#include "topk.cuh"
 
 namespace dbq {
 namespace {
 
 constexpr int kThreads = 1024;
-constexpr int kCap = 2048;          // shared candidate buffer (running top-k + new)
 constexpr int kGroup = 1024;        // entries whose counters live in shared memory
-constexpr int kMaxChunk4 = 4096;    // uint4 per plane per chunk (64 KiB per plane)
+constexpr int kMaxChunk4 = 2048;    // uint4 per plane per chunk = 2 per thread
 
-struct Smem {
-    uint4* pat;        // [2][chunk4]
-    double* key;       // [kCap]
-    int64_t* idx;      // [kCap]
-    uint64_t* pay;     // [kCap]
-    uint32_t* icnt;    // [kGroup][2]
-    int* misc;         // [0] = appended count, [1] = is-last flag
-};
-
-__device__ __forceinline__ Smem carve(unsigned char* raw, int chunk4)
-{
-    Smem s;
-    s.pat = reinterpret_cast<uint4*>(raw);
-    unsigned char* p = raw + (size_t)2 * chunk4 * sizeof(uint4);
-    s.key = reinterpret_cast<double*>(p);
-    p += kCap * sizeof(double);
-    s.idx = reinterpret_cast<int64_t*>(p);
-    p += kCap * sizeof(int64_t);
-    s.pay = reinterpret_cast<uint64_t*>(p);
-    p += kCap * sizeof(uint64_t);
-    s.icnt = reinterpret_cast<uint32_t*>(p);
-    p += kGroup * 2 * sizeof(uint32_t);
-    s.misc = reinterpret_cast<int*>(p);
-    return s;
-}
-
-__device__ __forceinline__ void topk_reset(Smem& s, int from)
-{
-    for (int i = from + threadIdx.x; i < kCap; i += blockDim.x) {
-        s.key[i] = kSentinelScore;
-        s.idx[i] = kSentinelIndex;
-        s.pay[i] = 0;
-    }
-}
-
-// Append a candidate if it beats the current k-th best.  The k-th best does
-// not change between flushes, so every thread may read it.
-__device__ __forceinline__ void topk_offer(Smem& s, int k, double score, int64_t index,
-                                           uint64_t payload)
-{
-    if (better(score, index, s.key[k - 1], s.idx[k - 1])) {
-        const int pos = k + atomicAdd(&s.misc[0], 1);
-        s.key[pos] = score;
-        s.idx[pos] = index;
-        s.pay[pos] = payload;
-    }
-}
-
-// Merge the appended candidates into the running top-k (slots [0, k)).
-__device__ __forceinline__ void topk_flush(Smem& s, int k)
-{
-    __syncthreads();
-    const int added = s.misc[0];
-    if (added > 0) {
-        const int n2 = next_pow2(k + added);
-        bitonic_sort_best_first(s.key, s.idx, s.pay, n2);   // ends with __syncthreads
-        for (int i = k + threadIdx.x; i < n2; i += blockDim.x) {
-            s.key[i] = kSentinelScore;
-            s.idx[i] = kSentinelIndex;
-            s.pay[i] = 0;
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) s.misc[0] = 0;
-    __syncthreads();
-}
-
+// Thread t always handles the 16-byte words t + u*kThreads (u < U) of the
+// current chunk of both planes, so it keeps the patient's words for those
+// positions in registers for the whole chunk and streams the database words
+// of EPI entries at a time against them.
 template <int U, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 scan_packed_kernel(const ScanPackedArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    Smem s = carve(smem_raw, a.chunk4);
+    TopK tk;
+    uint32_t* icnt = reinterpret_cast<uint32_t*>(topk_carve(tk, smem_raw));   // [kGroup][2]
     const int tid = threadIdx.x;
     const int lane = tid & 31;
     const int k = a.k;
+    const bool want_topk = a.hits != nullptr;
     const int64_t e_begin = (int64_t)blockIdx.x * a.n / gridDim.x;
     const int64_t e_end = ((int64_t)blockIdx.x + 1) * a.n / gridDim.x;
     const uint32_t P1 = a.pcount[0];
     const uint32_t P2 = a.pcount[1];
     const uint2* ecount2 = reinterpret_cast<const uint2*>(a.ecount);
 
-    topk_reset(s, 0);
-    if (tid == 0) s.misc[0] = 0;
-    int loaded_chunk = -1;
+    topk_init(tk);
 
     for (int64_t g0 = e_begin; g0 < e_end; g0 += kGroup) {
         const int gn = (int)((e_end - g0) < kGroup ? (e_end - g0) : kGroup);
-        for (int i = tid; i < 2 * kGroup; i += kThreads) s.icnt[i] = 0u;
+        for (int i = tid; i < 2 * kGroup; i += kThreads) icnt[i] = 0u;
+        __syncthreads();
         for (int c = 0; c < a.nchunks; ++c) {
             const int c0 = c * a.chunk4;
             const int clen = (a.wp4 - c0) < a.chunk4 ? (a.wp4 - c0) : a.chunk4;
-            if (loaded_chunk != c) {
-                __syncthreads();   // nobody still reads the previous chunk
-                for (int j = tid; j < clen; j += kThreads) {
-                    s.pat[j] = a.patient[c0 + j];
-                    s.pat[a.chunk4 + j] = a.patient[a.wp4 + c0 + j];
-                }
-                loaded_chunk = c;
+            uint4 pa[U], pb[U];   // the patient's words at this thread's positions
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int j = tid + u * kThreads;
+                pa[u] = (j < clen) ? a.patient[c0 + j] : make_uint4(0, 0, 0, 0);
+                pb[u] = (j < clen) ? a.patient[a.wp4 + c0 + j] : make_uint4(0, 0, 0, 0);
             }
-            __syncthreads();
             for (int i0 = 0; i0 < gn; i0 += EPI) {
                 uint4 x[EPI][U], y[EPI][U];
 #pragma unroll
@@ -156,17 +94,14 @@ scan_packed_kernel(const ScanPackedArgs a)
                     uint32_t a1 = 0, a2 = 0;
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const int j = tid + u * kThreads;
-                        if (j < clen) {
-                            a1 += popc_and4(x[q][u], s.pat[j]);
-                            a2 += popc_and4(y[q][u], s.pat[a.chunk4 + j]);
-                        }
+                        a1 += popc_and4(x[q][u], pa[u]);
+                        a2 += popc_and4(y[q][u], pb[u]);
                     }
                     a1 = __reduce_add_sync(0xffffffffu, a1);
                     a2 = __reduce_add_sync(0xffffffffu, a2);
                     if (lane == 0 && (i0 + q) < gn) {
-                        if (a1) atomicAdd(&s.icnt[2 * (i0 + q)], a1);
-                        if (a2) atomicAdd(&s.icnt[2 * (i0 + q) + 1], a2);
+                        if (a1) atomicAdd(&icnt[2 * (i0 + q)], a1);
+                        if (a2) atomicAdd(&icnt[2 * (i0 + q) + 1], a2);
                     }
                 }
             }
@@ -174,69 +109,30 @@ scan_packed_kernel(const ScanPackedArgs a)
         __syncthreads();   // the group's counters are complete
         for (int i = tid; i < gn; i += kThreads) {
             const int64_t e = g0 + i;
-            const uint32_t I1 = s.icnt[2 * i];
-            const uint32_t I2 = s.icnt[2 * i + 1];
+            const uint32_t I1 = icnt[2 * i];
+            const uint32_t I2 = icnt[2 * i + 1];
             const uint2 E = ecount2[e];
-            if (a.counts_out) {
+            if (a.counts_out)
                 reinterpret_cast<uint4*>(a.counts_out)[e] = make_uint4(I1, I2, E.x, E.y);
-            }
-            if (a.hits) {
-                const double sc = score_rn(I1, I2, E.x, E.y, P1, P2);
-                topk_offer(s, k, sc, e, (uint64_t)I1 | ((uint64_t)I2 << 32));
-            }
+            if (want_topk)
+                topk_offer(tk, k, score_rn(I1, I2, E.x, E.y, P1, P2), e,
+                           (uint64_t)I1 | ((uint64_t)I2 << 32),
+                           (uint64_t)E.x | ((uint64_t)E.y << 32));
         }
-        if (a.hits) topk_flush(s, k);
+        if (want_topk) topk_flush(tk, k);
         else __syncthreads();
     }
-    if (!a.hits) return;
-
-    // ---- publish this CTA's list; the last CTA merges all of them
-    Cand* mine = a.cand + (int64_t)blockIdx.x * k;
-    for (int j = tid; j < k; j += kThreads) {
-        Cand c;
-        c.score = s.key[j];
-        c.index = s.idx[j];
-        c.payload = s.pay[j];
-        mine[j] = c;
-    }
-    __threadfence();
-    __syncthreads();
-    if (tid == 0) {
-        // wraps to 0 when the last CTA arrives, ready for the next launch
-        const unsigned int done = atomicInc(a.ticket, gridDim.x - 1);
-        s.misc[1] = (done == gridDim.x - 1) ? 1 : 0;
-    }
-    __syncthreads();
-    if (!s.misc[1]) return;
-    __threadfence();
-
-    topk_reset(s, 0);
-    __syncthreads();
-    const int64_t m = (int64_t)gridDim.x * k;
-    const int round = kCap - k;
-    for (int64_t r0 = 0; r0 < m; r0 += round) {
-        for (int j = tid; j < round; j += kThreads) {
-            const int64_t r = r0 + j;
-            if (r < m) {
-                const Cand* src = a.cand + r;
-                const double sc = __ldcg(&src->score);
-                const long long ix = __ldcg(reinterpret_cast<const long long*>(&src->index));
-                const unsigned long long py =
-                    __ldcg(reinterpret_cast<const unsigned long long*>(&src->payload));
-                if (ix != kSentinelIndex) topk_offer(s, k, sc, (int64_t)ix, (uint64_t)py);
-            }
-        }
-        topk_flush(s, k);
-    }
+    if (!want_topk) return;
+    if (!topk_publish(tk, k, a.cand, a.ticket)) return;
+    topk_merge_published(tk, k, a.cand, (int64_t)gridDim.x * k);
     for (int j = tid; j < k; j += kThreads) {
         Hit h;
-        h.index = s.idx[j];
-        h.score = s.key[j];
-        h.i1 = (uint32_t)(s.pay[j] & 0xffffffffu);
-        h.i2 = (uint32_t)(s.pay[j] >> 32);
-        const uint2 E = (h.index >= 0 && h.index < a.n) ? ecount2[h.index] : make_uint2(0, 0);
-        h.e1 = E.x;
-        h.e2 = E.y;
+        h.index = tk.idx[j];
+        h.score = tk.key[j];
+        h.i1 = (uint32_t)(tk.pay0[j] & 0xffffffffu);
+        h.i2 = (uint32_t)(tk.pay0[j] >> 32);
+        h.e1 = (uint32_t)(tk.pay1[j] & 0xffffffffu);
+        h.e2 = (uint32_t)(tk.pay1[j] >> 32);
         h.p1 = P1;
         h.p2 = P2;
         a.hits[j] = h;
@@ -247,8 +143,8 @@ scan_packed_kernel(const ScanPackedArgs a)
 
 size_t scan_packed_smem(int chunk4)
 {
-    return (size_t)2 * chunk4 * sizeof(uint4) + (size_t)kCap * (8 + 8 + 8) +
-           (size_t)kGroup * 2 * sizeof(uint32_t) + 4 * sizeof(int);
+    (void)chunk4;   // the patient lives in registers
+    return topk_smem_bytes() + (size_t)kGroup * 2 * sizeof(uint32_t);
 }
 
 void scan_packed_chunking(int wp4, int* chunk4, int* nchunks)
@@ -281,8 +177,7 @@ cudaError_t launch_scan_packed(const ScanPackedArgs& a, int grid, cudaStream_t s
         return cudaGetLastError();
     };
     if (a.chunk4 <= kThreads) return run(scan_packed_kernel<1, 4>);
-    if (a.chunk4 <= 2 * kThreads) return run(scan_packed_kernel<2, 2>);
-    return run(scan_packed_kernel<4, 1>);
+    return run(scan_packed_kernel<2, 2>);
 }
 
 }  // namespace dbq

@@ -1,0 +1,170 @@
+// topk.cuh -- block-level running top-k and the cross-CTA merge used by the
+// fused query kernels.
+//
+// The best match of Section 2.3 (Ezhov et al. 2022) is the entry with the
+// largest combined Dice; the top-k generalises it.  Order: score
+// descending, then database index ascending, so the result is independent of
+// CTA scheduling.  Candidates carry two 64-bit payload words (the entry's
+// counts) so the final hits need no second pass over the database.
+//
+// Shared-memory protocol (all threads of the block take part in every call):
+//   * slots [0, k) hold the running top-k, best first, padded with sentinels;
+//   * topk_offer() appends a candidate at k + (atomic counter) when it beats
+//     the current k-th best -- at most kTopkCap - k offers between flushes;
+//   * topk_flush() bitonic-sorts the k + appended slots and keeps the first k.
+// After the scan each CTA publishes its k slots to global scratch and the
+// last CTA to arrive (atomicInc ticket that wraps to zero, no spinning)
+// merges all of them with the same offer/flush rounds.
+#pragma once
+
+#include "common.cuh"
+
+namespace dbq {
+
+constexpr int kTopkCap = 2048;
+
+struct TopK {
+    double* key;      // [kTopkCap]
+    int64_t* idx;     // [kTopkCap]
+    uint64_t* pay0;   // [kTopkCap]
+    uint64_t* pay1;   // [kTopkCap]
+    int* misc;        // [0] appended count, [1] is-last flag
+};
+
+constexpr size_t topk_smem_bytes() { return (size_t)kTopkCap * 32 + 4 * sizeof(int); }
+
+// Carve a TopK from `p` (8-byte aligned); returns the first byte after it.
+__device__ __forceinline__ unsigned char* topk_carve(TopK& t, unsigned char* p)
+{
+    t.key = reinterpret_cast<double*>(p);
+    p += kTopkCap * sizeof(double);
+    t.idx = reinterpret_cast<int64_t*>(p);
+    p += kTopkCap * sizeof(int64_t);
+    t.pay0 = reinterpret_cast<uint64_t*>(p);
+    p += kTopkCap * sizeof(uint64_t);
+    t.pay1 = reinterpret_cast<uint64_t*>(p);
+    p += kTopkCap * sizeof(uint64_t);
+    t.misc = reinterpret_cast<int*>(p);
+    p += 4 * sizeof(int);
+    return p;
+}
+
+__device__ __forceinline__ void topk_clear_slot(TopK& t, int i)
+{
+    t.key[i] = kSentinelScore;
+    t.idx[i] = kSentinelIndex;
+    t.pay0[i] = 0;
+    t.pay1[i] = 0;
+}
+
+// Sentinels everywhere; call before first use.  Ends with a barrier.
+__device__ __forceinline__ void topk_init(TopK& t)
+{
+    for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
+    if (threadIdx.x == 0) t.misc[0] = 0;
+    __syncthreads();
+}
+
+__device__ __forceinline__ void topk_offer(TopK& t, int k, double score, int64_t index,
+                                           uint64_t p0, uint64_t p1)
+{
+    if (better(score, index, t.key[k - 1], t.idx[k - 1])) {
+        const int pos = k + atomicAdd(&t.misc[0], 1);
+        t.key[pos] = score;
+        t.idx[pos] = index;
+        t.pay0[pos] = p0;
+        t.pay1[pos] = p1;
+    }
+}
+
+__device__ __forceinline__ void bitonic_sort_topk(TopK& t, int n)
+{
+    for (int size = 2; size <= n; size <<= 1) {
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            for (int i = threadIdx.x; i < (n >> 1); i += blockDim.x) {
+                const int lo = 2 * i - (i & (stride - 1));
+                const int hi = lo + stride;
+                const bool up = (lo & size) == 0;
+                const bool hi_better = better(t.key[hi], t.idx[hi], t.key[lo], t.idx[lo]);
+                if (hi_better == up) {
+                    const double kk = t.key[lo]; t.key[lo] = t.key[hi]; t.key[hi] = kk;
+                    const int64_t ii = t.idx[lo]; t.idx[lo] = t.idx[hi]; t.idx[hi] = ii;
+                    const uint64_t a = t.pay0[lo]; t.pay0[lo] = t.pay0[hi]; t.pay0[hi] = a;
+                    const uint64_t b = t.pay1[lo]; t.pay1[lo] = t.pay1[hi]; t.pay1[hi] = b;
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Merge the appended candidates into slots [0, k).  Starts and ends with a
+// barrier.
+__device__ __forceinline__ void topk_flush(TopK& t, int k)
+{
+    __syncthreads();
+    const int added = t.misc[0];
+    if (added > 0) {
+        const int n2 = next_pow2(k + added);
+        bitonic_sort_topk(t, n2);
+        for (int i = k + threadIdx.x; i < n2; i += blockDim.x) topk_clear_slot(t, i);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) t.misc[0] = 0;
+    __syncthreads();
+}
+
+// Publish this CTA's k slots to cand[blockIdx.x * k ...] and take a ticket.
+// Returns true (in every thread) in the last CTA to arrive, which then sees
+// every CTA's list.
+__device__ __forceinline__ bool topk_publish(TopK& t, int k, Cand* cand, unsigned int* ticket)
+{
+    Cand* mine = cand + (int64_t)blockIdx.x * k;
+    for (int j = threadIdx.x; j < k; j += blockDim.x) {
+        Cand c;
+        c.score = t.key[j];
+        c.index = t.idx[j];
+        c.pay0 = t.pay0[j];
+        c.pay1 = t.pay1[j];
+        mine[j] = c;
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned int done = atomicInc(ticket, gridDim.x - 1);   // wraps to 0 at the end
+        t.misc[1] = (done == gridDim.x - 1) ? 1 : 0;
+    }
+    __syncthreads();
+    const bool last = t.misc[1] != 0;
+    if (last) __threadfence();
+    return last;
+}
+
+// In the last CTA: merge the m published candidates into slots [0, k).
+__device__ __forceinline__ void topk_merge_published(TopK& t, int k, const Cand* cand, int64_t m)
+{
+    for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
+    if (threadIdx.x == 0) t.misc[0] = 0;
+    __syncthreads();
+    const int round = kTopkCap - k;
+    for (int64_t r0 = 0; r0 < m; r0 += round) {
+        for (int j = threadIdx.x; j < round; j += blockDim.x) {
+            const int64_t r = r0 + j;
+            if (r < m) {
+                const Cand* src = cand + r;
+                const double sc = __ldcg(&src->score);
+                const long long ix = __ldcg(reinterpret_cast<const long long*>(&src->index));
+                if (ix != kSentinelIndex) {
+                    const unsigned long long p0 =
+                        __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay0));
+                    const unsigned long long p1 =
+                        __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay1));
+                    topk_offer(t, k, sc, (int64_t)ix, (uint64_t)p0, (uint64_t)p1);
+                }
+            }
+        }
+        topk_flush(t, k);
+    }
+}
+
+}  // namespace dbq
