@@ -46,6 +46,19 @@ WORKLOADS = {
                                desc="1,024 x 64^3 bit-packed, t=(0.6,0.25), top-10"),
 }
 DEFAULT_WORKLOAD = "exact_packed_50k_128"
+# DRAM traffic of the dominant kernel from one `ncu --set full` capture of a
+# small case (summaries in profiles/), per entry read plus fixed writes; valid
+# only while the kernel's sources hash to the captured version.
+TRAFFIC = {
+    "scan_packed_kernel": dict(files=("scan_packed.cu", "topk.cuh", "common.cuh"),
+                               sha="7327dbf9102ae100", entries=2000,
+                               read_bytes=1049188352, write_bytes=3352320,
+                               capture="profiles/scan_packed_2k_128_ncu_full.md"),
+    "scan_f16_kernel": dict(files=("scan_f16.cu", "topk.cuh", "common.cuh"),
+                            sha="0d144eaf8bf7f42c", entries=4000,
+                            read_bytes=2097310464, write_bytes=3112192,
+                            capture="profiles/scan_f16_4k_64_ncu_full.md"),
+}
 METRIC = "DB entries/s per query (HBM GB/s vs peak); batched queries/s at top-1 match"
 FALLBACK_HBM_GBS = 6800.0
 
@@ -53,6 +66,22 @@ FALLBACK_HBM_GBS = 6800.0
 def _dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def _traffic(kernel: str, n_entries: int):
+    """Scaled DRAM bytes per launch, or None if the kernel changed since the
+    capture."""
+    import hashlib
+    t = TRAFFIC.get(kernel)
+    if t is None:
+        return None
+    h = hashlib.sha256()
+    for f in t["files"]:
+        with open(os.path.join(ROOT, "paper_2205_04550_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest()[:16] != t["sha"]:
+        return None
+    return t["read_bytes"] / t["entries"] * n_entries + t["write_bytes"]
 
 
 def _peaks():
@@ -372,6 +401,8 @@ def main(argv=None):
 
     peak, peak_kind = _peaks()
     alg = algorithmic_bytes(wl)
+    kname = "scan_f16_kernel" if f16 else "scan_packed_kernel"
+    traffic = _traffic(kname, n_entries)
     achieved = alg / scan_s / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": "entries/s", "n_gpus": world,
@@ -388,10 +419,11 @@ def main(argv=None):
         "e2e": {"value": e2e_value, "unit": "entries/s",
                 "h2d_bytes_per_step": int(pats[0].nbytes), "d2h_bytes_per_step": k * 40},
         "gpu_launches": 2 * args.steps,   # per step: patient pack + fused scan
-        "roofline": {"bound": "hbm", "kernel": "scan_f16_kernel" if f16 else "scan_packed_kernel",
-                     "achieved": achieved,
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": achieved,
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": traffic,
+                     "traffic_note": "ncu DRAM read+write of a small capture scaled per entry"
+                     if traffic else "kernel changed since the last capture",
                      "algorithmic_bytes_per_launch": alg,
                      "kernel_ms": scan_s * 1000.0},
         "clocks": clk,
