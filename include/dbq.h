@@ -190,6 +190,31 @@ int db_get_masks(dbq_db* db, int64_t first, int64_t count, uint32_t* planes,
  */
 int db_info(const dbq_db* db, int64_t out[8]);
 
+/*
+ * db_scan_packed_noalloc -- the bit-packed exact query for callers that
+ * cannot allocate device memory (a memory pool that owns the whole GPU, a
+ * request path that must not synchronise on an allocation, a plug-in host
+ * that forbids device allocations).  The paper has no counterpart: it is an
+ * interface variant of db_query_prepared, not a step of the method.
+ *   planes          device [n][2][stride_words] bit planes (layout above;
+ *                   bits past the last voxel 0), 16-byte aligned.
+ *   sizes           device [n][2] mask sizes |E_1|, |E_2|, 8-byte aligned.
+ *   stride_words    words per plane in `planes` and `patient_planes`; a
+ *                   multiple of 4 that covers ceil(V/32).
+ *   patient_planes  device [2][stride_words] patient planes, 16-byte aligned.
+ *   patient_sizes   device [2] |P_1|, |P_2|.
+ *   k               1 <= k <= min(n, 64); DBQ_ERANGE otherwise.
+ *   hits            device [k] output, 8-byte aligned.
+ * Only enqueues work on `stream`; allocates nothing.  Its scratch is one
+ * fixed array of 512.25 KiB in device memory that every GPU loading the
+ * library keeps until exit, shared by all calls: calls that overlap on the
+ * GPU race.  The first call on a device caches the array's address; make it
+ * before any stream capture.  Devices with more than 256 SMs are rejected.
+ */
+int db_scan_packed_noalloc(const uint32_t* planes, const uint32_t* sizes, int64_t n,
+                           int64_t stride_words, const uint32_t* patient_planes,
+                           const uint32_t* patient_sizes, int k, dbq_hit* hits, void* stream);
+
 /* db_destroy -- free everything the handle owns.  NULL is accepted. */
 int db_destroy(dbq_db* db);
 

@@ -75,6 +75,8 @@ _SIGS = [
                                       _P, _P]),
     ("db_get_masks", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P]),
     ("db_info", ctypes.c_int, [_P, _P]),
+    ("db_scan_packed_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
+                                              ctypes.c_int, _P, _P]),
     ("db_destroy", ctypes.c_int, [_P]),
     ("db_last_error", ctypes.c_char_p, []),
 ]
@@ -220,6 +222,15 @@ def db_info(db: int) -> dict:
     _check(load().db_info(db, out.ctypes.data))
     keys = ("n", "v", "words", "padded_words", "storage", "built", "n_params", "device_bytes")
     return dict(zip(keys, (int(x) for x in out)))
+
+
+def db_scan_packed_noalloc(planes, sizes, n: int, stride_words: int, patient_planes,
+                           patient_sizes, k: int, hits_dev, stream=None):
+    """Allocation-free exact query over caller-owned device buffers (see
+    include/dbq.h); only enqueues work."""
+    _check(load().db_scan_packed_noalloc(_ptr(planes), _ptr(sizes), n, stride_words,
+                                         _ptr(patient_planes), _ptr(patient_sizes), k,
+                                         _ptr(hits_dev), _stream(stream)))
 
 
 def db_destroy(db: int):

@@ -76,6 +76,8 @@ constexpr size_t kStageBytes = size_t(256) << 20;   // host-input staging chunk
 
 }  // namespace
 
+int dbq::record_error(int code, const char* msg) { return fail(code, "%s", msg); }
+
 struct dbq_db {
     std::mutex mu;
     int device = 0;

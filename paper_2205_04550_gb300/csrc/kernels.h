@@ -77,4 +77,7 @@ cudaError_t launch_scan_f16(const ScanF16Args& a, int grid, cudaStream_t stream)
 cudaError_t launch_rows_to_f16(const void* src, int src_f16, int64_t count, int64_t v,
                                int64_t pitch, uint16_t* dst, cudaStream_t stream);
 
+// Set the calling thread's db_last_error() message; returns `code`.
+int record_error(int code, const char* msg);
+
 }  // namespace dbq
