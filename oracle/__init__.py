@@ -86,6 +86,16 @@ def _load():
         lib.oracle_downsample_nn_u8.argtypes = [P, i32, i32, i32, i32, P]
         lib.oracle_downsample_nn_u8.restype = i32
         lib.oracle_num_threads.restype = i32
+        lib.oracle_bf16_bits.argtypes = [f32]
+        lib.oracle_bf16_bits.restype = ctypes.c_uint16
+        lib.oracle_bf16_value.argtypes = [ctypes.c_uint16]
+        lib.oracle_bf16_value.restype = f64
+        lib.oracle_e4m3_value.argtypes = [ctypes.c_uint8]
+        lib.oracle_e4m3_value.restype = f64
+        lib.oracle_e4m3_code.argtypes = [f64]
+        lib.oracle_e4m3_code.restype = ctypes.c_uint8
+        lib.oracle_embed.argtypes = [P, i32, i32, i32, i32, P, P, P]
+        lib.oracle_embed.restype = i32
         _lib = lib
         return lib
 
@@ -235,6 +245,47 @@ def block_mean(mask: np.ndarray, nx: int, ny: int, nz: int, f: int) -> np.ndarra
     if lib.oracle_block_mean(_p(m), nx, ny, nz, f, _p(out)) != 0:
         raise ValueError("grid not divisible by block size")
     return out
+
+
+def bf16_bits(x: float) -> int:
+    return _load().oracle_bf16_bits(np.float32(x))
+
+
+def bf16_value(h: int) -> float:
+    return _load().oracle_bf16_value(int(h) & 0xFFFF)
+
+
+def e4m3_value(c: int) -> float:
+    return _load().oracle_e4m3_value(int(c) & 0xFF)
+
+
+def e4m3_code(x: float) -> int:
+    return _load().oracle_e4m3_code(float(x))
+
+
+def embed(mask: np.ndarray, nx: int, ny: int, nz: int, f: int = 8):
+    """Prefilter embedding of one byte mask [V]: (bf16 bits [d] uint16,
+    e4m3 codes [d] uint8, scale float32)."""
+    lib = _load()
+    m = _c(mask.reshape(-1), np.uint8)
+    d = (nx // f) * (ny // f) * (nz // f)
+    b = np.empty(d, dtype=np.uint16)
+    q = np.empty(d, dtype=np.uint8)
+    sc = np.empty(1, dtype=np.float32)
+    if lib.oracle_embed(_p(m), nx, ny, nz, f, _p(b), _p(q), _p(sc)) != d:
+        raise ValueError("grid not divisible by block size")
+    return b, q, np.float32(sc[0])
+
+
+def bf16_to_f64(bits: np.ndarray) -> np.ndarray:
+    lib = _load()
+    return np.array([lib.oracle_bf16_value(int(h)) for h in np.asarray(bits).reshape(-1)])
+
+
+def e4m3_to_f64(codes: np.ndarray) -> np.ndarray:
+    lib = _load()
+    table = np.array([lib.oracle_e4m3_value(c) for c in range(256)])
+    return table[np.asarray(codes, dtype=np.uint8)]
 
 
 def l2(a: np.ndarray, b: np.ndarray) -> float:

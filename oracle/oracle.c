@@ -37,6 +37,14 @@
  * of each binary mask and the Euclidean distance between those block means,
  * computed in binary64.
  *
+ * The prefilter's stored encodings are written out from their formats:
+ * bfloat16 is binary32 rounded to nearest-even at bit 16; FP8 E4M3 (bias 7,
+ * 3 fraction bits, largest finite 448, no infinity) is round-to-nearest-even
+ * with saturation at +-448, applied to e / s with the per-row scale
+ * s = max(e) / 448 computed in binary32 (s = 1 for an all-zero row).  The
+ * decisions that produce those codes are taken in binary32, as the kernels
+ * take them.
+ *
  * The nearest-neighbour downsampling of Section 2.3 (an order-0 spline
  * resampling to 64^3 or 32^3) is out[i] = in[f*i] along each axis.
  *
@@ -293,6 +301,87 @@ int oracle_block_mean(const uint8_t* mask, int nx, int ny, int nz, int f, double
                 out[bx + bx_n * (by + by_n * bz)] = (double)count / ((double)f * f * f);
             }
     return 0;
+}
+
+/* bfloat16 encoding of a binary32 value: round to nearest-even at bit 16.
+   Returns the bit pattern; NaN/Inf are not produced by the callers. */
+uint16_t oracle_bf16_bits(float x)
+{
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    uint32_t lsb = (b >> 16) & 1u;
+    b += 0x7FFFu + lsb;
+    return (uint16_t)(b >> 16);
+}
+
+double oracle_bf16_value(uint16_t h)
+{
+    uint32_t b = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
+/* FP8 E4M3 value of code c (sign, 4-bit exponent with bias 7, 3-bit fraction;
+   exponent 15 with fraction 7 is NaN). */
+double oracle_e4m3_value(uint8_t c)
+{
+    int sign = (c >> 7) & 1;
+    int expo = (c >> 3) & 0xF;
+    int frac = c & 0x7;
+    double mag;
+    if (expo == 15 && frac == 7) return NAN;
+    if (expo == 0) mag = ldexp((double)frac, -9);             /* frac/8 * 2^-6 */
+    else mag = ldexp((double)(8 + frac), expo - 10);          /* (1+frac/8) * 2^(expo-7) */
+    return sign ? -mag : mag;
+}
+
+/* FP8 E4M3 code nearest to x (ties to even code), saturating at +-448:
+   searched over all finite codes of x's sign -- slow and plain. */
+uint8_t oracle_e4m3_code(double x)
+{
+    int neg = signbit(x) ? 1 : 0;
+    double a = fabs(x);
+    if (a >= 448.0) return (uint8_t)((neg << 7) | 0x7E);
+    uint8_t best = 0;
+    double best_err = INFINITY;
+    for (int c = 0; c < 0x7F; ++c) {                /* 0x7F is NaN */
+        double v = oracle_e4m3_value((uint8_t)c);
+        double err = fabs(v - a);
+        if (err < best_err || (err == best_err && (c & 1) == 0)) {
+            best_err = err;
+            best = (uint8_t)c;
+        }
+    }
+    return (uint8_t)((neg << 7) | best);
+}
+
+/* Embedding of one byte mask: f^3 block counts / f^3 (exact in binary32),
+   encoded as bfloat16 and as FP8 E4M3 with the row scale s (see header).
+   out_bf16[d], out_e4m3[d], out_scale[1]; returns d or -1. */
+int oracle_embed(const uint8_t* mask, int nx, int ny, int nz, int f,
+                 uint16_t* out_bf16, uint8_t* out_e4m3, float* out_scale)
+{
+    if (f <= 0 || nx % f || ny % f || nz % f) return -1;
+    int d = (nx / f) * (ny / f) * (nz / f);
+    double* mean = (double*)malloc(sizeof(double) * (size_t)d);
+    if (!mean) return -1;
+    oracle_block_mean(mask, nx, ny, nz, f, mean);
+    float m = 0.0f;
+    for (int j = 0; j < d; ++j) {
+        float e = (float)mean[j];                   /* count / f^3, exact */
+        out_bf16[j] = oracle_bf16_bits(e);
+        if (e > m) m = e;
+    }
+    float s = (m == 0.0f) ? 1.0f : m / 448.0f;
+    for (int j = 0; j < d; ++j) {
+        float e = (float)mean[j];
+        float r = e / s;                            /* binary32, as the kernel divides */
+        out_e4m3[j] = oracle_e4m3_code((double)r);
+    }
+    *out_scale = s;
+    free(mean);
+    return d;
 }
 
 /* Euclidean distance between two vectors of length d, in binary64. */

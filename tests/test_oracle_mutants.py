@@ -26,6 +26,10 @@ MUTANTS = {
     "f16_exponent_off_by_one": ("expo - 25", "expo - 24"),
     "block_mean_transposed": ("out[bx + bx_n * (by + by_n * bz)]", "out[by + by_n * (bx + bx_n * bz)]"),
     "unpack_bit_reversed": (">> (x % 32)) & 1u", ">> (31 - x % 32)) & 1u"),
+    "bf16_rounds_half_up": ("b += 0x7FFFu + lsb;", "b += 0x8000u;"),
+    "e4m3_scale_wrong_max": ("float s = (m == 0.0f) ? 1.0f : m / 448.0f;",
+                             "float s = (m == 0.0f) ? 1.0f : m / 240.0f;"),
+    "e4m3_subnormal_exponent": ("mag = ldexp((double)frac, -9);", "mag = ldexp((double)frac, -10);"),
     "patient_flair_at_t1": ("        mask[v + x] = (uint8_t)in_mask_f32(vol[x], t2);",
                             "        mask[v + x] = (uint8_t)in_mask_f32(vol[x], t1);"),
 }
@@ -43,6 +47,7 @@ def test_pins_catch_mutant(name, tmp_path):
                     "-ffp-contract=off", str(mutated), "-o", str(lib), "-lm"], check=True)
     env = dict(os.environ, DBQ_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
-                        os.path.join(ROOT, "tests", "test_oracle_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_embed_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
