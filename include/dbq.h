@@ -76,6 +76,16 @@ enum dbq_storage {
                            database at its own (t1, t2)                      */
 };
 
+/* db_create flags. */
+#define DBQ_FLAG_EMBED 1u  /* also build the prefilter embeddings (see db_query_batch) */
+
+/* Query modes of db_query_batch. */
+enum dbq_mode {
+    DBQ_MODE_EXACT = 0,       /* the brute-force loop over every entry           */
+    DBQ_MODE_EMBED_BF16 = 1,  /* bfloat16 embedding prefilter + exact re-ranking  */
+    DBQ_MODE_EMBED_FP8 = 2    /* FP8 E4M3 embedding prefilter + exact re-ranking  */
+};
+
 /* One ranked result.  p1/p2 are the patient's mask sizes. */
 typedef struct dbq_hit {
     int64_t index;     /* database entry                                      */
@@ -97,7 +107,10 @@ typedef struct dbq_hit {
  *                built with (Section 2.3 uses 0.6 and 0.2); each must be a
  *                finite number in (0, 1].  F16 storage: ignored.
  *   n_params     doubles of theta kept per entry (0..64), returned with hits.
- *   flags        0 (reserved for later options).
+ *   flags        0, or DBQ_FLAG_EMBED: BITS storage only, nx a multiple of 32
+ *                and ny, nz multiples of 8; db_build_masks() then also builds
+ *                the prefilter embeddings (2 x (nx/8)(ny/8)(nz/8) values per
+ *                entry, bfloat16 and FP8 E4M3 with per-row scales).
  * Returns DBQ_OK and *out, or DBQ_EINVAL / DBQ_ENOMEM / DBQ_ECUDA.
  */
 int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storage,
@@ -121,8 +134,12 @@ int db_load_volumes(dbq_db* db, int64_t first, int64_t count, const void* vols, 
 /*
  * db_build_masks -- finish the build: check that every entry in
  * [0, capacity) has been loaded and make the database queryable.  The masks
- * themselves are written as volumes are loaded, so this call reads no
- * volume.  Returns DBQ_ESTATE if an entry is missing.
+ * themselves are written as volumes are loaded.  With DBQ_FLAG_EMBED this
+ * call computes each mask's embedding: the mean of every 8 x 8 x 8 block
+ * (the low-dimensional representations queried by L2 in Section 2.3),
+ * encoded as bfloat16 (round to nearest-even) and as FP8 E4M3 of e / s with
+ * s = max(e) / 448 per row (binary32), plus the rows' squared norms.
+ * Returns DBQ_ESTATE if an entry is missing.
  */
 int db_build_masks(dbq_db* db, void* stream);
 
@@ -189,6 +206,50 @@ int db_get_masks(dbq_db* db, int64_t first, int64_t count, uint32_t* planes,
  * out[5] = built (0/1), out[6] = n_params, out[7] = device bytes held.
  */
 int db_info(const dbq_db* db, int64_t out[8]);
+
+/*
+ * db_query_batch -- `nq` queries, each against the database
+ * dbs[db_of_query[q]], returning k hits per query.
+ *   patients      [nq] pointers (host or device), each a volume of `kind`
+ *                 (DBQ_F32 / DBQ_F16) or DBQ_BITS planes for its database.
+ *   t1, t2        [nq] per-query thresholds, or NULL (NaN: the build
+ *                 thresholds of a bit-packed database).
+ *   mode          DBQ_MODE_EXACT: the full loop per query (any storage).
+ *                 DBQ_MODE_EMBED_BF16 / _FP8: for databases built with
+ *                 DBQ_FLAG_EMBED, the L2 prefilter over the embeddings
+ *                 (L = L2_T1Gd + L2_FLAIR of the non-squared distances,
+ *                 Section 2.3; a tensor-core GEMM with fp32 accumulation)
+ *                 keeps the `n_candidates` closest entries per query (ties to
+ *                 the lower index), which are re-ranked by the exact Dice
+ *                 loop; the hits are exact for the entries they name.
+ *   n_candidates  1 <= k <= n_candidates <= min(N, 1024) (embedding modes).
+ *   hits          host [nq][k]; params host [nq][k][n_params] or NULL.
+ * Queries are processed in groups of up to 256 per database.  Returns after
+ * the results are in host memory.
+ */
+int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
+                   const void* const* patients, int kind, const float* t1, const float* t2,
+                   int k, int mode, int n_candidates, dbq_hit* hits, double* params,
+                   void* stream);
+
+/*
+ * db_prefilter -- the prefilter step of db_query_batch alone, for
+ * measurement and checking: distances dist [nq][N] (host or device, or
+ * NULL) and the n_candidates closest entries per query, ascending, cand
+ * [nq][n_candidates] int32 (host or device, or NULL).  nq <= 256; bit-packed
+ * databases built with DBQ_FLAG_EMBED only.
+ */
+int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int mode,
+                 int n_candidates, float* dist, int32_t* cand, void* stream);
+
+/*
+ * db_get_embeddings -- copy the embeddings of entries [first, first+count):
+ * bf16 [count][2][d] (uint16 bit patterns), e4m3 [count][2][d] codes, scale
+ * [count][2], norm_bf16 and norm_fp8 [count][2] (squared norms of the
+ * decoded rows).  Any output may be NULL; host or device memory.
+ */
+int db_get_embeddings(dbq_db* db, int64_t first, int64_t count, uint16_t* bf16, uint8_t* e4m3,
+                      float* scale, float* norm_bf16, float* norm_fp8, void* stream);
 
 /*
  * db_scan_packed_noalloc -- the bit-packed exact query for callers that

@@ -10,13 +10,17 @@ from __future__ import annotations
 import numpy as np
 
 from . import _dbq
-from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_STORE_BITS, DBQ_STORE_F16, HIT_DTYPE,
-                   DbqError, db_build_masks, db_create, db_destroy, db_get_masks, db_info,
-                   db_last_error, db_load_volumes, db_prepare_patient, db_query,
-                   db_query_async, db_query_prepared, db_scan_counts)
+from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_MODE_EMBED_BF16,
+                   DBQ_MODE_EMBED_FP8, DBQ_MODE_EXACT, DBQ_STORE_BITS, DBQ_STORE_F16, HIT_DTYPE,
+                   DbqError, db_build_masks, db_create, db_destroy, db_get_embeddings,
+                   db_get_masks, db_info, db_last_error, db_load_volumes, db_prefilter,
+                   db_prepare_patient, db_query, db_query_async, db_query_batch,
+                   db_query_prepared, db_scan_counts, db_scan_packed_noalloc)
 
 __all__ = ["Database", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_F16", "DBQ_BITS",
-           "DBQ_STORE_BITS", "DBQ_STORE_F16", "db_create", "db_load_volumes",
+           "DBQ_STORE_BITS", "DBQ_STORE_F16", "DBQ_FLAG_EMBED", "DBQ_MODE_EXACT",
+           "DBQ_MODE_EMBED_BF16", "DBQ_MODE_EMBED_FP8", "db_query_batch", "db_prefilter",
+           "db_get_embeddings", "db_scan_packed_noalloc", "db_create", "db_load_volumes",
            "db_build_masks", "db_query", "db_query_async", "db_prepare_patient",
            "db_query_prepared", "db_scan_counts", "db_get_masks",
            "db_info", "db_destroy", "db_last_error"]
@@ -26,14 +30,16 @@ class Database:
     """Owns one libdbq handle; methods map one-to-one onto the C calls."""
 
     def __init__(self, shape, capacity: int, storage: int = DBQ_STORE_BITS,
-                 t1: float = 0.6, t2: float = 0.25, n_params: int = 0):
+                 t1: float = 0.6, t2: float = 0.25, n_params: int = 0, embed: bool = False):
         nx, ny, nz = shape
         self.shape = (int(nx), int(ny), int(nz))
         self.capacity = int(capacity)
         self.storage = storage
         self.t1, self.t2 = float(np.float32(t1)), float(np.float32(t2))
         self.n_params = int(n_params)
-        self.handle = db_create(nx, ny, nz, capacity, storage, t1, t2, n_params)
+        self.embed = bool(embed)
+        self.handle = db_create(nx, ny, nz, capacity, storage, t1, t2, n_params,
+                                DBQ_FLAG_EMBED if embed else 0)
 
     def load(self, first: int, vols, params=None, stream=None):
         db_load_volumes(self.handle, first, int(vols.shape[0]), vols, params=params,
@@ -61,6 +67,31 @@ class Database:
         sizes = np.zeros((count, 2), dtype=np.uint32)
         db_get_masks(self.handle, first, count, planes, sizes)
         return planes, sizes
+
+    def embeddings(self, first: int, count: int):
+        """-> dict of bf16 bits [count,2,d] uint16, e4m3 codes [count,2,d] uint8,
+        scale, norm_bf16, norm_fp8 [count,2] float32."""
+        nx, ny, nz = self.shape
+        d = (nx // 8) * (ny // 8) * (nz // 8)
+        out = dict(bf16=np.zeros((count, 2, d), np.uint16), e4m3=np.zeros((count, 2, d), np.uint8),
+                   scale=np.zeros((count, 2), np.float32),
+                   norm_bf16=np.zeros((count, 2), np.float32),
+                   norm_fp8=np.zeros((count, 2), np.float32))
+        db_get_embeddings(self.handle, first, count, **out)
+        return out
+
+    def prefilter(self, patients, mode: int, n_candidates: int = 0, kind=None):
+        """-> (dist [nq, N] float32, cand [nq, n_candidates] int32 or None)."""
+        nq = len(patients)
+        dist = np.zeros((nq, self.capacity), np.float32)
+        cand = np.zeros((nq, n_candidates), np.int32) if n_candidates else None
+        db_prefilter(self.handle, patients, mode, n_candidates, dist, cand, kind)
+        return dist, cand
+
+    def query_batch(self, patients, k: int, mode: int = DBQ_MODE_EXACT, n_candidates: int = 0,
+                    t1=None, t2=None, kind=None):
+        return db_query_batch([self.handle], [0] * len(patients), patients, k, mode,
+                              n_candidates, t1, t2, kind, self.n_params)
 
     def info(self) -> dict:
         return db_info(self.handle)

@@ -31,6 +31,12 @@ DBQ_BITS = 2
 DBQ_STORE_BITS = 0
 DBQ_STORE_F16 = 1
 
+DBQ_FLAG_EMBED = 1
+
+DBQ_MODE_EXACT = 0
+DBQ_MODE_EMBED_BF16 = 1
+DBQ_MODE_EMBED_FP8 = 2
+
 STATUS_NAMES = {0: "DBQ_OK", -1: "DBQ_EINVAL", -2: "DBQ_ENOMEM", -3: "DBQ_ESTATE",
                 -4: "DBQ_ECUDA", -5: "DBQ_ETIMEOUT", -6: "DBQ_ERANGE"}
 
@@ -75,6 +81,12 @@ _SIGS = [
                                       _P, _P]),
     ("db_get_masks", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P]),
     ("db_info", ctypes.c_int, [_P, _P]),
+    ("db_query_batch", ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P, _P]),
+    ("db_prefilter", ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
+                                    ctypes.c_int, _P, _P, _P]),
+    ("db_get_embeddings", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P,
+                                         _P]),
     ("db_scan_packed_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                               ctypes.c_int, _P, _P]),
     ("db_destroy", ctypes.c_int, [_P]),
@@ -222,6 +234,44 @@ def db_info(db: int) -> dict:
     _check(load().db_info(db, out.ctypes.data))
     keys = ("n", "v", "words", "padded_words", "storage", "built", "n_params", "device_bytes")
     return dict(zip(keys, (int(x) for x in out)))
+
+
+def _ptr_array(xs):
+    arr = (ctypes.c_void_p * len(xs))()
+    for i, x in enumerate(xs):
+        arr[i] = _ptr(x)
+    return arr
+
+
+def db_query_batch(dbs, db_of_query, patients, k: int, mode: int = DBQ_MODE_EXACT,
+                   n_candidates: int = 0, t1=None, t2=None, kind: int | None = None,
+                   n_params: int = 0, stream=None):
+    """-> (hits [nq, k] HIT_DTYPE, params [nq, k, n_params] or None)."""
+    nq = len(patients)
+    hits = np.zeros((nq, k), dtype=HIT_DTYPE)
+    params = np.zeros((nq, k, n_params), dtype=np.float64) if n_params else None
+    dba = (ctypes.c_void_p * len(dbs))(*dbs)
+    dq = np.ascontiguousarray(db_of_query, dtype=np.int32)
+    a1 = None if t1 is None else np.ascontiguousarray(t1, dtype=np.float32)
+    a2 = None if t2 is None else np.ascontiguousarray(t2, dtype=np.float32)
+    _check(load().db_query_batch(dba, dq.ctypes.data, nq, _ptr_array(patients),
+                                 _kind_of(patients[0]) if kind is None else kind,
+                                 _ptr(a1), _ptr(a2), k, mode, n_candidates,
+                                 hits.ctypes.data, _ptr(params), _stream(stream)))
+    return hits, params
+
+
+def db_prefilter(db: int, patients, mode: int, n_candidates: int = 0, dist=None, cand=None,
+                 kind: int | None = None, stream=None):
+    _check(load().db_prefilter(db, len(patients), _ptr_array(patients),
+                               _kind_of(patients[0]) if kind is None else kind, mode,
+                               n_candidates, _ptr(dist), _ptr(cand), _stream(stream)))
+
+
+def db_get_embeddings(db: int, first: int, count: int, bf16=None, e4m3=None, scale=None,
+                      norm_bf16=None, norm_fp8=None, stream=None):
+    _check(load().db_get_embeddings(db, first, count, _ptr(bf16), _ptr(e4m3), _ptr(scale),
+                                    _ptr(norm_bf16), _ptr(norm_fp8), _stream(stream)))
 
 
 def db_scan_packed_noalloc(planes, sizes, n: int, stride_words: int, patient_planes,

@@ -4,6 +4,7 @@
 // query workspace, staging of host inputs, and the launches of the kernels
 // in pack.cu and scan_packed.cu (and, for half-precision storage,
 // scan_f16.cu).  Every step of a query runs in those kernels.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -109,6 +110,33 @@ struct dbq_db {
     dbq::Hit* hits_dev = nullptr;   // [kMaxK]
     dbq::Hit* hits_host = nullptr;  // pinned [kMaxK]
     uint32_t* counts_dev = nullptr; // [n][4], allocated on first db_scan_counts
+    // prefilter embeddings (DBQ_FLAG_EMBED)
+    int dims = 0;                   // per segmentation
+    uint16_t* emb_bf16 = nullptr;   // [n][2][dims]
+    uint8_t* emb_f8 = nullptr;      // [n][2][dims]
+    float* emb_scale = nullptr;     // [n][2]
+    float* emb_nb = nullptr;        // [n][2] squared norms, bf16 rows
+    float* emb_nf = nullptr;        // [n][2] squared norms, fp8 rows
+    // batch workspace (allocated on first use)
+    int bq = 0;                     // capacity in queries
+    int bk = 0;                     // capacity in hits per query
+    void* bstage = nullptr;         // host patients staged [bq][max bytes]
+    size_t bstage_each = 0;
+    const void** bptrs = nullptr;   // device [bq] patient pointers
+    uint32_t* bplanes = nullptr;    // [bq][2][wp]
+    uint32_t* bpcount = nullptr;    // [bq][2]
+    uint16_t* bq_bf16 = nullptr;    // [bq][2][dims]
+    uint8_t* bq_f8 = nullptr;
+    float* bq_scale = nullptr;
+    float* bq_nb = nullptr;
+    float* bq_nf = nullptr;
+    float* bdist = nullptr;         // [bq][n]
+    int32_t* bcand = nullptr;       // [bq][1024]
+    dbq::Cand* brr = nullptr;       // [bq][slices][bk]
+    unsigned int* btickets = nullptr;
+    dbq::Hit* bhits = nullptr;      // [bq][bk] device
+    dbq::Hit* bhits_host = nullptr; // pinned
+    int* bstatus = nullptr;         // device status of the tensor-core kernel
     bool prepared = false;          // a patient sits in pplanes/pcount
     float prep_t1 = 0.f, prep_t2 = 0.f;
     int grid = 1;
@@ -128,6 +156,27 @@ struct dbq_db {
         cudaFree(hits_dev);
         cudaFreeHost(hits_host);
         cudaFree(counts_dev);
+        cudaFree(emb_bf16);
+        cudaFree(emb_f8);
+        cudaFree(emb_scale);
+        cudaFree(emb_nb);
+        cudaFree(emb_nf);
+        cudaFree(bstage);
+        cudaFree(bptrs);
+        cudaFree(bplanes);
+        cudaFree(bpcount);
+        cudaFree(bq_bf16);
+        cudaFree(bq_f8);
+        cudaFree(bq_scale);
+        cudaFree(bq_nb);
+        cudaFree(bq_nf);
+        cudaFree(bdist);
+        cudaFree(bcand);
+        cudaFree(brr);
+        cudaFree(btickets);
+        cudaFree(bhits);
+        cudaFreeHost(bhits_host);
+        cudaFree(bstatus);
     }
 };
 
@@ -265,6 +314,181 @@ int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaSt
 
 }  // namespace
 
+namespace {
+
+constexpr int kBatchQ = 256;      // queries per prefilter group (tensor-core N)
+constexpr int kRerankSlices = 8;
+
+size_t patient_bytes(const dbq_db* db, int kind)
+{
+    if (kind == DBQ_BITS) return (size_t)2 * db->words * sizeof(uint32_t);
+    if (kind == DBQ_F16) return (size_t)db->v * 2;
+    return (size_t)db->v * 4;
+}
+
+template <typename T>
+int grow(dbq_db* db, T** p, size_t bytes, const char* what)
+{
+    cudaFree(*p);
+    *p = nullptr;
+    return dev_alloc(db, p, bytes, what);
+}
+
+// Batch workspace for up to kBatchQ queries and k hits each.
+int ensure_batch(dbq_db* db, int k)
+{
+    int rc = DBQ_OK;
+    if (db->bq < kBatchQ) {
+        const size_t q = kBatchQ;
+        rc = grow(db, &db->bptrs, q * sizeof(void*), "batch pointers");
+        if (!rc) rc = grow(db, &db->bplanes, q * 2 * db->wp * 4, "batch patient planes");
+        if (!rc) rc = grow(db, &db->bpcount, q * 2 * 4, "batch patient sizes");
+        if (!rc) rc = grow(db, &db->bhits, q * kMaxK * sizeof(dbq::Hit), "batch hits");
+        if (!rc) rc = grow(db, &db->btickets, q * sizeof(unsigned int), "batch tickets");
+        if (!rc) rc = grow(db, &db->bstatus, 16, "status");
+        if (!rc && db->dims) {
+            const size_t rows = q * 2;
+            rc = grow(db, &db->bq_bf16, rows * db->dims * 2, "query bf16 embeddings");
+            if (!rc) rc = grow(db, &db->bq_f8, rows * db->dims, "query fp8 embeddings");
+            if (!rc) rc = grow(db, &db->bq_scale, rows * 4, "query scales");
+            if (!rc) rc = grow(db, &db->bq_nb, rows * 4, "query bf16 norms");
+            if (!rc) rc = grow(db, &db->bq_nf, rows * 4, "query fp8 norms");
+            if (!rc) rc = grow(db, &db->bdist, q * (size_t)db->n * 4, "prefilter distances");
+            if (!rc) rc = grow(db, &db->bcand, q * 1024 * 4, "prefilter candidates");
+            if (!rc) rc = grow(db, &db->brr, q * kRerankSlices * kMaxK * sizeof(dbq::Cand),
+                               "re-rank lists");
+        }
+        if (!rc && !db->bhits_host) {
+            cudaError_t err = cudaMallocHost(reinterpret_cast<void**>(&db->bhits_host),
+                                             q * kMaxK * sizeof(dbq::Hit));
+            if (err != cudaSuccess) {
+                cudaGetLastError();
+                db->bhits_host = nullptr;
+                rc = fail(DBQ_ENOMEM, "pinned host allocation failed");
+            }
+        }
+        if (!rc) {
+            cudaError_t err = cudaMemset(db->btickets, 0, q * sizeof(unsigned int));
+            if (err == cudaSuccess) err = cudaMemset(db->bstatus, 0, 16);
+            if (err == cudaSuccess) err = cudaDeviceSynchronize();
+            if (err != cudaSuccess) rc = cuda_fail(err, "batch workspace initialisation");
+        }
+        if (rc) return rc;
+        db->bq = kBatchQ;
+    }
+    (void)k;
+    return DBQ_OK;
+}
+
+// Threshold (or import) nq patients into bplanes / bpcount.
+int prepare_batch(dbq_db* db, int nq, const void* const* patients, int kind, float t1, float t2,
+                  cudaStream_t s)
+{
+    const size_t bytes = patient_bytes(db, kind);
+    std::vector<const void*> ptrs((size_t)nq);
+    bool any_host = false;
+    for (int q = 0; q < nq; ++q) {
+        if (!patients[q]) return fail(DBQ_EINVAL, "patient %d is NULL", q);
+        any_host |= !is_device_ptr(patients[q]);
+    }
+    if (any_host && db->bstage_each < bytes) {
+        int rc = grow(db, reinterpret_cast<char**>(&db->bstage), (size_t)kBatchQ * bytes,
+                      "batch patient staging");
+        if (rc) {
+            db->bstage_each = 0;
+            return rc;
+        }
+        db->bstage_each = bytes;
+    }
+    for (int q = 0; q < nq; ++q) {
+        if (is_device_ptr(patients[q])) {
+            ptrs[q] = patients[q];
+        } else {
+            char* dst = static_cast<char*>(db->bstage) + (size_t)q * db->bstage_each;
+            DBQ_CUDA(cudaMemcpyAsync(dst, patients[q], bytes, cudaMemcpyHostToDevice, s));
+            ptrs[q] = dst;
+        }
+    }
+    DBQ_CUDA(cudaMemsetAsync(db->bpcount, 0, (size_t)nq * 2 * 4, s));
+    if (kind == DBQ_BITS) {
+        for (int q = 0; q < nq; ++q) {
+            cudaError_t err = dbq::launch_import_bits(
+                static_cast<const uint32_t*>(ptrs[q]), db->words, db->v, db->wp,
+                db->bplanes + (size_t)q * 2 * db->wp, db->bpcount + 2 * q, s);
+            if (err != cudaSuccess) return cuda_fail(err, "patient import");
+        }
+    } else {
+        DBQ_CUDA(cudaMemcpyAsync(db->bptrs, ptrs.data(), (size_t)nq * sizeof(void*),
+                                 cudaMemcpyHostToDevice, s));
+        cudaError_t err = dbq::launch_pack_ptrs(db->bptrs, kind == DBQ_F16, nq, db->v, db->wp, t1,
+                                                t2, db->bplanes, db->bpcount, s);
+        if (err != cudaSuccess) return cuda_fail(err, "batch patient packing");
+    }
+    // the pointer array is pageable: the copy above has been staged already
+    return DBQ_OK;
+}
+
+// Prefilter for the nq prepared patients: embeddings, tensor-core distances,
+// candidate selection into bdist / bcand.
+int run_prefilter(dbq_db* db, int nq, int fp8, int c, cudaStream_t s)
+{
+    cudaError_t err = dbq::launch_embed(db->bplanes, nq, db->wp, db->nx, db->ny, db->nz,
+                                        db->bq_bf16, db->bq_f8, db->bq_scale, db->bq_nb,
+                                        db->bq_nf, s);
+    if (err != cudaSuccess) return cuda_fail(err, "query embedding launch");
+    dbq::GemmArgs g;
+    g.e_bf16 = db->emb_bf16;
+    g.e_f8 = db->emb_f8;
+    g.enorm = fp8 ? db->emb_nf : db->emb_nb;
+    g.escale = db->emb_scale;
+    g.q_bf16 = db->bq_bf16;
+    g.q_f8 = db->bq_f8;
+    g.qnorm = fp8 ? db->bq_nf : db->bq_nb;
+    g.qscale = db->bq_scale;
+    g.n = db->n;
+    g.nq = nq;
+    g.dims = db->dims;
+    g.dist = db->bdist;
+    g.status = db->bstatus;
+    err = dbq::launch_prefilter_gemm(g, fp8, db->grid, s);
+    if (err != cudaSuccess) return cuda_fail(err, "prefilter GEMM launch");
+    if (c > 0) {
+        err = dbq::launch_select_smallest(db->bdist, nq, db->n, c, db->bcand, s);
+        if (err != cudaSuccess) return cuda_fail(err, "candidate selection launch");
+    }
+    return DBQ_OK;
+}
+
+int check_status(dbq_db* db, cudaStream_t s)
+{
+    int st[4] = {0, 0, 0, 0};
+    DBQ_CUDA(cudaMemcpyAsync(st, db->bstatus, sizeof st, cudaMemcpyDeviceToHost, s));
+    DBQ_CUDA(cudaStreamSynchronize(s));
+    if (st[0] != 0) {
+        cudaMemsetAsync(db->bstatus, 0, 16, s);
+        cudaStreamSynchronize(s);
+        return fail(DBQ_ETIMEOUT, "tensor-core prefilter gave up waiting (role %d)", st[0]);
+    }
+    return DBQ_OK;
+}
+
+int check_prefilter_args(dbq_db* db, int mode, int c, int k)
+{
+    if (!db->built) return fail(DBQ_ESTATE, "database not built (call db_build_masks)");
+    if (!db->dims) return fail(DBQ_ESTATE, "database has no embeddings (DBQ_FLAG_EMBED)");
+    if (mode != DBQ_MODE_EMBED_BF16 && mode != DBQ_MODE_EMBED_FP8)
+        return fail(DBQ_EINVAL, "unknown prefilter mode %d", mode);
+    if (mode == DBQ_MODE_EMBED_FP8 && db->dims % 128)
+        return fail(DBQ_EINVAL, "FP8 prefilter needs a multiple of 128 embedding dims");
+    if (mode == DBQ_MODE_EMBED_BF16 && db->dims % 64)
+        return fail(DBQ_EINVAL, "bf16 prefilter needs a multiple of 64 embedding dims");
+    if (c < 1 || c > 1024 || c > db->n || c < k)
+        return fail(DBQ_ERANGE, "n_candidates %d outside [k, min(N, 1024)]", c);
+    return DBQ_OK;
+}
+
+}  // namespace
+
 extern "C" {
 
 const char* db_last_error(void) { return g_last_error.c_str(); }
@@ -284,7 +508,12 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
     if (storage == DBQ_STORE_BITS && (!threshold_ok(t1) || !threshold_ok(t2)))
         return fail(DBQ_EINVAL, "build thresholds must be finite and in (0, 1]");
     if (n_params < 0 || n_params > 64) return fail(DBQ_EINVAL, "n_params must be in [0, 64]");
-    if (flags != 0) return fail(DBQ_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~DBQ_FLAG_EMBED) return fail(DBQ_EINVAL, "unknown flags 0x%x", flags);
+    if ((flags & DBQ_FLAG_EMBED) &&
+        (storage != DBQ_STORE_BITS || !dbq::embed_supported(nx, ny, nz)))
+        return fail(DBQ_EINVAL,
+                    "embeddings need bit-packed storage, nx a multiple of 32 and ny, nz "
+                    "multiples of 8");
 
     int dev = 0;
     DBQ_CUDA(cudaGetDevice(&dev));
@@ -327,6 +556,15 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
     } else {
         rc = dev_alloc(db, &db->vols16, (size_t)capacity * db->vp * sizeof(uint16_t),
                        "binary16 volumes");
+    }
+    if (!rc && (flags & DBQ_FLAG_EMBED)) {
+        db->dims = dbq::embed_dims(nx, ny, nz);
+        const size_t rows = (size_t)capacity * 2;
+        rc = dev_alloc(db, &db->emb_bf16, rows * db->dims * 2, "bf16 embeddings");
+        if (!rc) rc = dev_alloc(db, &db->emb_f8, rows * db->dims, "fp8 embeddings");
+        if (!rc) rc = dev_alloc(db, &db->emb_scale, rows * 4, "fp8 scales");
+        if (!rc) rc = dev_alloc(db, &db->emb_nb, rows * 4, "bf16 norms");
+        if (!rc) rc = dev_alloc(db, &db->emb_nf, rows * 4, "fp8 norms");
     }
     db->grid = dbq::scan_packed_grid(dev);
     dbq::scan_packed_chunking(db->wp4, &db->chunk4, &db->nchunks);
@@ -440,7 +678,14 @@ int db_build_masks(dbq_db* db, void* stream)
                     (long long)db->n);
     DeviceGuard guard(db->device);
     if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
-    DBQ_CUDA(cudaStreamSynchronize(reinterpret_cast<cudaStream_t>(stream)));
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (db->flags & DBQ_FLAG_EMBED) {
+        cudaError_t err = dbq::launch_embed(db->planes, db->n, db->wp, db->nx, db->ny, db->nz,
+                                            db->emb_bf16, db->emb_f8, db->emb_scale, db->emb_nb,
+                                            db->emb_nf, s);
+        if (err != cudaSuccess) return cuda_fail(err, "embedding launch");
+    }
+    DBQ_CUDA(cudaStreamSynchronize(s));
     db->built = true;
     return DBQ_OK;
 }
@@ -581,6 +826,169 @@ int db_get_masks(dbq_db* db, int64_t first, int64_t count, uint32_t* planes, uin
         DBQ_CUDA(cudaMemcpyAsync(sizes, db->ecount + 2 * first, (size_t)count * 2 * 4,
                                  cudaMemcpyDefault, s));
     DBQ_CUDA(cudaStreamSynchronize(s));
+    return DBQ_OK;
+}
+
+int db_get_embeddings(dbq_db* db, int64_t first, int64_t count, uint16_t* bf16, uint8_t* e4m3,
+                      float* scale, float* norm_bf16, float* norm_fp8, void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (!db->dims) return fail(DBQ_ESTATE, "database has no embeddings (DBQ_FLAG_EMBED)");
+    if (!db->built) return fail(DBQ_ESTATE, "database not built (call db_build_masks)");
+    if (first < 0 || count < 0 || first + count > db->n)
+        return fail(DBQ_ERANGE, "entries outside [0, N)");
+    if (count == 0) return DBQ_OK;
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t rows = (size_t)count * 2, r0 = (size_t)first * 2;
+    if (bf16)
+        DBQ_CUDA(cudaMemcpyAsync(bf16, db->emb_bf16 + r0 * db->dims, rows * db->dims * 2,
+                                 cudaMemcpyDefault, s));
+    if (e4m3)
+        DBQ_CUDA(cudaMemcpyAsync(e4m3, db->emb_f8 + r0 * db->dims, rows * db->dims,
+                                 cudaMemcpyDefault, s));
+    if (scale)
+        DBQ_CUDA(cudaMemcpyAsync(scale, db->emb_scale + r0, rows * 4, cudaMemcpyDefault, s));
+    if (norm_bf16)
+        DBQ_CUDA(cudaMemcpyAsync(norm_bf16, db->emb_nb + r0, rows * 4, cudaMemcpyDefault, s));
+    if (norm_fp8)
+        DBQ_CUDA(cudaMemcpyAsync(norm_fp8, db->emb_nf + r0, rows * 4, cudaMemcpyDefault, s));
+    DBQ_CUDA(cudaStreamSynchronize(s));
+    return DBQ_OK;
+}
+
+int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int mode,
+                 int n_candidates, float* dist, int32_t* cand, void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    if (!patients) return fail(DBQ_EINVAL, "patients is NULL");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (nq < 1 || nq > kBatchQ) return fail(DBQ_ERANGE, "nq must be in [1, %d]", kBatchQ);
+    int rc = check_prefilter_args(db, mode, cand ? n_candidates : 1, 1);
+    if (rc) return rc;
+    if (kind != DBQ_F32 && kind != DBQ_F16 && kind != DBQ_BITS)
+        return fail(DBQ_EINVAL, "unknown patient kind %d", kind);
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    rc = ensure_batch(db, 1);
+    if (!rc) rc = prepare_batch(db, nq, patients, kind, db->t1, db->t2, s);
+    if (!rc) rc = run_prefilter(db, nq, mode == DBQ_MODE_EMBED_FP8, cand ? n_candidates : 0, s);
+    if (rc) return rc;
+    if (dist)
+        DBQ_CUDA(cudaMemcpyAsync(dist, db->bdist, (size_t)nq * db->n * 4, cudaMemcpyDefault, s));
+    if (cand)
+        DBQ_CUDA(cudaMemcpyAsync(cand, db->bcand, (size_t)nq * n_candidates * 4,
+                                 cudaMemcpyDefault, s));
+    return check_status(db, s);
+}
+
+int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
+                   const void* const* patients, int kind, const float* t1, const float* t2,
+                   int k, int mode, int n_candidates, dbq_hit* hits, double* params,
+                   void* stream)
+{
+    if (!dbs || !db_of_query || !patients || !hits) return fail(DBQ_EINVAL, "NULL argument");
+    if (nq < 0) return fail(DBQ_EINVAL, "nq < 0");
+    if (mode != DBQ_MODE_EXACT && mode != DBQ_MODE_EMBED_BF16 && mode != DBQ_MODE_EMBED_FP8)
+        return fail(DBQ_EINVAL, "unknown mode %d", mode);
+    if (kind != DBQ_F32 && kind != DBQ_F16 && kind != DBQ_BITS)
+        return fail(DBQ_EINVAL, "unknown patient kind %d", kind);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // group queries by database, keeping their order inside a group
+    std::vector<int> order((size_t)nq);
+    for (int q = 0; q < nq; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return db_of_query[a] < db_of_query[b]; });
+    size_t i = 0;
+    while (i < order.size()) {
+        const int dbi = db_of_query[order[i]];
+        size_t j = i;
+        while (j < order.size() && db_of_query[order[j]] == dbi) ++j;
+        dbq_db* db = dbs[dbi];
+        if (!db) return fail(DBQ_EINVAL, "database %d is NULL", dbi);
+        std::lock_guard<std::mutex> lock(db->mu);
+        DeviceGuard guard(db->device);
+        if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+        for (size_t g0 = i; g0 < j; g0 += kBatchQ) {
+            const int gn = (int)std::min<size_t>(kBatchQ, j - g0);
+            float a1 = t1 ? t1[order[g0]] : NAN, a2 = t2 ? t2[order[g0]] : NAN;
+            int rc = check_query_args(db, kind, &a1, &a2, k);
+            if (rc) return rc;
+            rc = ensure_batch(db, k);
+            if (rc) return rc;
+            if (mode == DBQ_MODE_EXACT) {
+                for (int q = 0; q < gn; ++q) {
+                    const int qi = order[g0 + q];
+                    float b1 = t1 ? t1[qi] : NAN, b2 = t2 ? t2[qi] : NAN;
+                    rc = check_query_args(db, kind, &b1, &b2, k);
+                    if (!rc) rc = prepare_patient(db, patients[qi], kind, b1, b2, s);
+                    if (!rc) rc = launch_query(db, k, db->bhits + (size_t)q * k, nullptr, s);
+                    if (rc) return rc;
+                }
+            } else {
+                if (db->storage != DBQ_STORE_BITS)
+                    return fail(DBQ_EINVAL, "embedding modes need a bit-packed database");
+                rc = check_prefilter_args(db, mode, n_candidates, k);
+                if (rc) return rc;
+                std::vector<const void*> pp((size_t)gn);
+                for (int q = 0; q < gn; ++q) {
+                    const int qi = order[g0 + q];
+                    float b1 = t1 ? t1[qi] : NAN, b2 = t2 ? t2[qi] : NAN;
+                    rc = check_query_args(db, kind, &b1, &b2, k);
+                    if (rc) return rc;
+                    pp[q] = patients[qi];
+                }
+                rc = prepare_batch(db, gn, pp.data(), kind, db->t1, db->t2, s);
+                if (!rc) rc = run_prefilter(db, gn, mode == DBQ_MODE_EMBED_FP8, n_candidates, s);
+                if (rc) return rc;
+                dbq::RerankArgs r;
+                r.planes = reinterpret_cast<const uint4*>(db->planes);
+                r.ecount = db->ecount;
+                r.n = db->n;
+                r.wp4 = db->wp4;
+                r.chunk4 = db->chunk4;
+                r.nchunks = db->nchunks;
+                r.patients = reinterpret_cast<const uint4*>(db->bplanes);
+                r.pcounts = db->bpcount;
+                r.cand = db->bcand;
+                r.nq = gn;
+                r.c = n_candidates;
+                r.k = k;
+                r.slices = std::min(kRerankSlices, n_candidates);
+                r.scratch = db->brr;
+                r.tickets = db->btickets;
+                r.hits = db->bhits;
+                cudaError_t err = dbq::launch_rerank(r, s);
+                if (err != cudaSuccess) return cuda_fail(err, "re-rank launch");
+            }
+            DBQ_CUDA(cudaMemcpyAsync(db->bhits_host, db->bhits, (size_t)gn * k * sizeof(dbq::Hit),
+                                     cudaMemcpyDeviceToHost, s));
+            if (mode != DBQ_MODE_EXACT) {
+                rc = check_status(db, s);
+                if (rc) return rc;
+            }
+            DBQ_CUDA(cudaStreamSynchronize(s));
+            for (int q = 0; q < gn; ++q) {
+                const int qi = order[g0 + q];
+                std::memcpy(hits + (size_t)qi * k, db->bhits_host + (size_t)q * k,
+                            (size_t)k * sizeof(dbq_hit));
+                if (params && db->n_params) {
+                    for (int h = 0; h < k; ++h) {
+                        const int64_t e = hits[(size_t)qi * k + h].index;
+                        if (e < 0 || e >= db->n)
+                            return fail(DBQ_ECUDA, "kernel returned index %lld", (long long)e);
+                        std::memcpy(params + ((size_t)qi * k + h) * db->n_params,
+                                    &db->params[(size_t)e * db->n_params],
+                                    sizeof(double) * db->n_params);
+                    }
+                }
+            }
+        }
+        i = j;
+    }
     return DBQ_OK;
 }
 

@@ -11,7 +11,7 @@
 
 namespace dbq {
 
-constexpr double kSentinelScore = -1.0;            // below every Dice score (>= 0)
+constexpr double kSentinelScore = -1.0e308;         // below every score and every -distance
 constexpr int64_t kSentinelIndex = INT64_MAX;
 
 // Device-side copy of dbq_hit (same layout as the C ABI struct).

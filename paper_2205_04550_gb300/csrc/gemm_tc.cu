@@ -1,0 +1,441 @@
+// gemm_tc.cu -- L2 prefilter distances on the 5th-generation tensor cores.
+//
+// For every (query q, entry e) and each segmentation k the squared L2
+// distance of the embeddings is |q_k|^2 + |e_k|^2 - 2 q_k . e_k; the
+// prefilter's distance is L = d_1 + d_2 with d_k the (non-squared) distance,
+// following the paper's L2_T1Gd + L2_FLAIR combination (Section 2.3).  The
+// dot products are a dense contraction (Q queries x N entries x D dims per
+// segmentation), so they run as a tcgen05 GEMM with fp32 accumulation in
+// tensor memory:
+//
+//   * one CTA per SM, persistent over tiles of 128 entries;
+//   * warp 0 (one thread) issues TMA loads of 128-byte-swizzled K-slices of
+//     the entry tile (128 rows) and of all queries (256 rows) into a 4-stage
+//     shared-memory ring guarded by full/empty mbarriers;
+//   * warp 1 owns 512 TMEM columns and one thread issues tcgen05.mma
+//     (M = 128 entries, N = 256 queries, K = 16 bf16 or 32 fp8 per
+//     instruction): columns [0, 256) accumulate q_1 . e_1, [256, 512)
+//     q_2 . e_2; tcgen05.commit frees each stage and signals the epilogue;
+//   * warps 2-5 read the accumulators with tcgen05.ld (each warp its 32-lane
+//     quarter), form L in binary32 and store L[q][e] coalesced.
+// Every mbarrier wait is bounded (iteration count and %globaltimer); on a
+// timeout the CTA records an error code in `status`, stops issuing work,
+// waits (bounded) for the copies and MMAs it has in flight, frees its TMEM
+// and returns.
+#include <cuda.h>
+
+#include "kernels.h"
+
+namespace dbq {
+namespace {
+
+constexpr int kBM = 128;          // entries per tile (TMEM lanes)
+constexpr int kBN = 256;          // queries per launch (MMA N)
+constexpr int kStages = 4;
+constexpr int kTileABytes = kBM * 128;   // 128 rows x 128 bytes (one swizzle atom wide)
+constexpr int kTileBBytes = kBN * 128;
+constexpr int kStageBytes = kTileABytes + kTileBBytes;
+constexpr int kThreads = 192;            // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait; false after the time limit, or -- when `abort_flag` is given
+// -- as soon as another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag)
+{
+    if (mbar_try(bar, parity)) return true;
+    const unsigned long long t0 = now_ns();
+    for (uint32_t i = 0;; ++i) {
+        if (mbar_try(bar, parity)) return true;
+        if ((i & 63) == 63) {
+            if (abort_flag && *abort_flag) return false;
+            if (now_ns() - t0 > kWaitNs) return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);          // start address
+    d |= (uint64_t)1 << 16;                           // leading byte offset (unused)
+    d |= (uint64_t)(1024 >> 4) << 32;                 // stride byte offset
+    d |= (uint64_t)1 << 46;                           // descriptor version (sm_100)
+    d |= (uint64_t)2 << 61;                           // 128-byte swizzle
+    return d;
+}
+
+template <bool kFp8>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                     uint32_t idesc, uint32_t accumulate)
+{
+    if (kFp8) {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+            : "memory");
+    }
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+        "%28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+          "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld()
+{
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Instruction descriptor: fp32 accumulator, A/B K-major, M = 128, N = 256;
+// operand format bf16 (kind::f16) or E4M3 (kind::f8f6f4).
+template <bool kFp8>
+__host__ __device__ constexpr uint32_t instr_desc()
+{
+    return (1u << 4)                                   // D format: f32
+           | ((kFp8 ? 0u : 1u) << 7)                   // A format: e4m3 / bf16
+           | ((kFp8 ? 0u : 1u) << 10)                  // B format
+           | ((uint32_t)(kBN >> 3) << 17)              // N / 8
+           | ((uint32_t)(kBM >> 4) << 24);             // M / 16
+}
+
+template <bool kFp8>
+__global__ void __launch_bounds__(kThreads, 1)
+prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
+                      const __grid_constant__ CUtensorMap tm_q, GemmArgs a)
+{
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte alignment for the swizzle atoms
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* ring = base;                                   // kStages x kStageBytes
+    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * kStageBytes);
+    // bars: full[kStages], empty[kStages], acc_full, acc_empty, drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 3);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    float* qnorm = reinterpret_cast<float*>(tmem_slot + 4);       // [2][kBN]
+    float* qscale = qnorm + 2 * kBN;                               // [2][kBN]
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int ktiles = a.dims / (kFp8 ? 128 : 64);                 // K-slices per segmentation
+    const int ntiles = (int)((a.n + kBM - 1) / kBM);
+
+    const uint32_t full0 = smem_u32(bars);
+    const uint32_t empty0 = smem_u32(bars + kStages);
+    const uint32_t acc_full = smem_u32(bars + 2 * kStages);
+    const uint32_t acc_empty = smem_u32(bars + 2 * kStages + 1);
+    const uint32_t drain = smem_u32(bars + 2 * kStages + 2);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 128);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int i = threadIdx.x; i < 2 * kBN; i += blockDim.x) {
+        const int q = i % kBN, k = i / kBN;
+        qnorm[i] = q < a.nq ? a.qnorm[2 * q + k] : 0.0f;
+        qscale[i] = (kFp8 && q < a.nq) ? a.qscale[2 * q + k] : 1.0f;
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                         smem_u32(tmem_slot))
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    uint32_t issued = 0;     // producer: stage loads issued
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t it = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+                for (int seg = 0; seg < 2 && ok; ++seg) {
+                    for (int kt = 0; kt < ktiles; ++kt, ++it) {
+                        const int s = it % kStages;
+                        const uint32_t ph = ((it / kStages) & 1) ^ 1;
+                        if (!mbar_wait(empty0 + 8 * s, ph, abort_flag)) { ok = false; break; }
+                        const uint32_t sa = smem_u32(ring + s * kStageBytes);
+                        const uint32_t sb = sa + kTileABytes;
+                        mbar_arrive_expect_tx(full0 + 8 * s, kStageBytes);
+                        const int x = seg * a.dims + kt * (kFp8 ? 128 : 64);
+                        tma_load_2d(sa, &tm_e, full0 + 8 * s, x, tile * kBM);
+                        tma_load_2d(sb, &tm_q, full0 + 8 * s, x, 0);
+                        ++issued;
+                    }
+                }
+            }
+            if (!ok) {
+                a.status[0] = 1;
+                *abort_flag = 1;
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            constexpr uint32_t idesc = instr_desc<kFp8>();
+            uint32_t it = 0, tiles_done = 0;
+            bool ok = true;
+            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tiles_done) {
+                if (!mbar_wait(acc_empty, (tiles_done & 1) ^ 1, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+                for (int seg = 0; seg < 2 && ok; ++seg) {
+                    const uint32_t d_tmem = tmem + seg * kBN;
+                    for (int kt = 0; kt < ktiles; ++kt, ++it) {
+                        const int s = it % kStages;
+                        if (!mbar_wait(full0 + 8 * s, (it / kStages) & 1, abort_flag)) {
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint32_t sa = smem_u32(ring + s * kStageBytes);
+                        const uint32_t sb = sa + kTileABytes;
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk) {
+                            // K step of 32 bytes inside the 128-byte swizzle atom
+                            umma<kFp8>(d_tmem, sw128_desc(sa + 32 * kk), sw128_desc(sb + 32 * kk),
+                                       idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                        }
+                        umma_commit(empty0 + 8 * s);   // frees the stage when these MMAs finish
+                    }
+                }
+                if (ok) umma_commit(acc_full);
+            }
+            if (!ok) {
+                a.status[0] = 2;
+                *abort_flag = 1;
+            }
+            // every MMA issued by this thread has completed once `drain` fires;
+            // TMEM is released only after that (or after the time limit)
+            umma_commit(drain);
+            if (!mbar_wait(drain, 0, nullptr)) a.status[0] = 3;
+        }
+    } else {
+        // epilogue warps 2..5: TMEM lane quarter = warp % 4
+        const int quarter = warp & 3;
+        const int row = quarter * 32 + lane;
+        uint32_t tiles_done = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tiles_done) {
+            if (!mbar_wait(acc_full, tiles_done & 1, abort_flag)) {
+                a.status[0] = 4;
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            const int64_t e = (int64_t)tile * kBM + row;
+            const bool valid = e < a.n;
+            float en0 = 0.f, en1 = 0.f, es0 = 1.f, es1 = 1.f;
+            if (valid) {
+                en0 = a.enorm[2 * e];
+                en1 = a.enorm[2 * e + 1];
+                if (kFp8) {
+                    es0 = a.escale[2 * e];
+                    es1 = a.escale[2 * e + 1];
+                }
+            }
+            for (int c = 0; c < kBN; c += 32) {
+                uint32_t r0[32], r1[32];
+                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + c;
+                tmem_ld32(taddr, r0);
+                tmem_ld32(taddr + kBN, r1);
+                tmem_wait_ld();
+                if (valid) {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const int q = c + j;
+                        if (q < a.nq) {
+                            float dot0 = __uint_as_float(r0[j]);
+                            float dot1 = __uint_as_float(r1[j]);
+                            if (kFp8) {
+                                dot0 = dot0 * (qscale[q] * es0);
+                                dot1 = dot1 * (qscale[kBN + q] * es1);
+                            }
+                            const float s0 = fmaxf(qnorm[q] + en0 - 2.0f * dot0, 0.0f);
+                            const float s1 = fmaxf(qnorm[kBN + q] + en1 - 2.0f * dot1, 0.0f);
+                            a.dist[(int64_t)q * a.n + e] = sqrtf(s0) + sqrtf(s1);
+                        }
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty);
+        }
+    }
+
+    __syncthreads();
+    if (warp == 0 && lane == 0 && *abort_flag) {
+        // let the loads already issued land before the CTA's shared memory is
+        // released: the last load into stage s completed phase (count_s - 1)
+        for (int s = 0; s < kStages; ++s) {
+            const uint32_t count_s = (issued + kStages - 1 - s) / kStages;
+            if (count_s == 0) continue;
+            mbar_wait(full0 + 8 * s, (count_s - 1) & 1, nullptr);
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+                     : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000,
+                                             cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    }
+    return fn;
+}
+
+bool make_map(CUtensorMap* m, const void* base, bool fp8, int64_t rows, int64_t cols, int box_rows)
+{
+    EncodeTiledFn enc = encode_fn();
+    if (!enc) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)cols * (fp8 ? 1 : 2)};
+    const cuuint32_t box[2] = {(cuuint32_t)(fp8 ? 128 : 64), (cuuint32_t)box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(m, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+               const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+size_t gemm_smem_bytes()
+{
+    return 1024 + (size_t)kStages * kStageBytes + (2 * kStages + 3) * 8 + 16 + 4 * kBN * 4;
+}
+
+int gemm_max_queries() { return kBN; }
+
+cudaError_t launch_prefilter_gemm(const GemmArgs& a, int fp8, int grid, cudaStream_t stream)
+{
+    if (a.nq < 1 || a.nq > kBN || a.n < 1 || a.dims % (fp8 ? 128 : 64) != 0)
+        return cudaErrorInvalidValue;
+    CUtensorMap tm_e, tm_q;
+    const void* eb = fp8 ? (const void*)a.e_f8 : (const void*)a.e_bf16;
+    const void* qb = fp8 ? (const void*)a.q_f8 : (const void*)a.q_bf16;
+    if (!make_map(&tm_e, eb, fp8, a.n, 2 * (int64_t)a.dims, kBM) ||
+        !make_map(&tm_q, qb, fp8, a.nq, 2 * (int64_t)a.dims, kBN))
+        return cudaErrorInvalidValue;
+    const size_t smem = gemm_smem_bytes();
+    const int ntiles = (int)((a.n + kBM - 1) / kBM);
+    if (grid > ntiles) grid = ntiles;
+    cudaError_t err;
+    if (fp8) {
+        err = cudaFuncSetAttribute(prefilter_gemm_kernel<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        prefilter_gemm_kernel<true><<<grid, kThreads, smem, stream>>>(tm_e, tm_q, a);
+    } else {
+        err = cudaFuncSetAttribute(prefilter_gemm_kernel<false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        prefilter_gemm_kernel<false><<<grid, kThreads, smem, stream>>>(tm_e, tm_q, a);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace dbq

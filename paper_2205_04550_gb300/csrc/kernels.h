@@ -16,6 +16,12 @@ cudaError_t launch_pack(const void* vols, int src_f16, int64_t count, int64_t v,
                         float t1, float t2, uint32_t* planes, uint32_t* ecount,
                         cudaStream_t stream);
 
+// launch_pack for `count` (<= 65535) volumes whose device addresses are in
+// the device array srcs[count].
+cudaError_t launch_pack_ptrs(const void* const* srcs, int src_f16, int count, int64_t v,
+                             int64_t wp, float t1, float t2, uint32_t* planes, uint32_t* ecount,
+                             cudaStream_t stream);
+
 // Round float32 to binary16, nearest-even (storage conversion of the
 // half-precision database).
 cudaError_t launch_to_f16(const float* src, int64_t n, uint16_t* dst, cudaStream_t stream);
@@ -76,6 +82,60 @@ cudaError_t launch_scan_f16(const ScanF16Args& a, int grid, cudaStream_t stream)
 // nearest-even) into rows of `pitch` halves; the padding is left untouched.
 cudaError_t launch_rows_to_f16(const void* src, int src_f16, int64_t count, int64_t v,
                                int64_t pitch, uint16_t* dst, cudaStream_t stream);
+
+// ---- embedding prefilter (a6-a8)
+
+// Embeddings need nx % 32 == 0 and ny, nz multiples of 8.
+bool embed_supported(int nx, int ny, int nz);
+int embed_dims(int nx, int ny, int nz);   // (nx/8)(ny/8)(nz/8) per segmentation
+// planes [count][2][wp] -> bf16 [count][2][d], e4m3 [count][2][d], scale,
+// squared norms of the decoded bf16 / fp8 rows [count][2].
+cudaError_t launch_embed(const uint32_t* planes, int64_t count, int64_t wp, int nx, int ny,
+                         int nz, uint16_t* out_bf16, uint8_t* out_f8, float* out_scale,
+                         float* out_norm_bf16, float* out_norm_f8, cudaStream_t stream);
+
+struct GemmArgs {
+    const uint16_t* e_bf16;   // [n][2*dims] entry embeddings (bf16 bits)
+    const uint8_t* e_f8;      // [n][2*dims] entry embeddings (e4m3 codes)
+    const float* enorm;       // [n][2] squared norms of the encoding used
+    const float* escale;      // [n][2] e4m3 row scales (fp8 only)
+    const uint16_t* q_bf16;   // [nq][2*dims]
+    const uint8_t* q_f8;      // [nq][2*dims]
+    const float* qnorm;       // [nq][2]
+    const float* qscale;      // [nq][2]
+    int64_t n;
+    int nq;                   // <= gemm_max_queries()
+    int dims;                 // per segmentation, multiple of 64 (bf16) / 128 (fp8)
+    float* dist;              // [nq][n] L = d_1 + d_2
+    int* status;              // device int, 0 = ok, else the role that timed out
+};
+size_t gemm_smem_bytes();
+int gemm_max_queries();
+cudaError_t launch_prefilter_gemm(const GemmArgs& a, int fp8, int grid, cudaStream_t stream);
+
+// The c smallest distances per query (ties to the lower index), ascending:
+// dist [nq][n] -> cand [nq][c] entry indices.  c <= 1024, c <= n.
+cudaError_t launch_select_smallest(const float* dist, int nq, int64_t n, int c, int32_t* cand,
+                                   cudaStream_t stream);
+
+// Exact re-ranking: for each query q, the packed scan restricted to the
+// entries cand[q][0..c) -> top-k hits [nq][k].  patient planes [nq][2][wp],
+// pcount [nq][2]; scratch: cand lists [nq][slices][k] and tickets [nq]
+// (zero between launches).
+struct RerankArgs {
+    const uint4* planes;        // database [n][2][wp4]
+    const uint32_t* ecount;     // [n][2]
+    int64_t n;
+    int wp4, chunk4, nchunks;
+    const uint4* patients;      // [nq][2][wp4]
+    const uint32_t* pcounts;    // [nq][2]
+    const int32_t* cand;        // [nq][c]
+    int nq, c, k, slices;
+    Cand* scratch;              // [nq][slices][k]
+    unsigned int* tickets;      // [nq]
+    Hit* hits;                  // [nq][k]
+};
+cudaError_t launch_rerank(const RerankArgs& a, cudaStream_t stream);
 
 // Set the calling thread's db_last_error() message; returns `code`.
 int record_error(int code, const char* msg);

@@ -67,6 +67,47 @@ pack_kernel(const void* __restrict__ vols, int64_t v, int64_t wp, float t1, floa
     }
 }
 
+// One source volume per blockIdx.y, taken from a device array of pointers.
+template <bool kHalf>
+__global__ void __launch_bounds__(kPackThreads)
+pack_ptrs_kernel(const void* const* __restrict__ srcs, int64_t v, int64_t wp, float t1, float t2,
+                 uint32_t* __restrict__ planes, uint32_t* __restrict__ ecount)
+{
+    const int64_t e = blockIdx.y;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * kPackThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kPackThreads) >> 5;
+    const void* src = srcs[e];
+    uint32_t* p1 = planes + e * 2 * wp;
+    uint32_t* p2 = p1 + wp;
+    uint32_t c1 = 0, c2 = 0;
+    for (int64_t w0 = warp * kPackUnroll; w0 < wp; w0 += nwarps * kPackUnroll) {
+        float val[kPackUnroll];
+#pragma unroll
+        for (int u = 0; u < kPackUnroll; ++u) {
+            const int64_t x = (w0 + u) * 32 + lane;
+            val[u] = (x < v) ? load_value<kHalf>(src, x) : 0.0f;
+        }
+#pragma unroll
+        for (int u = 0; u < kPackUnroll; ++u) {
+            const int64_t w = w0 + u;
+            const bool in = w * 32 + lane < v;
+            const uint32_t b1 = __ballot_sync(0xffffffffu, in && val[u] >= t1);
+            const uint32_t b2 = __ballot_sync(0xffffffffu, in && val[u] >= t2);
+            if (lane == 0 && w < wp) {
+                p1[w] = b1;
+                p2[w] = b2;
+                c1 += __popc(b1);
+                c2 += __popc(b2);
+            }
+        }
+    }
+    if (lane == 0 && (c1 | c2)) {
+        atomicAdd(&ecount[2 * e], c1);
+        atomicAdd(&ecount[2 * e + 1], c2);
+    }
+}
+
 __global__ void import_bits_kernel(const uint32_t* __restrict__ src, int64_t words, int64_t v,
                                    int64_t wp, uint32_t* __restrict__ planes,
                                    uint32_t* __restrict__ pcount)
@@ -168,6 +209,23 @@ cudaError_t launch_pack(const void* vols, int src_f16, int64_t count, int64_t v,
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
+}
+
+cudaError_t launch_pack_ptrs(const void* const* srcs, int src_f16, int count, int64_t v,
+                             int64_t wp, float t1, float t2, uint32_t* planes, uint32_t* ecount,
+                             cudaStream_t stream)
+{
+    if (count <= 0) return cudaSuccess;
+    const int64_t warps_needed = (wp + kPackUnroll - 1) / kPackUnroll;
+    int64_t bx = (warps_needed * 32 + kPackThreads - 1) / kPackThreads;
+    if (bx > 64) bx = 64;
+    if (bx < 1) bx = 1;
+    dim3 grid((unsigned)bx, (unsigned)count);
+    if (src_f16)
+        pack_ptrs_kernel<true><<<grid, kPackThreads, 0, stream>>>(srcs, v, wp, t1, t2, planes, ecount);
+    else
+        pack_ptrs_kernel<false><<<grid, kPackThreads, 0, stream>>>(srcs, v, wp, t1, t2, planes, ecount);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_import_bits(const uint32_t* src, int64_t words, int64_t v, int64_t wp,

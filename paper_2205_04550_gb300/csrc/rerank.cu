@@ -1,0 +1,101 @@
+// rerank.cu -- exact Dice re-ranking of the prefilter's candidates.
+//
+// The candidates of each query are scored by the same exact loop as the
+// full scan (Section 2.3 of Ezhov et al. 2022: Dice at both thresholds,
+// added, largest wins), so the returned hits carry exact counts and binary64
+// scores; only which entries are looked at comes from the prefilter.
+//
+// Work items are (query, slice of its candidates); the grid walks them
+// round-robin.  Each item gathers its candidates' planes with the shared
+// count loop of scan_core.cuh (patient words in registers), keeps a running
+// top-k, publishes it to the query's scratch row, and the last item of a
+// query (per-query atomic ticket, no spinning) merges the slices into the
+// query's k hits.
+#include "kernels.h"
+#include "scan_core.cuh"
+#include "topk.cuh"
+
+namespace dbq {
+namespace {
+
+constexpr int kGroupMax = 1024;
+
+template <int U, int EPI>
+__global__ void __launch_bounds__(kScanThreads, 1)
+rerank_kernel(const RerankArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TopK tk;
+    uint32_t* icnt = reinterpret_cast<uint32_t*>(topk_carve(tk, smem_raw));   // [kGroupMax][2]
+    const int tid = threadIdx.x;
+    const int per = (a.c + a.slices - 1) / a.slices;
+    const int items = a.nq * a.slices;
+    const uint2* ecount2 = reinterpret_cast<const uint2*>(a.ecount);
+    for (int item = blockIdx.x; item < items; item += gridDim.x) {
+        const int q = item / a.slices;
+        const int sl = item % a.slices;
+        const int first = sl * per;
+        const int gn = (a.c - first) < per ? (a.c - first) : per;
+        const int32_t* list = a.cand + (int64_t)q * a.c + first;
+        const uint4* patient = a.patients + (int64_t)q * 2 * a.wp4;
+        const uint32_t P1 = a.pcounts[2 * q];
+        const uint32_t P2 = a.pcounts[2 * q + 1];
+        topk_init(tk);
+        for (int i = tid; i < 2 * kGroupMax; i += kScanThreads) icnt[i] = 0u;
+        __syncthreads();
+        if (gn > 0)
+            count_group<U, EPI>(a.planes, a.wp4, a.chunk4, a.nchunks, patient, list, 0, gn, icnt);
+        __syncthreads();
+        for (int i = tid; i < gn; i += kScanThreads) {
+            const int64_t e = list[i];
+            const uint32_t I1 = icnt[2 * i], I2 = icnt[2 * i + 1];
+            const uint2 E = ecount2[e];
+            topk_offer(tk, a.k, score_rn(I1, I2, E.x, E.y, P1, P2), e,
+                       (uint64_t)I1 | ((uint64_t)I2 << 32), (uint64_t)E.x | ((uint64_t)E.y << 32));
+        }
+        topk_flush(tk, a.k);
+        Cand* rows = a.scratch + (int64_t)q * a.slices * a.k;
+        if (topk_publish_slot(tk, a.k, rows, sl, a.slices, a.tickets + q)) {
+            topk_merge_published(tk, a.k, rows, (int64_t)a.slices * a.k);
+            for (int j = tid; j < a.k; j += kScanThreads) {
+                Hit h;
+                h.index = tk.idx[j];
+                h.score = tk.key[j];
+                h.i1 = (uint32_t)(tk.pay0[j] & 0xffffffffu);
+                h.i2 = (uint32_t)(tk.pay0[j] >> 32);
+                h.e1 = (uint32_t)(tk.pay1[j] & 0xffffffffu);
+                h.e2 = (uint32_t)(tk.pay1[j] >> 32);
+                h.p1 = P1;
+                h.p2 = P2;
+                a.hits[(int64_t)q * a.k + j] = h;
+            }
+        }
+        __syncthreads();   // the shared top-k is reused by the next item
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_rerank(const RerankArgs& a, cudaStream_t stream)
+{
+    if (a.nq < 1 || a.c < 1 || a.k < 1 || a.k > a.c || a.slices < 1 ||
+        (a.c + a.slices - 1) / a.slices > kGroupMax)
+        return cudaErrorInvalidValue;
+    const size_t smem = topk_smem_bytes() + (size_t)kGroupMax * 2 * sizeof(uint32_t);
+    int dev = 0, sms = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int items = a.nq * a.slices;
+    const int grid = items < sms ? items : sms;
+    auto run = [&](auto kern) -> cudaError_t {
+        cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               (int)smem);
+        if (err != cudaSuccess) return err;
+        kern<<<grid, kScanThreads, smem, stream>>>(a);
+        return cudaGetLastError();
+    };
+    if (a.chunk4 <= kScanThreads) return run(rerank_kernel<1, 4>);
+    return run(rerank_kernel<2, 2>);
+}
+
+}  // namespace dbq

@@ -24,19 +24,16 @@
 //   * Each CTA writes its list to scratch; the last CTA to finish (atomic
 //     ticket, no spinning) merges all lists and writes the k hits.
 #include "kernels.h"
+#include "scan_core.cuh"
 #include "topk.cuh"
 
 namespace dbq {
 namespace {
 
-constexpr int kThreads = 1024;
+constexpr int kThreads = kScanThreads;
 constexpr int kGroup = 1024;        // entries whose counters live in shared memory
 constexpr int kMaxChunk4 = 2048;    // uint4 per plane per chunk = 2 per thread
 
-// Thread t always handles the 16-byte words t + u*kThreads (u < U) of the
-// current chunk of both planes, so it keeps the patient's words for those
-// positions in registers for the whole chunk and streams the database words
-// of EPI entries at a time against them.
 template <int U, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
 scan_packed_kernel(const ScanPackedArgs a)
@@ -45,7 +42,6 @@ scan_packed_kernel(const ScanPackedArgs a)
     TopK tk;
     uint32_t* icnt = reinterpret_cast<uint32_t*>(topk_carve(tk, smem_raw));   // [kGroup][2]
     const int tid = threadIdx.x;
-    const int lane = tid & 31;
     const int k = a.k;
     const bool want_topk = a.hits != nullptr;
     const int64_t e_begin = (int64_t)blockIdx.x * a.n / gridDim.x;
@@ -60,52 +56,8 @@ scan_packed_kernel(const ScanPackedArgs a)
         const int gn = (int)((e_end - g0) < kGroup ? (e_end - g0) : kGroup);
         for (int i = tid; i < 2 * kGroup; i += kThreads) icnt[i] = 0u;
         __syncthreads();
-        for (int c = 0; c < a.nchunks; ++c) {
-            const int c0 = c * a.chunk4;
-            const int clen = (a.wp4 - c0) < a.chunk4 ? (a.wp4 - c0) : a.chunk4;
-            uint4 pa[U], pb[U];   // the patient's words at this thread's positions
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int j = tid + u * kThreads;
-                pa[u] = (j < clen) ? a.patient[c0 + j] : make_uint4(0, 0, 0, 0);
-                pb[u] = (j < clen) ? a.patient[a.wp4 + c0 + j] : make_uint4(0, 0, 0, 0);
-            }
-            for (int i0 = 0; i0 < gn; i0 += EPI) {
-                uint4 x[EPI][U], y[EPI][U];
-#pragma unroll
-                for (int q = 0; q < EPI; ++q) {
-                    const bool ev = (i0 + q) < gn;
-                    const uint4* p0 = a.planes + (g0 + i0 + q) * 2 * a.wp4 + c0;
-                    const uint4* p1 = p0 + a.wp4;
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        const int j = tid + u * kThreads;
-                        if (ev && j < clen) {
-                            x[q][u] = ld_stream(p0 + j);
-                            y[q][u] = ld_stream(p1 + j);
-                        } else {
-                            x[q][u] = make_uint4(0, 0, 0, 0);
-                            y[q][u] = make_uint4(0, 0, 0, 0);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int q = 0; q < EPI; ++q) {
-                    uint32_t a1 = 0, a2 = 0;
-#pragma unroll
-                    for (int u = 0; u < U; ++u) {
-                        a1 += popc_and4(x[q][u], pa[u]);
-                        a2 += popc_and4(y[q][u], pb[u]);
-                    }
-                    a1 = __reduce_add_sync(0xffffffffu, a1);
-                    a2 = __reduce_add_sync(0xffffffffu, a2);
-                    if (lane == 0 && (i0 + q) < gn) {
-                        if (a1) atomicAdd(&icnt[2 * (i0 + q)], a1);
-                        if (a2) atomicAdd(&icnt[2 * (i0 + q) + 1], a2);
-                    }
-                }
-            }
-        }
+        count_group<U, EPI>(a.planes, a.wp4, a.chunk4, a.nchunks, a.patient, nullptr, g0, gn,
+                            icnt);
         __syncthreads();   // the group's counters are complete
         for (int i = tid; i < gn; i += kThreads) {
             const int64_t e = g0 + i;

@@ -114,12 +114,13 @@ __device__ __forceinline__ void topk_flush(TopK& t, int k)
     __syncthreads();
 }
 
-// Publish this CTA's k slots to cand[blockIdx.x * k ...] and take a ticket.
-// Returns true (in every thread) in the last CTA to arrive, which then sees
-// every CTA's list.
-__device__ __forceinline__ bool topk_publish(TopK& t, int k, Cand* cand, unsigned int* ticket)
+// Publish the k slots to dst[slot * k ...] and take a ticket on a counter
+// shared by `nslots` publishers.  Returns true (in every thread) in the last
+// publisher to arrive, which then sees every list.
+__device__ __forceinline__ bool topk_publish_slot(TopK& t, int k, Cand* dst, int slot, int nslots,
+                                                  unsigned int* ticket)
 {
-    Cand* mine = cand + (int64_t)blockIdx.x * k;
+    Cand* mine = dst + (int64_t)slot * k;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         Cand c;
         c.score = t.key[j];
@@ -131,13 +132,19 @@ __device__ __forceinline__ bool topk_publish(TopK& t, int k, Cand* cand, unsigne
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
-        const unsigned int done = atomicInc(ticket, gridDim.x - 1);   // wraps to 0 at the end
-        t.misc[1] = (done == gridDim.x - 1) ? 1 : 0;
+        const unsigned int done = atomicInc(ticket, (unsigned int)nslots - 1);   // wraps to 0
+        t.misc[1] = (done == (unsigned int)nslots - 1) ? 1 : 0;
     }
     __syncthreads();
     const bool last = t.misc[1] != 0;
     if (last) __threadfence();
     return last;
+}
+
+// One slot per CTA of the grid.
+__device__ __forceinline__ bool topk_publish(TopK& t, int k, Cand* cand, unsigned int* ticket)
+{
+    return topk_publish_slot(t, k, cand, blockIdx.x, gridDim.x, ticket);
 }
 
 // In the last CTA: merge the m published candidates into slots [0, k).
