@@ -243,6 +243,15 @@ int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int 
                  int n_candidates, float* dist, int32_t* cand, void* stream);
 
 /*
+ * db_stage_times -- GPU milliseconds of the stages of the handle's last
+ * embedding-mode db_query_batch group: ms[0] patient thresholding, ms[1]
+ * query embeddings, ms[2] tensor-core distances, ms[3] candidate selection,
+ * ms[4] exact re-ranking.  n <= 5 values are written; DBQ_ESTATE if no such
+ * batch has run.
+ */
+int db_stage_times(dbq_db* db, float* ms, int n);
+
+/*
  * db_get_embeddings -- copy the embeddings of entries [first, first+count):
  * bf16 [count][2][d] (uint16 bit patterns), e4m3 [count][2][d] codes, scale
  * [count][2], norm_bf16 and norm_fp8 [count][2] (squared norms of the

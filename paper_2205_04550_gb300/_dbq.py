@@ -87,6 +87,7 @@ _SIGS = [
                                     ctypes.c_int, _P, _P, _P]),
     ("db_get_embeddings", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P,
                                          _P]),
+    ("db_stage_times", ctypes.c_int, [_P, _P, ctypes.c_int]),
     ("db_scan_packed_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                               ctypes.c_int, _P, _P]),
     ("db_destroy", ctypes.c_int, [_P]),
@@ -272,6 +273,14 @@ def db_get_embeddings(db: int, first: int, count: int, bf16=None, e4m3=None, sca
                       norm_bf16=None, norm_fp8=None, stream=None):
     _check(load().db_get_embeddings(db, first, count, _ptr(bf16), _ptr(e4m3), _ptr(scale),
                                     _ptr(norm_bf16), _ptr(norm_fp8), _stream(stream)))
+
+
+def db_stage_times(db: int) -> dict:
+    """GPU ms per stage of the handle's last embedding-mode batch."""
+    ms = np.zeros(5, dtype=np.float32)
+    _check(load().db_stage_times(db, ms.ctypes.data, 5))
+    keys = ("patients", "query_embed", "gemm", "select", "rerank")
+    return dict(zip(keys, (float(x) for x in ms)))
 
 
 def db_scan_packed_noalloc(planes, sizes, n: int, stride_words: int, patient_planes,

@@ -137,6 +137,8 @@ struct dbq_db {
     dbq::Hit* bhits = nullptr;      // [bq][bk] device
     dbq::Hit* bhits_host = nullptr; // pinned
     int* bstatus = nullptr;         // device status of the tensor-core kernel
+    cudaEvent_t ev[6] = {};         // stage boundaries of the last embedding batch
+    bool ev_valid = false;
     bool prepared = false;          // a patient sits in pplanes/pcount
     float prep_t1 = 0.f, prep_t2 = 0.f;
     int grid = 1;
@@ -177,6 +179,8 @@ struct dbq_db {
         cudaFree(bhits);
         cudaFreeHost(bhits_host);
         cudaFree(bstatus);
+        for (cudaEvent_t e : ev)
+            if (e) cudaEventDestroy(e);
     }
 };
 
@@ -430,12 +434,26 @@ int prepare_batch(dbq_db* db, int nq, const void* const* patients, int kind, flo
 
 // Prefilter for the nq prepared patients: embeddings, tensor-core distances,
 // candidate selection into bdist / bcand.
+void mark(dbq_db* db, int i, cudaStream_t s)
+{
+    if (!db->ev[0]) {
+        for (cudaEvent_t& e : db->ev)
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                cudaGetLastError();
+                e = nullptr;
+            }
+    }
+    if (db->ev[i]) cudaEventRecord(db->ev[i], s);
+}
+
 int run_prefilter(dbq_db* db, int nq, int fp8, int c, cudaStream_t s)
 {
+    mark(db, 1, s);
     cudaError_t err = dbq::launch_embed(db->bplanes, nq, db->wp, db->nx, db->ny, db->nz,
                                         db->bq_bf16, db->bq_f8, db->bq_scale, db->bq_nb,
                                         db->bq_nf, s);
     if (err != cudaSuccess) return cuda_fail(err, "query embedding launch");
+    mark(db, 2, s);
     dbq::GemmArgs g;
     g.e_bf16 = db->emb_bf16;
     g.e_f8 = db->emb_f8;
@@ -452,10 +470,12 @@ int run_prefilter(dbq_db* db, int nq, int fp8, int c, cudaStream_t s)
     g.status = db->bstatus;
     err = dbq::launch_prefilter_gemm(g, fp8, db->grid, s);
     if (err != cudaSuccess) return cuda_fail(err, "prefilter GEMM launch");
+    mark(db, 3, s);
     if (c > 0) {
         err = dbq::launch_select_smallest(db->bdist, nq, db->n, c, db->bcand, s);
         if (err != cudaSuccess) return cuda_fail(err, "candidate selection launch");
     }
+    mark(db, 4, s);
     return DBQ_OK;
 }
 
@@ -941,6 +961,7 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
                     if (rc) return rc;
                     pp[q] = patients[qi];
                 }
+                mark(db, 0, s);
                 rc = prepare_batch(db, gn, pp.data(), kind, db->t1, db->t2, s);
                 if (!rc) rc = run_prefilter(db, gn, mode == DBQ_MODE_EMBED_FP8, n_candidates, s);
                 if (rc) return rc;
@@ -963,6 +984,8 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
                 r.hits = db->bhits;
                 cudaError_t err = dbq::launch_rerank(r, s);
                 if (err != cudaSuccess) return cuda_fail(err, "re-rank launch");
+                mark(db, 5, s);
+                db->ev_valid = db->ev[0] != nullptr;
             }
             DBQ_CUDA(cudaMemcpyAsync(db->bhits_host, db->bhits, (size_t)gn * k * sizeof(dbq::Hit),
                                      cudaMemcpyDeviceToHost, s));
@@ -988,6 +1011,20 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
             }
         }
         i = j;
+    }
+    return DBQ_OK;
+}
+
+int db_stage_times(dbq_db* db, float* ms, int n)
+{
+    if (!db || !ms) return fail(DBQ_EINVAL, "NULL pointer argument");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (!db->ev_valid) return fail(DBQ_ESTATE, "no embedding batch has run on this handle");
+    DeviceGuard guard(db->device);
+    for (int i = 0; i < n && i < 5; ++i) {
+        float t = 0.f;
+        DBQ_CUDA(cudaEventElapsedTime(&t, db->ev[i], db->ev[i + 1]));
+        ms[i] = t;
     }
     return DBQ_OK;
 }
