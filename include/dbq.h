@@ -79,6 +79,13 @@ enum dbq_storage {
 /* db_create flags. */
 #define DBQ_FLAG_EMBED 1u  /* also build the prefilter embeddings (see db_query_batch) */
 
+/* Options of db_set_option. */
+enum dbq_option {
+    DBQ_OPT_SPARSE = 1   /* 1: exact scans of a bit-packed database read only the
+                            words where the patient's mask is non-zero (exact
+                            counts, fewer bytes); 0 (default): read every word */
+};
+
 /* Query modes of db_query_batch. */
 enum dbq_mode {
     DBQ_MODE_EXACT = 0,       /* the brute-force loop over every entry           */
@@ -241,6 +248,26 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
  */
 int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int mode,
                  int n_candidates, float* dist, int32_t* cand, void* stream);
+
+/*
+ * db_set_option -- set a per-handle option (enum dbq_option).
+ * DBQ_OPT_SPARSE: |P_k n E_k| only involves the voxels of the patient's
+ * masks (the Dice numerator, Section 2.3), so with value 1 every exact scan
+ * and every re-ranking of a bit-packed database lists the patient's non-zero
+ * 64-byte granules first and reads only those words of each entry.  Results
+ * are identical; the bytes read per entry shrink to the patient's support.
+ * Ignored by half-precision databases (their mask sizes are computed at
+ * query time from every voxel).
+ */
+int db_set_option(dbq_db* db, int option, int64_t value);
+
+/*
+ * db_last_support -- with DBQ_OPT_SPARSE, the lengths (in 16-byte words) of
+ * the support lists of the last patient prepared by a single-patient call:
+ * out[0] plane 1, out[1] plane 2.  Bytes read per entry by the sparse scan =
+ * 16 * (out[0] + out[1]).  DBQ_ESTATE without such a patient.
+ */
+int db_last_support(dbq_db* db, int64_t out[2]);
 
 /*
  * db_stage_times -- GPU milliseconds of the stages of the handle's last

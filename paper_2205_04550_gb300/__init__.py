@@ -15,12 +15,14 @@ from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_MODE_EMBED_BF
                    DbqError, db_build_masks, db_create, db_destroy, db_get_embeddings,
                    db_get_masks, db_info, db_last_error, db_load_volumes, db_prefilter,
                    db_prepare_patient, db_query, db_query_async, db_query_batch,
-                   db_query_prepared, db_scan_counts, db_scan_packed_noalloc)
+                   db_query_prepared, db_scan_counts, db_scan_packed_noalloc, db_set_option,
+                   db_stage_times, DBQ_OPT_SPARSE)
 
 __all__ = ["Database", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_F16", "DBQ_BITS",
            "DBQ_STORE_BITS", "DBQ_STORE_F16", "DBQ_FLAG_EMBED", "DBQ_MODE_EXACT",
            "DBQ_MODE_EMBED_BF16", "DBQ_MODE_EMBED_FP8", "db_query_batch", "db_prefilter",
-           "db_get_embeddings", "db_scan_packed_noalloc", "db_create", "db_load_volumes",
+           "db_get_embeddings", "db_scan_packed_noalloc", "db_set_option", "db_stage_times",
+           "DBQ_OPT_SPARSE", "db_create", "db_load_volumes",
            "db_build_masks", "db_query", "db_query_async", "db_prepare_patient",
            "db_query_prepared", "db_scan_counts", "db_get_masks",
            "db_info", "db_destroy", "db_last_error"]
@@ -67,6 +69,10 @@ class Database:
         sizes = np.zeros((count, 2), dtype=np.uint32)
         db_get_masks(self.handle, first, count, planes, sizes)
         return planes, sizes
+
+    def set_sparse(self, on: bool = True):
+        """Exact scans read only the patient's support (identical results)."""
+        db_set_option(self.handle, DBQ_OPT_SPARSE, 1 if on else 0)
 
     def embeddings(self, first: int, count: int):
         """-> dict of bf16 bits [count,2,d] uint16, e4m3 codes [count,2,d] uint8,

@@ -33,6 +33,8 @@ DBQ_STORE_F16 = 1
 
 DBQ_FLAG_EMBED = 1
 
+DBQ_OPT_SPARSE = 1
+
 DBQ_MODE_EXACT = 0
 DBQ_MODE_EMBED_BF16 = 1
 DBQ_MODE_EMBED_FP8 = 2
@@ -88,6 +90,8 @@ _SIGS = [
     ("db_get_embeddings", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P,
                                          _P]),
     ("db_stage_times", ctypes.c_int, [_P, _P, ctypes.c_int]),
+    ("db_set_option", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
+    ("db_last_support", ctypes.c_int, [_P, _P]),
     ("db_scan_packed_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                               ctypes.c_int, _P, _P]),
     ("db_destroy", ctypes.c_int, [_P]),
@@ -273,6 +277,17 @@ def db_get_embeddings(db: int, first: int, count: int, bf16=None, e4m3=None, sca
                       norm_bf16=None, norm_fp8=None, stream=None):
     _check(load().db_get_embeddings(db, first, count, _ptr(bf16), _ptr(e4m3), _ptr(scale),
                                     _ptr(norm_bf16), _ptr(norm_fp8), _stream(stream)))
+
+
+def db_set_option(db: int, option: int, value: int):
+    _check(load().db_set_option(db, option, value))
+
+
+def db_last_support(db: int):
+    """Support-list lengths (16-byte words) of the last sparse patient."""
+    out = np.zeros(2, dtype=np.int64)
+    _check(load().db_last_support(db, out.ctypes.data))
+    return int(out[0]), int(out[1])
 
 
 def db_stage_times(db: int) -> dict:

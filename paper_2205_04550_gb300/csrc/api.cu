@@ -139,6 +139,11 @@ struct dbq_db {
     int* bstatus = nullptr;         // device status of the tensor-core kernel
     cudaEvent_t ev[6] = {};         // stage boundaries of the last embedding batch
     bool ev_valid = false;
+    bool sparse = false;            // DBQ_OPT_SPARSE
+    uint32_t* plist = nullptr;      // [2][wp4] patient support lists
+    uint32_t* plen = nullptr;       // [2]
+    uint32_t* bsup = nullptr;       // [bq][2][wp4]
+    uint32_t* bsuplen = nullptr;    // [bq][2]
     bool prepared = false;          // a patient sits in pplanes/pcount
     float prep_t1 = 0.f, prep_t2 = 0.f;
     int grid = 1;
@@ -179,6 +184,10 @@ struct dbq_db {
         cudaFree(bhits);
         cudaFreeHost(bhits_host);
         cudaFree(bstatus);
+        cudaFree(plist);
+        cudaFree(plen);
+        cudaFree(bsup);
+        cudaFree(bsuplen);
         for (cudaEvent_t e : ev)
             if (e) cudaEventDestroy(e);
     }
@@ -243,6 +252,10 @@ int prepare_patient(dbq_db* db, const void* patient, int kind, float t1, float t
         err = dbq::launch_pack(src, kind == DBQ_F16, 1, db->v, db->wp, t1, t2, db->pplanes,
                                db->pcount, s);
     if (err != cudaSuccess) return cuda_fail(err, "patient packing");
+    if (db->sparse && db->storage == DBQ_STORE_BITS) {
+        err = dbq::launch_support(db->pplanes, 1, db->wp4, db->plist, db->plen, s);
+        if (err != cudaSuccess) return cuda_fail(err, "support list launch");
+    }
     db->prepared = true;
     db->prep_t1 = t1;
     db->prep_t2 = t2;
@@ -290,6 +303,8 @@ int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaSt
         a.ticket = db->ticket;
         a.hits = hits;
         a.counts_out = counts_out;
+        a.sup_list = db->sparse ? db->plist : nullptr;
+        a.sup_len = db->sparse ? db->plen : nullptr;
         cudaError_t err = dbq::launch_scan_packed(a, db->grid, s);
         if (err != cudaSuccess) return cuda_fail(err, "scan_packed launch");
         return DBQ_OK;
@@ -350,6 +365,8 @@ int ensure_batch(dbq_db* db, int k)
         if (!rc) rc = grow(db, &db->bhits, q * kMaxK * sizeof(dbq::Hit), "batch hits");
         if (!rc) rc = grow(db, &db->btickets, q * sizeof(unsigned int), "batch tickets");
         if (!rc) rc = grow(db, &db->bstatus, 16, "status");
+        if (!rc) rc = grow(db, &db->bsup, q * 2 * db->wp4 * 4, "batch support lists");
+        if (!rc) rc = grow(db, &db->bsuplen, q * 2 * 4, "batch support lengths");
         if (!rc && db->dims) {
             const size_t rows = q * 2;
             rc = grow(db, &db->bq_bf16, rows * db->dims * 2, "query bf16 embeddings");
@@ -427,6 +444,10 @@ int prepare_batch(dbq_db* db, int nq, const void* const* patients, int kind, flo
         cudaError_t err = dbq::launch_pack_ptrs(db->bptrs, kind == DBQ_F16, nq, db->v, db->wp, t1,
                                                 t2, db->bplanes, db->bpcount, s);
         if (err != cudaSuccess) return cuda_fail(err, "batch patient packing");
+    }
+    if (db->sparse && db->storage == DBQ_STORE_BITS) {
+        cudaError_t err = dbq::launch_support(db->bplanes, nq, db->wp4, db->bsup, db->bsuplen, s);
+        if (err != cudaSuccess) return cuda_fail(err, "support list launch");
     }
     // the pointer array is pageable: the copy above has been staged already
     return DBQ_OK;
@@ -590,6 +611,8 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
     dbq::scan_packed_chunking(db->wp4, &db->chunk4, &db->nchunks);
     if (!rc) rc = dev_alloc(db, &db->pplanes, (size_t)2 * db->wp * sizeof(uint32_t), "patient");
     if (!rc) rc = dev_alloc(db, &db->pcount, 4 * sizeof(uint32_t), "patient sizes");
+    if (!rc) rc = dev_alloc(db, &db->plist, (size_t)2 * db->wp4 * sizeof(uint32_t), "support lists");
+    if (!rc) rc = dev_alloc(db, &db->plen, 4 * sizeof(uint32_t), "support lengths");
     if (!rc)
         rc = dev_alloc(db, &db->cand, (size_t)db->grid * kMaxK * sizeof(dbq::Cand),
                        "candidate lists");
@@ -982,6 +1005,8 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
                 r.scratch = db->brr;
                 r.tickets = db->btickets;
                 r.hits = db->bhits;
+                r.sup_lists = db->sparse ? db->bsup : nullptr;
+                r.sup_lens = db->sparse ? db->bsuplen : nullptr;
                 cudaError_t err = dbq::launch_rerank(r, s);
                 if (err != cudaSuccess) return cuda_fail(err, "re-rank launch");
                 mark(db, 5, s);
@@ -1012,6 +1037,33 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
         }
         i = j;
     }
+    return DBQ_OK;
+}
+
+int db_set_option(dbq_db* db, int option, int64_t value)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (option == DBQ_OPT_SPARSE) {
+        if (value != 0 && value != 1) return fail(DBQ_EINVAL, "DBQ_OPT_SPARSE takes 0 or 1");
+        db->sparse = value == 1;
+        db->prepared = false;   // a prepared patient has no support lists yet
+        return DBQ_OK;
+    }
+    return fail(DBQ_EINVAL, "unknown option %d", option);
+}
+
+int db_last_support(dbq_db* db, int64_t out[2])
+{
+    if (!db || !out) return fail(DBQ_EINVAL, "NULL pointer argument");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (!db->sparse || !db->prepared || db->storage != DBQ_STORE_BITS)
+        return fail(DBQ_ESTATE, "no sparse patient prepared");
+    DeviceGuard guard(db->device);
+    uint32_t len[2] = {0, 0};
+    DBQ_CUDA(cudaMemcpy(len, db->plen, sizeof len, cudaMemcpyDeviceToHost));
+    out[0] = len[0];
+    out[1] = len[1];
     return DBQ_OK;
 }
 

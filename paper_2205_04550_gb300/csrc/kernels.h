@@ -31,6 +31,12 @@ cudaError_t launch_to_f16(const float* src, int64_t n, uint16_t* dst, cudaStream
 cudaError_t launch_import_bits(const uint32_t* src, int64_t words, int64_t v, int64_t wp,
                                uint32_t* planes, uint32_t* pcount, cudaStream_t stream);
 
+// Support lists of nq patients' planes [nq][2][wp4 uint4] -> lists
+// [nq][2][wp4] (16-byte word offsets of non-zero 64-byte granules) and
+// lens [nq][2].
+cudaError_t launch_support(const uint32_t* planes, int nq, int wp4, uint32_t* lists,
+                           uint32_t* lens, cudaStream_t stream);
+
 // Arguments of the fused exact packed scan.
 struct ScanPackedArgs {
     const uint4* planes;      // [n][2][wp4] database bit planes
@@ -46,6 +52,8 @@ struct ScanPackedArgs {
     unsigned int* ticket;     // scratch counter, 0 between launches
     Hit* hits;                // [k] output (device), may be null when counts_out is set
     uint32_t* counts_out;     // [n][4] per-entry (I1, I2, E1, E2), or null
+    const uint32_t* sup_list; // [2][wp4] patient support lists, or null for the dense scan
+    const uint32_t* sup_len;  // [2]
 };
 
 // Grid size (CTAs) the scan uses on this device, and its shared memory bytes.
@@ -134,6 +142,8 @@ struct RerankArgs {
     Cand* scratch;              // [nq][slices][k]
     unsigned int* tickets;      // [nq]
     Hit* hits;                  // [nq][k]
+    const uint32_t* sup_lists;  // [nq][2][wp4] support lists, or null (dense)
+    const uint32_t* sup_lens;   // [nq][2]
 };
 cudaError_t launch_rerank(const RerankArgs& a, cudaStream_t stream);
 

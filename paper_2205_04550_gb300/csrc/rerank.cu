@@ -20,7 +20,7 @@ namespace {
 
 constexpr int kGroupMax = 1024;
 
-template <int U, int EPI>
+template <int U, int EPI, bool kSparse>
 __global__ void __launch_bounds__(kScanThreads, 1)
 rerank_kernel(const RerankArgs a)
 {
@@ -43,8 +43,16 @@ rerank_kernel(const RerankArgs a)
         topk_init(tk);
         for (int i = tid; i < 2 * kGroupMax; i += kScanThreads) icnt[i] = 0u;
         __syncthreads();
-        if (gn > 0)
-            count_group<U, EPI>(a.planes, a.wp4, a.chunk4, a.nchunks, patient, list, 0, gn, icnt);
+        if (gn > 0) {
+            Support sup;
+            if (kSparse) {
+                sup.list1 = a.sup_lists + (int64_t)q * 2 * a.wp4;
+                sup.list2 = sup.list1 + a.wp4;
+                sup.len = a.sup_lens + 2 * q;
+            }
+            count_group<U, EPI, kSparse>(a.planes, a.wp4, a.chunk4, a.nchunks, patient, list, 0,
+                                         gn, icnt, sup);
+        }
         __syncthreads();
         for (int i = tid; i < gn; i += kScanThreads) {
             const int64_t e = list[i];
@@ -94,8 +102,12 @@ cudaError_t launch_rerank(const RerankArgs& a, cudaStream_t stream)
         kern<<<grid, kScanThreads, smem, stream>>>(a);
         return cudaGetLastError();
     };
-    if (a.chunk4 <= kScanThreads) return run(rerank_kernel<1, 4>);
-    return run(rerank_kernel<2, 2>);
+    if (a.sup_lists) {
+        if (a.chunk4 <= kScanThreads) return run(rerank_kernel<1, 4, true>);
+        return run(rerank_kernel<2, 2, true>);
+    }
+    if (a.chunk4 <= kScanThreads) return run(rerank_kernel<1, 4, false>);
+    return run(rerank_kernel<2, 2, false>);
 }
 
 }  // namespace dbq

@@ -17,27 +17,49 @@ namespace dbq {
 
 constexpr int kScanThreads = 1024;
 
+// Patient support lists: for plane k, the 16-byte word offsets of the
+// patient's non-zero 64-byte granules (four consecutive offsets per
+// granule, ascending), and their count.  Words outside the list are zero in
+// the patient, so they add nothing to |P_k n E_k| and need not be read.
+struct Support {
+    const uint32_t* list1;   // [wp4] offsets into plane 1
+    const uint32_t* list2;   // [wp4] offsets into plane 2
+    const uint32_t* len;     // [2]  list lengths
+};
+
 // icnt[2 * i + k] += I_k of entry i of the group (i < gn); the group's
-// entries are list[g0 + i] when `list` is given, else g0 + i.  icnt must be
-// zeroed and visible (barrier) before the call; the call ends without a
-// barrier.
-template <int U, int EPI>
+// entries are list[g0 + i] when `list` is given, else g0 + i.  With kSparse
+// the positions visited are the patient's support lists instead of all
+// words.  icnt must be zeroed and visible (barrier) before the call; the call
+// ends without a barrier.
+template <int U, int EPI, bool kSparse = false>
 __device__ __forceinline__ void count_group(const uint4* __restrict__ planes, int wp4, int chunk4,
                                             int nchunks, const uint4* __restrict__ patient,
                                             const int32_t* __restrict__ list, int64_t g0, int gn,
-                                            uint32_t* icnt)
+                                            uint32_t* icnt, Support sup = Support{})
 {
     const int tid = threadIdx.x;
     const int lane = tid & 31;
+    int len1 = wp4, len2 = wp4;
+    if (kSparse) {
+        len1 = (int)sup.len[0];
+        len2 = (int)sup.len[1];
+        const int longest = len1 > len2 ? len1 : len2;
+        nchunks = (longest + chunk4 - 1) / chunk4;
+    }
     for (int c = 0; c < nchunks; ++c) {
         const int c0 = c * chunk4;
-        const int clen = (wp4 - c0) < chunk4 ? (wp4 - c0) : chunk4;
+        const int clen1 = (len1 - c0) < chunk4 ? (len1 - c0) : chunk4;
+        const int clen2 = (len2 - c0) < chunk4 ? (len2 - c0) : chunk4;
         uint4 pa[U], pb[U];
+        uint32_t o1[U], o2[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int j = tid + u * kScanThreads;
-            pa[u] = (j < clen) ? patient[c0 + j] : make_uint4(0, 0, 0, 0);
-            pb[u] = (j < clen) ? patient[wp4 + c0 + j] : make_uint4(0, 0, 0, 0);
+            o1[u] = (j < clen1) ? (kSparse ? sup.list1[c0 + j] : (uint32_t)(c0 + j)) : 0u;
+            o2[u] = (j < clen2) ? (kSparse ? sup.list2[c0 + j] : (uint32_t)(c0 + j)) : 0u;
+            pa[u] = (j < clen1) ? patient[o1[u]] : make_uint4(0, 0, 0, 0);
+            pb[u] = (j < clen2) ? patient[wp4 + o2[u]] : make_uint4(0, 0, 0, 0);
         }
         for (int i0 = 0; i0 < gn; i0 += EPI) {
             uint4 x[EPI][U], y[EPI][U];
@@ -46,18 +68,13 @@ __device__ __forceinline__ void count_group(const uint4* __restrict__ planes, in
                 const bool ev = (i0 + q) < gn;
                 int64_t e = g0 + i0 + q;
                 if (list && ev) e = list[e];
-                const uint4* p0 = planes + e * 2 * wp4 + c0;
+                const uint4* p0 = planes + e * 2 * wp4;
                 const uint4* p1 = p0 + wp4;
 #pragma unroll
                 for (int u = 0; u < U; ++u) {
                     const int j = tid + u * kScanThreads;
-                    if (ev && j < clen) {
-                        x[q][u] = ld_stream(p0 + j);
-                        y[q][u] = ld_stream(p1 + j);
-                    } else {
-                        x[q][u] = make_uint4(0, 0, 0, 0);
-                        y[q][u] = make_uint4(0, 0, 0, 0);
-                    }
+                    x[q][u] = (ev && j < clen1) ? ld_stream(p0 + o1[u]) : make_uint4(0, 0, 0, 0);
+                    y[q][u] = (ev && j < clen2) ? ld_stream(p1 + o2[u]) : make_uint4(0, 0, 0, 0);
                 }
             }
 #pragma unroll

@@ -34,7 +34,7 @@ constexpr int kThreads = kScanThreads;
 constexpr int kGroup = 1024;        // entries whose counters live in shared memory
 constexpr int kMaxChunk4 = 2048;    // uint4 per plane per chunk = 2 per thread
 
-template <int U, int EPI>
+template <int U, int EPI, bool kSparse>
 __global__ void __launch_bounds__(kThreads, 1)
 scan_packed_kernel(const ScanPackedArgs a)
 {
@@ -56,8 +56,12 @@ scan_packed_kernel(const ScanPackedArgs a)
         const int gn = (int)((e_end - g0) < kGroup ? (e_end - g0) : kGroup);
         for (int i = tid; i < 2 * kGroup; i += kThreads) icnt[i] = 0u;
         __syncthreads();
-        count_group<U, EPI>(a.planes, a.wp4, a.chunk4, a.nchunks, a.patient, nullptr, g0, gn,
-                            icnt);
+        Support sup;
+        sup.list1 = a.sup_list;
+        sup.list2 = a.sup_list + a.wp4;
+        sup.len = a.sup_len;
+        count_group<U, EPI, kSparse>(a.planes, a.wp4, a.chunk4, a.nchunks, a.patient, nullptr, g0,
+                                     gn, icnt, sup);
         __syncthreads();   // the group's counters are complete
         for (int i = tid; i < gn; i += kThreads) {
             const int64_t e = g0 + i;
@@ -128,8 +132,12 @@ cudaError_t launch_scan_packed(const ScanPackedArgs& a, int grid, cudaStream_t s
         kern<<<grid, kThreads, smem, stream>>>(a);
         return cudaGetLastError();
     };
-    if (a.chunk4 <= kThreads) return run(scan_packed_kernel<1, 4>);
-    return run(scan_packed_kernel<2, 2>);
+    if (a.sup_list) {
+        if (a.chunk4 <= kThreads) return run(scan_packed_kernel<1, 4, true>);
+        return run(scan_packed_kernel<2, 2, true>);
+    }
+    if (a.chunk4 <= kThreads) return run(scan_packed_kernel<1, 4, false>);
+    return run(scan_packed_kernel<2, 2, false>);
 }
 
 }  // namespace dbq

@@ -90,5 +90,12 @@ def test_exact_query_50000_entries_128cube_sampled(torch):
         np.testing.assert_array_equal(hit_counts, counts[idx])
         theta = synth.entry_params(shape, synth.DB_SEED, idx)
         np.testing.assert_array_equal(params, theta)
+        # the sparse scan (patient support only) gives the identical result
+        db.set_sparse(True)
+        s_hits, _ = db.query(patient, k)
+        s_counts, _ = db.scan_counts(patient)
+        db.set_sparse(False)
+        assert s_hits.tobytes() == hits.tobytes()
+        np.testing.assert_array_equal(s_counts, counts)
     finally:
         db.close()

@@ -1,0 +1,105 @@
+"""The sparse exact scan (DBQ_OPT_SPARSE): reading only the words where the
+patient's masks are non-zero must give exactly the counts, scores and order
+of the full loop (Section 2.3: the Dice numerator only involves the
+patient's voxels).  Bit-exact against the oracle and against the dense scan."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_04550_gb300 import (DBQ_MODE_EMBED_BF16, DBQ_STORE_BITS, Database, _dbq,
+                                    synth)
+from tests._gpu_helpers import assert_hits_equal, random_db
+
+pytestmark = pytest.mark.gpu
+
+T1, T2 = np.float32(0.6), np.float32(0.25)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    from paper_2205_04550_gb300 import build
+    build.build()
+    return _t
+
+
+CASES = [((1, 1, 1), 5, 5), ((9, 10, 11), 153, 10), ((17, 5, 3), 300, 300),
+         ((33, 31, 30), 500, 7), ((64, 64, 64), 160, 12), ((128, 32, 32), 90, 9)]
+
+
+def _sparse_patient(shape, seed, frac=0.1):
+    """A patient whose masks cover a small box of the grid."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    p = np.zeros((nz, ny, nx), np.float32)
+    z0, y0, x0 = (rng.integers(0, max(1, d // 2)) for d in (nz, ny, nx))
+    dz, dy, dx = (max(1, int(d * frac ** (1 / 3))) for d in (nz, ny, nx))
+    p[z0:z0 + dz, y0:y0 + dy, x0:x0 + dx] = rng.random((min(dz, nz - z0), min(dy, ny - y0),
+                                                         min(dx, nx - x0)), dtype=np.float32)
+    return p
+
+
+@pytest.mark.parametrize("shape,n,k", CASES)
+def test_sparse_equals_oracle(torch, shape, n, k):
+    vols, _ = random_db(shape, n, seed=n)
+    with Database(shape, n, DBQ_STORE_BITS, T1, T2) as db:
+        db.load(0, vols)
+        db.build()
+        db.set_sparse(True)
+        for seed in range(3):
+            patient = _sparse_patient(shape, seed)
+            ref = oracle.query(vols, patient, T1, T2, k)
+            counts, pcount = db.scan_counts(patient)
+            np.testing.assert_array_equal(counts, ref["all_counts"])
+            hits, _ = db.query(patient, k)
+            assert_hits_equal(hits, ref, k)
+
+
+def test_sparse_empty_and_full_patients(torch):
+    shape = (32, 16, 8)
+    vols, _ = random_db(shape, 200, seed=4)
+    vols[17] = 0.0
+    vols[18] = 0.0
+    with Database(shape, 200, DBQ_STORE_BITS, T1, T2) as db:
+        db.load(0, vols)
+        db.build()
+        db.set_sparse(True)
+        for patient in (np.zeros(shape[::-1], np.float32), np.ones(shape[::-1], np.float32)):
+            ref = oracle.query(vols, patient, T1, T2, 20)
+            hits, _ = db.query(patient, 20)
+            assert_hits_equal(hits, ref, 20)
+            l1, l2 = _dbq.db_last_support(db.handle)
+            words = db.info()["padded_words"] // 4
+            if patient.any():
+                assert l1 == l2 == words
+            else:
+                assert l1 == l2 == 0
+        # an empty patient against empty entries: Dice 1 for both, lowest index first
+        hits, _ = db.query(np.zeros(shape[::-1], np.float32), 2)
+        assert list(hits["index"]) == [17, 18] and hits["score"][0] == 1.0
+
+
+def test_sparse_toggle_and_surrogate(torch):
+    shape = (64, 64, 64)
+    vols, theta = synth.database_np(shape, 300)
+    pats, _ = synth.patients_np(shape, [1, 2, 3])
+    vols[77] = pats[2]
+    with Database(shape, 300, DBQ_STORE_BITS, T1, T2, embed=True) as db:
+        db.load(0, vols)
+        db.build()
+        for p in pats:
+            dense, _ = db.query(p, 25)
+            db.set_sparse(True)
+            sparse, _ = db.query(p, 25)
+            db.set_sparse(False)
+            assert dense.tobytes() == sparse.tobytes()
+            assert_hits_equal(sparse, oracle.query(vols, p, T1, T2, 25), 25)
+        # re-ranking with support lists gives the same hits
+        dense_b, _ = db.query_batch(list(pats), 10, DBQ_MODE_EMBED_BF16, 64)
+        db.set_sparse(True)
+        sparse_b, _ = db.query_batch(list(pats), 10, DBQ_MODE_EMBED_BF16, 64)
+        exact_b, _ = db.query_batch(list(pats), 10)
+        assert dense_b.tobytes() == sparse_b.tobytes()
+        for q in range(3):
+            assert_hits_equal(exact_b[q], oracle.query(vols, pats[q], T1, T2, 10), 10)
+        assert sparse_b[2][0]["index"] == 77
