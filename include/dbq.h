@@ -240,6 +240,35 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
                    void* stream);
 
 /*
+ * Query plans: many exact queries against several bit-packed databases (of
+ * any resolutions) in one persistent launch.  A plan owns the device
+ * workspace for up to `max_queries` queries of k hits each; db_plan_query
+ * only enqueues work (no host synchronisation, no allocation), so it can be
+ * captured into a CUDA graph and replayed.
+ *
+ * db_plan_create  dbs[ndb] must live on one device, be bit-packed and
+ *                 built, and outlive the plan.  1 <= k <= 1024.
+ * db_plan_set     DBQ_PLAN_ITEMS_PER_SM: work items (query slices) per SM
+ *                 of one launch (default 4; chosen by the autotuner).
+ * db_plan_query   patients_dev[nq] device pointers (kind DBQ_F32 / DBQ_F16
+ *                 volumes or DBQ_BITS planes of the query's database),
+ *                 t1/t2 per query or NULL (NaN = build thresholds; others
+ *                 must equal them), hits_dev [nq][k] device output.  Each
+ *                 query honours its database's DBQ_OPT_SPARSE setting.  The
+ *                 plan's host-side tables are rewritten by each call: a call
+ *                 outside stream capture waits until the previous call's
+ *                 tables have been copied to the device.
+ * db_plan_destroy frees the plan (NULL accepted).
+ */
+typedef struct dbq_plan dbq_plan;
+enum dbq_plan_param { DBQ_PLAN_ITEMS_PER_SM = 1 };
+int db_plan_create(dbq_plan** out, dbq_db* const* dbs, int ndb, int max_queries, int k);
+int db_plan_set(dbq_plan* plan, int param, int64_t value);
+int db_plan_query(dbq_plan* plan, const int* db_of_query, int nq, const void* const* patients_dev,
+                  int kind, const float* t1, const float* t2, dbq_hit* hits_dev, void* stream);
+int db_plan_destroy(dbq_plan* plan);
+
+/*
  * db_prefilter -- the prefilter step of db_query_batch alone, for
  * measurement and checking: distances dist [nq][N] (host or device, or
  * NULL) and the n_candidates closest entries per query, ascending, cand

@@ -16,13 +16,15 @@ from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_MODE_EMBED_BF
                    db_get_masks, db_info, db_last_error, db_load_volumes, db_prefilter,
                    db_prepare_patient, db_query, db_query_async, db_query_batch,
                    db_query_prepared, db_scan_counts, db_scan_packed_noalloc, db_set_option,
-                   db_stage_times, DBQ_OPT_SPARSE)
+                   db_stage_times, DBQ_OPT_SPARSE, DBQ_PLAN_ITEMS_PER_SM, db_plan_create,
+                   db_plan_set, db_plan_query, db_plan_destroy)
 
 __all__ = ["Database", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_F16", "DBQ_BITS",
            "DBQ_STORE_BITS", "DBQ_STORE_F16", "DBQ_FLAG_EMBED", "DBQ_MODE_EXACT",
            "DBQ_MODE_EMBED_BF16", "DBQ_MODE_EMBED_FP8", "db_query_batch", "db_prefilter",
            "db_get_embeddings", "db_scan_packed_noalloc", "db_set_option", "db_stage_times",
-           "DBQ_OPT_SPARSE", "db_create", "db_load_volumes",
+           "DBQ_OPT_SPARSE", "DBQ_PLAN_ITEMS_PER_SM", "Plan", "db_plan_create",
+           "db_plan_set", "db_plan_query", "db_plan_destroy", "db_create", "db_load_volumes",
            "db_build_masks", "db_query", "db_query_async", "db_prepare_patient",
            "db_query_prepared", "db_scan_counts", "db_get_masks",
            "db_info", "db_destroy", "db_last_error"]
@@ -105,6 +107,42 @@ class Database:
     def close(self):
         if self.handle:
             db_destroy(self.handle)
+            self.handle = 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Plan:
+    """Many exact queries against several bit-packed databases in one
+    persistent launch (db_plan_*).  ``query`` only enqueues work and can be
+    captured in a CUDA graph; outputs are device buffers of dbq_hit records."""
+
+    def __init__(self, databases, max_queries: int, k: int):
+        self.databases = list(databases)
+        self.max_queries = int(max_queries)
+        self.k = int(k)
+        self.handle = db_plan_create([d.handle for d in self.databases], max_queries, k)
+
+    def set_items_per_sm(self, value: int):
+        db_plan_set(self.handle, DBQ_PLAN_ITEMS_PER_SM, int(value))
+
+    def query(self, db_of_query, patients_dev, hits_dev, kind=None, stream=None, keep=None):
+        db_plan_query(self.handle, db_of_query, patients_dev, hits_dev, kind, stream=stream,
+                      _keep=keep)
+
+    def close(self):
+        if self.handle:
+            db_plan_destroy(self.handle)
             self.handle = 0
 
     def __enter__(self):

@@ -35,6 +35,8 @@ DBQ_FLAG_EMBED = 1
 
 DBQ_OPT_SPARSE = 1
 
+DBQ_PLAN_ITEMS_PER_SM = 1
+
 DBQ_MODE_EXACT = 0
 DBQ_MODE_EMBED_BF16 = 1
 DBQ_MODE_EMBED_FP8 = 2
@@ -92,6 +94,11 @@ _SIGS = [
     ("db_stage_times", ctypes.c_int, [_P, _P, ctypes.c_int]),
     ("db_set_option", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     ("db_last_support", ctypes.c_int, [_P, _P]),
+    ("db_plan_create", ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int]),
+    ("db_plan_set", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
+    ("db_plan_query", ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]),
+    ("db_plan_destroy", ctypes.c_int, [_P]),
     ("db_scan_packed_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                               ctypes.c_int, _P, _P]),
     ("db_destroy", ctypes.c_int, [_P]),
@@ -281,6 +288,37 @@ def db_get_embeddings(db: int, first: int, count: int, bf16=None, e4m3=None, sca
 
 def db_set_option(db: int, option: int, value: int):
     _check(load().db_set_option(db, option, value))
+
+
+def db_plan_create(dbs, max_queries: int, k: int) -> int:
+    h = _P()
+    arr = (ctypes.c_void_p * len(dbs))(*dbs)
+    _check(load().db_plan_create(ctypes.byref(h), arr, len(dbs), max_queries, k))
+    return h.value
+
+
+def db_plan_set(plan: int, param: int, value: int):
+    _check(load().db_plan_set(plan, param, value))
+
+
+def db_plan_query(plan: int, db_of_query, patients_dev, hits_dev, kind: int | None = None,
+                  t1=None, t2=None, stream=None, _keep=None):
+    """Enqueue the plan's persistent exact scan; patients and hits are device
+    memory.  ``_keep`` (a list) receives the argument arrays so a caller that
+    captures the call into a graph can keep them alive."""
+    dq = np.ascontiguousarray(db_of_query, dtype=np.int32)
+    a1 = None if t1 is None else np.ascontiguousarray(t1, dtype=np.float32)
+    a2 = None if t2 is None else np.ascontiguousarray(t2, dtype=np.float32)
+    pa = _ptr_array(patients_dev)
+    if _keep is not None:
+        _keep.extend([dq, a1, a2, pa])
+    _check(load().db_plan_query(plan, dq.ctypes.data, len(patients_dev), pa,
+                                _kind_of(patients_dev[0]) if kind is None else kind,
+                                _ptr(a1), _ptr(a2), _ptr(hits_dev), _stream(stream)))
+
+
+def db_plan_destroy(plan: int):
+    _check(load().db_plan_destroy(plan))
 
 
 def db_last_support(db: int):

@@ -530,6 +530,48 @@ int check_prefilter_args(dbq_db* db, int mode, int c, int k)
 
 }  // namespace
 
+struct dbq_plan {
+    std::vector<dbq_db*> dbs;
+    int device = 0;
+    int maxq = 0, k = 0;
+    int items_per_sm = 4;
+    int sms = 1;
+    int64_t max_wp = 0;
+    int max_slices = 64;
+    uint32_t* planes = nullptr;       // [maxq][2][max_wp]
+    uint32_t* pcount = nullptr;       // [maxq][2]
+    uint32_t* sup = nullptr;          // [maxq][2][max_wp / 4]
+    uint32_t* suplen = nullptr;       // [maxq][2]
+    dbq::Cand* scratch = nullptr;     // [maxq][max_slices][k]
+    unsigned int* tickets = nullptr;  // [maxq]
+    unsigned int* counter = nullptr;
+    dbq::QueryTask* tasks_dev = nullptr;
+    dbq::QueryTask* tasks_host = nullptr;   // pinned
+    int2* items_dev = nullptr;
+    int2* items_host = nullptr;             // pinned
+    const void** ptrs_dev = nullptr;
+    const void** ptrs_host = nullptr;       // pinned
+    cudaEvent_t copied = nullptr;
+    bool copy_pending = false;
+    ~dbq_plan()
+    {
+        cudaFree(planes);
+        cudaFree(pcount);
+        cudaFree(sup);
+        cudaFree(suplen);
+        cudaFree(scratch);
+        cudaFree(tickets);
+        cudaFree(counter);
+        cudaFree(tasks_dev);
+        cudaFreeHost(tasks_host);
+        cudaFree(items_dev);
+        cudaFreeHost(items_host);
+        cudaFree(ptrs_dev);
+        cudaFreeHost(ptrs_host);
+        if (copied) cudaEventDestroy(copied);
+    }
+};
+
 extern "C" {
 
 const char* db_last_error(void) { return g_last_error.c_str(); }
@@ -1078,6 +1120,215 @@ int db_stage_times(dbq_db* db, float* ms, int n)
         DBQ_CUDA(cudaEventElapsedTime(&t, db->ev[i], db->ev[i + 1]));
         ms[i] = t;
     }
+    return DBQ_OK;
+}
+
+int db_plan_create(dbq_plan** out, dbq_db* const* dbs, int ndb, int max_queries, int k)
+{
+    if (!out || !dbs) return fail(DBQ_EINVAL, "NULL pointer argument");
+    *out = nullptr;
+    if (ndb < 1 || max_queries < 1 || max_queries > 65535)
+        return fail(DBQ_EINVAL, "need 1 <= ndb and 1 <= max_queries <= 65535");
+    if (k < 1 || k > kMaxK) return fail(DBQ_ERANGE, "k must be in [1, %d]", kMaxK);
+    dbq_plan* p = new (std::nothrow) dbq_plan;
+    if (!p) return fail(DBQ_ENOMEM, "host allocation failed");
+    p->maxq = max_queries;
+    p->k = k;
+    for (int i = 0; i < ndb; ++i) {
+        dbq_db* db = dbs[i];
+        if (!db) { delete p; return fail(DBQ_EINVAL, "database %d is NULL", i); }
+        std::lock_guard<std::mutex> lock(db->mu);
+        if (db->storage != DBQ_STORE_BITS || !db->built) {
+            delete p;
+            return fail(DBQ_ESTATE, "plans need built bit-packed databases (database %d)", i);
+        }
+        if (i == 0) p->device = db->device;
+        if (db->device != p->device) {
+            delete p;
+            return fail(DBQ_EINVAL, "all databases of a plan must be on one device");
+        }
+        if (k > db->n) { delete p; return fail(DBQ_ERANGE, "k exceeds database %d size", i); }
+        p->max_wp = std::max<int64_t>(p->max_wp, db->wp);
+        p->dbs.push_back(db);
+    }
+    DeviceGuard guard(p->device);
+    if (!guard.ok) { delete p; return fail(DBQ_ECUDA, "cannot select device"); }
+    cudaDeviceGetAttribute(&p->sms, cudaDevAttrMultiProcessorCount, p->device);
+    const size_t q = (size_t)max_queries;
+    const size_t max_items = q * p->max_slices;
+    auto dalloc = [&](auto** ptr, size_t bytes) -> bool {
+        if (cudaMalloc(reinterpret_cast<void**>(ptr), bytes ? bytes : 16) != cudaSuccess) {
+            cudaGetLastError();
+            *ptr = nullptr;
+            return false;
+        }
+        return true;
+    };
+    auto halloc = [&](auto** ptr, size_t bytes) -> bool {
+        if (cudaMallocHost(reinterpret_cast<void**>(ptr), bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *ptr = nullptr;
+            return false;
+        }
+        return true;
+    };
+    bool ok = dalloc(&p->planes, q * 2 * p->max_wp * 4) && dalloc(&p->pcount, q * 2 * 4) &&
+              dalloc(&p->sup, q * 2 * (p->max_wp / 4) * 4) && dalloc(&p->suplen, q * 2 * 4) &&
+              dalloc(&p->scratch, q * p->max_slices * k * sizeof(dbq::Cand)) &&
+              dalloc(&p->tickets, q * 4) && dalloc(&p->counter, 16) &&
+              dalloc(&p->tasks_dev, q * sizeof(dbq::QueryTask)) &&
+              halloc(&p->tasks_host, q * sizeof(dbq::QueryTask)) &&
+              dalloc(&p->items_dev, max_items * sizeof(int2)) &&
+              halloc(&p->items_host, max_items * sizeof(int2)) &&
+              dalloc(&p->ptrs_dev, q * sizeof(void*)) && halloc(&p->ptrs_host, q * sizeof(void*));
+    if (!ok) {
+        delete p;
+        return fail(DBQ_ENOMEM, "plan allocation failed");
+    }
+    cudaError_t err = cudaMemset(p->tickets, 0, q * 4);
+    if (err == cudaSuccess) err = cudaEventCreateWithFlags(&p->copied, cudaEventDisableTiming);
+    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) {
+        delete p;
+        return cuda_fail(err, "plan initialisation");
+    }
+    *out = p;
+    return DBQ_OK;
+}
+
+int db_plan_set(dbq_plan* plan, int param, int64_t value)
+{
+    if (!plan) return fail(DBQ_EINVAL, "plan is NULL");
+    if (param == DBQ_PLAN_ITEMS_PER_SM) {
+        if (value < 1 || value > 64) return fail(DBQ_EINVAL, "items per SM must be in [1, 64]");
+        plan->items_per_sm = (int)value;
+        return DBQ_OK;
+    }
+    return fail(DBQ_EINVAL, "unknown plan parameter %d", param);
+}
+
+int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const* patients_dev,
+                  int kind, const float* t1, const float* t2, dbq_hit* hits_dev, void* stream)
+{
+    if (!p || !db_of_query || !patients_dev || !hits_dev)
+        return fail(DBQ_EINVAL, "NULL pointer argument");
+    if (nq < 1 || nq > p->maxq) return fail(DBQ_ERANGE, "nq must be in [1, %d]", p->maxq);
+    if (kind != DBQ_F32 && kind != DBQ_F16 && kind != DBQ_BITS)
+        return fail(DBQ_EINVAL, "unknown patient kind %d", kind);
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", p->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    DBQ_CUDA(cudaStreamIsCapturing(s, &cap));
+    if (p->copy_pending && cap == cudaStreamCaptureStatusNone) {
+        DBQ_CUDA(cudaEventSynchronize(p->copied));   // host tables free for reuse
+        p->copy_pending = false;
+    }
+    const int ndb = (int)p->dbs.size();
+    for (int q = 0; q < nq; ++q) {
+        const int d = db_of_query[q];
+        if (d < 0 || d >= ndb) return fail(DBQ_EINVAL, "query %d names database %d", q, d);
+        if (!patients_dev[q]) return fail(DBQ_EINVAL, "patient %d is NULL", q);
+        dbq_db* db = p->dbs[d];
+        float a = t1 ? t1[q] : NAN, b = t2 ? t2[q] : NAN;
+        if ((!std::isnan(a) && a != db->t1) || (!std::isnan(b) && b != db->t2))
+            return fail(DBQ_EINVAL, "query %d: thresholds differ from database %d's", q, d);
+    }
+    // group the queries by database; each group's patient slots are contiguous
+    std::vector<int> order((size_t)nq);
+    for (int q = 0; q < nq; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return db_of_query[a] < db_of_query[b]; });
+    // work-item budget: items_per_sm * SMs, shared in proportion to bytes
+    double total = 0;
+    for (int q = 0; q < nq; ++q) {
+        const dbq_db* db = p->dbs[db_of_query[q]];
+        total += (double)db->n * db->wp4;
+    }
+    const double budget = (double)p->items_per_sm * p->sms;
+    int nitems = 0;
+    size_t word_off = 0, sup_off = 0;
+    int slot = 0;
+    size_t g = 0;
+    while (g < order.size()) {
+        const int d = db_of_query[order[g]];
+        size_t h = g;
+        while (h < order.size() && db_of_query[order[h]] == d) ++h;
+        dbq_db* db = p->dbs[d];
+        const int cnt = (int)(h - g);
+        uint32_t* gplanes = p->planes + word_off;
+        uint32_t* gcount = p->pcount + 2 * slot;
+        uint32_t* gsup = p->sup + sup_off;
+        uint32_t* glen = p->suplen + 2 * slot;
+        DBQ_CUDA(cudaMemsetAsync(gcount, 0, (size_t)cnt * 2 * 4, s));
+        if (kind == DBQ_BITS) {
+            for (int i = 0; i < cnt; ++i) {
+                cudaError_t err = dbq::launch_import_bits(
+                    static_cast<const uint32_t*>(patients_dev[order[g + i]]), db->words, db->v,
+                    db->wp, gplanes + (size_t)i * 2 * db->wp, gcount + 2 * i, s);
+                if (err != cudaSuccess) return cuda_fail(err, "patient import");
+            }
+        } else {
+            for (int i = 0; i < cnt; ++i) p->ptrs_host[slot + i] = patients_dev[order[g + i]];
+            DBQ_CUDA(cudaMemcpyAsync(p->ptrs_dev + slot, p->ptrs_host + slot,
+                                     (size_t)cnt * sizeof(void*), cudaMemcpyHostToDevice, s));
+            cudaError_t err = dbq::launch_pack_ptrs(p->ptrs_dev + slot, kind == DBQ_F16, cnt,
+                                                    db->v, db->wp, db->t1, db->t2, gplanes,
+                                                    gcount, s);
+            if (err != cudaSuccess) return cuda_fail(err, "patient packing");
+        }
+        if (db->sparse) {
+            cudaError_t err = dbq::launch_support(gplanes, cnt, db->wp4, gsup, glen, s);
+            if (err != cudaSuccess) return cuda_fail(err, "support list launch");
+        }
+        for (int i = 0; i < cnt; ++i) {
+            const int q = order[g + i];
+            dbq::QueryTask& t = p->tasks_host[slot + i];
+            t.planes = reinterpret_cast<const uint4*>(db->planes);
+            t.ecount = db->ecount;
+            t.n = db->n;
+            t.wp4 = db->wp4;
+            t.chunk4 = db->chunk4;
+            t.nchunks = db->nchunks;
+            t.k = p->k;
+            int sl = (int)std::lround(budget * ((double)db->n * db->wp4) / total);
+            sl = std::max(1, std::min(sl, p->max_slices));
+            if ((int64_t)sl > db->n) sl = (int)db->n;
+            t.slices = sl;
+            t.patient = reinterpret_cast<const uint4*>(gplanes + (size_t)i * 2 * db->wp);
+            t.pcount = gcount + 2 * i;
+            t.sup_list = db->sparse ? gsup + (size_t)i * 2 * db->wp4 : nullptr;
+            t.sup_len = db->sparse ? glen + 2 * i : nullptr;
+            t.scratch = p->scratch + (size_t)(slot + i) * p->max_slices * p->k;
+            t.ticket = p->tickets + slot + i;
+            t.hits = reinterpret_cast<dbq::Hit*>(hits_dev) + (size_t)q * p->k;
+            for (int j = 0; j < sl; ++j) p->items_host[nitems++] = make_int2(slot + i, j);
+        }
+        word_off += (size_t)cnt * 2 * db->wp;
+        sup_off += (size_t)cnt * 2 * db->wp4;
+        slot += cnt;
+        g = h;
+    }
+    DBQ_CUDA(cudaMemcpyAsync(p->tasks_dev, p->tasks_host, (size_t)nq * sizeof(dbq::QueryTask),
+                             cudaMemcpyHostToDevice, s));
+    DBQ_CUDA(cudaMemcpyAsync(p->items_dev, p->items_host, (size_t)nitems * sizeof(int2),
+                             cudaMemcpyHostToDevice, s));
+    if (cap == cudaStreamCaptureStatusNone) {
+        DBQ_CUDA(cudaEventRecord(p->copied, s));
+        p->copy_pending = true;
+    }
+    cudaError_t err = dbq::launch_scan_tasks(p->tasks_dev, p->items_dev, nitems, p->counter,
+                                             p->sms, s);
+    if (err != cudaSuccess) return cuda_fail(err, "task scan launch");
+    return DBQ_OK;
+}
+
+int db_plan_destroy(dbq_plan* plan)
+{
+    if (!plan) return DBQ_OK;
+    DeviceGuard guard(plan->device);
+    cudaDeviceSynchronize();
+    delete plan;
     return DBQ_OK;
 }
 

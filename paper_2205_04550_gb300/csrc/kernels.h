@@ -147,6 +147,27 @@ struct RerankArgs {
 };
 cudaError_t launch_rerank(const RerankArgs& a, cudaStream_t stream);
 
+// ---- many exact queries in one persistent launch
+struct QueryTask {
+    const uint4* planes;        // database planes [n][2][wp4]
+    const uint32_t* ecount;     // [n][2]
+    int64_t n;
+    int wp4, chunk4, nchunks;
+    int k;                      // hits wanted (<= 1024)
+    int slices;                 // work items of this query
+    const uint4* patient;       // [2][wp4]
+    const uint32_t* pcount;     // [2]
+    const uint32_t* sup_list;   // [2][wp4] support lists, or null (dense)
+    const uint32_t* sup_len;    // [2]
+    Cand* scratch;              // [slices][k]
+    unsigned int* ticket;       // zero between launches
+    Hit* hits;                  // [k]
+};
+size_t scan_tasks_smem();
+// items[i] = (task, slice); next_item is a device counter (cleared here).
+cudaError_t launch_scan_tasks(const QueryTask* tasks, const int2* items, int nitems,
+                              unsigned int* next_item, int grid, cudaStream_t stream);
+
 // Set the calling thread's db_last_error() message; returns `code`.
 int record_error(int code, const char* msg);
 

@@ -1,0 +1,117 @@
+// scan_tasks.cu -- many exact queries, against several bit-packed databases
+// of different resolutions, in one persistent launch.
+//
+// Each query is the brute-force loop of Section 2.3 (Ezhov et al. 2022) over
+// its database.  A query is split into slices of its entries; the work items
+// (query, slice) of all queries form one list that the CTAs of a persistent
+// grid take from a global counter, so queries of different sizes balance
+// over the GPU.  An item counts its entries with the shared count loop
+// (dense, or restricted to the patient's support lists), keeps a running
+// top-k, publishes it to the query's scratch row; the last item of a query
+// (per-query atomic ticket, no spinning) merges the slices into its k hits.
+#include "kernels.h"
+#include "scan_core.cuh"
+#include "topk.cuh"
+
+namespace dbq {
+namespace {
+
+constexpr int kGroup = 1024;
+
+template <int U, int EPI>
+__device__ __forceinline__ void count_task(const QueryTask& t, int64_t g0, int gn, uint32_t* icnt)
+{
+    if (t.sup_list) {
+        Support sup;
+        sup.list1 = t.sup_list;
+        sup.list2 = t.sup_list + t.wp4;
+        sup.len = t.sup_len;
+        count_group<U, EPI, true>(t.planes, t.wp4, t.chunk4, t.nchunks, t.patient, nullptr, g0,
+                                  gn, icnt, sup);
+    } else {
+        count_group<U, EPI, false>(t.planes, t.wp4, t.chunk4, t.nchunks, t.patient, nullptr, g0,
+                                   gn, icnt);
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads, 1)
+scan_tasks_kernel(const QueryTask* __restrict__ tasks, const int2* __restrict__ items, int nitems,
+                  unsigned int* __restrict__ next_item)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TopK tk;
+    uint32_t* icnt = reinterpret_cast<uint32_t*>(topk_carve(tk, smem_raw));   // [kGroup][2]
+    __shared__ int item_s;
+    __shared__ QueryTask task_s;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) item_s = (int)atomicAdd(next_item, 1u);
+        __syncthreads();
+        const int item = item_s;
+        __syncthreads();
+        if (item >= nitems) break;
+        const int2 it = items[item];
+        if (tid == 0) task_s = tasks[it.x];
+        __syncthreads();
+        const QueryTask& t = task_s;
+        const int sl = it.y;
+        const int64_t e_begin = (int64_t)sl * t.n / t.slices;
+        const int64_t e_end = ((int64_t)sl + 1) * t.n / t.slices;
+        const uint32_t P1 = t.pcount[0], P2 = t.pcount[1];
+        const uint2* ecount2 = reinterpret_cast<const uint2*>(t.ecount);
+        topk_init(tk);
+        for (int64_t g0 = e_begin; g0 < e_end; g0 += kGroup) {
+            const int gn = (int)((e_end - g0) < kGroup ? (e_end - g0) : kGroup);
+            for (int i = tid; i < 2 * kGroup; i += kScanThreads) icnt[i] = 0u;
+            __syncthreads();
+            if (t.chunk4 <= kScanThreads) count_task<1, 4>(t, g0, gn, icnt);
+            else count_task<2, 2>(t, g0, gn, icnt);
+            __syncthreads();
+            for (int i = tid; i < gn; i += kScanThreads) {
+                const int64_t e = g0 + i;
+                const uint32_t I1 = icnt[2 * i], I2 = icnt[2 * i + 1];
+                const uint2 E = ecount2[e];
+                topk_offer(tk, t.k, score_rn(I1, I2, E.x, E.y, P1, P2), e,
+                           (uint64_t)I1 | ((uint64_t)I2 << 32),
+                           (uint64_t)E.x | ((uint64_t)E.y << 32));
+            }
+            topk_flush(tk, t.k);
+        }
+        if (topk_publish_slot(tk, t.k, t.scratch, sl, t.slices, t.ticket)) {
+            topk_merge_published(tk, t.k, t.scratch, (int64_t)t.slices * t.k);
+            for (int j = tid; j < t.k; j += kScanThreads) {
+                Hit h;
+                h.index = tk.idx[j];
+                h.score = tk.key[j];
+                h.i1 = (uint32_t)(tk.pay0[j] & 0xffffffffu);
+                h.i2 = (uint32_t)(tk.pay0[j] >> 32);
+                h.e1 = (uint32_t)(tk.pay1[j] & 0xffffffffu);
+                h.e2 = (uint32_t)(tk.pay1[j] >> 32);
+                h.p1 = P1;
+                h.p2 = P2;
+                t.hits[j] = h;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+size_t scan_tasks_smem() { return topk_smem_bytes() + (size_t)kGroup * 2 * sizeof(uint32_t); }
+
+cudaError_t launch_scan_tasks(const QueryTask* tasks, const int2* items, int nitems,
+                              unsigned int* next_item, int grid, cudaStream_t stream)
+{
+    if (nitems <= 0) return cudaSuccess;
+    const size_t smem = scan_tasks_smem();
+    cudaError_t err = cudaFuncSetAttribute(scan_tasks_kernel,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    err = cudaMemsetAsync(next_item, 0, sizeof(unsigned int), stream);
+    if (err != cudaSuccess) return err;
+    scan_tasks_kernel<<<grid, kScanThreads, smem, stream>>>(tasks, items, nitems, next_item);
+    return cudaGetLastError();
+}
+
+}  // namespace dbq

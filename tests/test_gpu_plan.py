@@ -1,0 +1,124 @@
+"""Query plans: many exact queries against databases of different
+resolutions in one persistent launch, optionally captured in a CUDA graph.
+Every hit list must equal the oracle's exact ranking (bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2205_04550_gb300 import DBQ_STORE_BITS, DBQ_STORE_F16, Database, DbqError, Plan, _dbq
+from tests._gpu_helpers import assert_hits_equal, random_db
+
+pytestmark = pytest.mark.gpu
+
+T1, T2 = np.float32(0.6), np.float32(0.25)
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as _t
+    from paper_2205_04550_gb300 import build
+    build.build()
+    return _t
+
+
+@pytest.fixture(scope="module")
+def two_dbs(torch):
+    s1, s2 = (64, 64, 64), (32, 32, 32)
+    v1, _ = random_db(s1, 500, seed=1)
+    v2, _ = random_db(s2, 1300, seed=2)
+    d1 = Database(s1, 500, DBQ_STORE_BITS, T1, T2)
+    d1.load(0, v1)
+    d1.build()
+    d2 = Database(s2, 1300, DBQ_STORE_BITS, T1, T2)
+    d2.load(0, v2)
+    d2.build()
+    yield (d1, v1), (d2, v2)
+    d1.close()
+    d2.close()
+
+
+def _patients(rng, vols, count):
+    out = []
+    for _ in range(count):
+        p = vols[rng.integers(0, len(vols))].copy()
+        p[rng.random(p.shape) < 0.3] = 0.0          # a perturbed copy of an entry
+        out.append(p)
+    return out
+
+
+@pytest.mark.parametrize("sparse", [False, True])
+@pytest.mark.parametrize("items_per_sm", [1, 4, 64])
+def test_plan_two_resolutions(torch, two_dbs, sparse, items_per_sm):
+    (d1, v1), (d2, v2) = two_dbs
+    d1.set_sparse(sparse)
+    rng = np.random.default_rng(items_per_sm)
+    pats = _patients(rng, v1, 5) + _patients(rng, v2, 6)
+    which = [0] * 5 + [1] * 6
+    perm = rng.permutation(len(pats))
+    pats = [pats[i] for i in perm]
+    which = [which[i] for i in perm]
+    k = 16
+    with Plan([d1, d2], 32, k) as plan:
+        plan.set_items_per_sm(items_per_sm)
+        dev = [torch.from_numpy(p).cuda() for p in pats]
+        hits = torch.zeros((len(pats), k * 40), dtype=torch.uint8, device="cuda")
+        plan.query(which, dev, hits)
+        torch.cuda.synchronize()
+        got = hits.cpu().numpy().view(_dbq.HIT_DTYPE)
+        for q, (p, w) in enumerate(zip(pats, which)):
+            vols = v1 if w == 0 else v2
+            assert_hits_equal(got[q], oracle.query(vols, p, T1, T2, k), k)
+    d1.set_sparse(False)
+
+
+def test_plan_captured_in_cuda_graph_and_replayed(torch, two_dbs):
+    (d1, v1), (d2, v2) = two_dbs
+    rng = np.random.default_rng(7)
+    nq, k = 6, 10
+    which = [0, 1, 0, 1, 1, 0]
+    shapes = [v1.shape[1:] if w == 0 else v2.shape[1:] for w in which]
+    slots = [torch.zeros(sh, dtype=torch.float32, device="cuda") for sh in shapes]
+    hits = torch.zeros((nq, k * 40), dtype=torch.uint8, device="cuda")
+    with Plan([d1, d2], nq, k) as plan:
+        keep = []
+        plan.query(which, slots, hits, keep=keep)     # first call outside capture
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                plan.query(which, slots, hits, keep=keep)
+        torch.cuda.synchronize()
+        for rep in range(3):
+            pats = [(_patients(rng, v1, 1) if w == 0 else _patients(rng, v2, 1))[0] for w in which]
+            for sl, p in zip(slots, pats):
+                sl.copy_(torch.from_numpy(p))
+            g.replay()
+            torch.cuda.synchronize()
+            got = hits.cpu().numpy().view(_dbq.HIT_DTYPE)
+            for q, (p, w) in enumerate(zip(pats, which)):
+                vols = v1 if w == 0 else v2
+                assert_hits_equal(got[q], oracle.query(vols, p, T1, T2, k), k)
+
+
+def test_plan_errors(torch, two_dbs):
+    (d1, v1), (d2, v2) = two_dbs
+    with pytest.raises(DbqError) as e:
+        Plan([d1], 4, 501)
+    assert e.value.status == _dbq.DBQ_ERANGE
+    with Database((8, 8, 8), 4, DBQ_STORE_F16) as d3:
+        d3.load(0, np.zeros((4, 8, 8, 8), np.float16).view(np.uint16))
+        d3.build()
+        with pytest.raises(DbqError) as e:
+            Plan([d3], 4, 1)
+        assert e.value.status == _dbq.DBQ_ESTATE
+    with Plan([d1, d2], 2, 3) as plan:
+        hits = torch.zeros((3, 3 * 40), dtype=torch.uint8, device="cuda")
+        p = torch.from_numpy(v1[0]).cuda()
+        with pytest.raises(DbqError):
+            plan.query([0, 0, 0], [p, p, p], hits)          # more than max_queries
+        with pytest.raises(DbqError):
+            plan.query([2], [p], hits)                      # no such database
+        with pytest.raises(DbqError):
+            _dbq.db_plan_query(plan.handle, [0], [p], hits, t1=[0.5], t2=[0.25])
