@@ -53,6 +53,16 @@ WORKLOADS = {
     "embed_10k_128": dict(shape=(128, 128, 128), n=10_000, k=10, t1=0.6, t2=0.25, embed=True,
                           queries=256, candidates=512, mode="bf16",
                           desc="10,000 x 128^3 bit-packed + bf16 embeddings (profiling size)"),
+    "plan_mix": dict(mix=[dict(shape=(64, 64, 64), n=100_000), dict(shape=(128, 128, 128), n=50_000)],
+                     share=[0.7, 0.3], queries=128, k=10, t1=0.6, t2=0.25,
+                     desc="128 queries per launch, 70% vs 100,000 x 64^3 and 30% vs 50,000 x "
+                          "128^3 bit-packed (both resident), one persistent plan launch, "
+                          "CUDA-graph replay, autotuned items per SM, top-10"),
+    "serve_mix": dict(mix=[dict(shape=(64, 64, 64), n=100_000), dict(shape=(128, 128, 128), n=50_000)],
+                      share=[0.7, 0.3], rate=200.0, requests=2000, max_batch=128, k=10,
+                      candidates=512, t1=0.6, t2=0.25,
+                      desc="Poisson arrivals 200 queries/s, 70% vs 100,000 x 64^3, 30% vs "
+                           "50,000 x 128^3 (resident, with embeddings), batches <= 128"),
     "exact_packed_1k_64": dict(shape=(64, 64, 64), n=1024, k=10, t1=0.6, t2=0.25,
                                desc="1,024 x 64^3 bit-packed, t=(0.6,0.25), top-10"),
 }
@@ -171,7 +181,7 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def build_database(torch, wl, chunk: int = 8):
+def build_database(torch, wl, chunk: int | None = None):
     """Generate the surrogate database on the GPU in L2-sized chunks and
     load each chunk as it is made (thresholded and packed for bit-packed
     storage, rounded to binary16 for half storage); not timed."""
@@ -182,6 +192,8 @@ def build_database(torch, wl, chunk: int = 8):
     gen = synth.DeviceGenerator(shape, synth.DB_SEED, np.arange(n))
     db = Database(shape, n, DBQ_STORE_F16 if f16 else DBQ_STORE_BITS, wl["t1"], wl["t2"],
                   synth.N_PARAMS, embed=bool(wl.get("embed")))
+    if chunk is None:   # about 64 MB of float32 volumes per chunk: L2-resident
+        chunk = max(8, (64 << 20) // (4 * nx * ny * nz))
     if f16:
         chunk *= 8
     buf = torch.empty((chunk, nz, ny, nx), dtype=torch.float16 if f16 else torch.float32,
@@ -402,6 +414,144 @@ def run_embed(args, wl, torch):
     return 0
 
 
+def _mix_databases(torch, wl, embed=False):
+    dbs = []
+    for part in wl["mix"]:
+        sub = dict(shape=part["shape"], n=part["n"], t1=wl["t1"], t2=wl["t2"], embed=embed)
+        dbs.append(build_database(torch, sub))
+    return dbs
+
+
+def _mix_patients(torch, wl, count, seed=7):
+    """Device patients of the request mix (held-out generator ids) and the
+    database each one queries."""
+    from paper_2205_04550_gb300 import synth
+    rng = np.random.default_rng(seed)
+    which = list((rng.random(count) >= wl["share"][0]).astype(int))
+    pats = []
+    for d, part in enumerate(wl["mix"]):
+        ids = [q for q in range(count) if which[q] == d]
+        if not ids:
+            continue
+        shape = part["shape"]
+        gen = synth.DeviceGenerator(shape, synth.DB_SEED,
+                                    synth.PATIENT_BASE + 1 + np.array(ids, dtype=np.uint64))
+        nx, ny, nz = shape
+        buf = torch.empty((len(ids), nz, ny, nx), dtype=torch.float32, device="cuda")
+        gen.fill(0, len(ids), buf)
+        pats.append((ids, buf))
+    out = [None] * count
+    for ids, buf in pats:
+        for j, q in enumerate(ids):
+            out[q] = buf[j]
+    return which, out
+
+
+def run_plan_mix(args, wl, torch):
+    """Batches of queries against two resident databases of different
+    resolutions in one persistent launch, captured in a CUDA graph."""
+    from paper_2205_04550_gb300 import Plan, tune
+    rank, world, local = _dist_env()
+    dbs = _mix_databases(torch, wl)
+    nq, k = wl["queries"], wl["k"]
+    which, pats = _mix_patients(torch, wl, nq)
+    hits = torch.zeros((nq, k * 40), dtype=torch.uint8, device="cuda")
+    results = {}
+    for sparse in (False, True):
+        for d in dbs:
+            d.set_sparse(sparse)
+        with Plan(dbs, nq, k) as plan:
+            tuned = tune.tune_plan(plan, which, pats, hits, sparse_flags=sparse)
+            keep = []
+            plan.query(which, pats, hits, keep=keep)
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            cs = torch.cuda.Stream()
+            cs.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(cs):
+                with torch.cuda.graph(g, stream=cs):
+                    plan.query(which, pats, hits, keep=keep)
+            torch.cuda.synchronize()
+            for _ in range(args.warmup):
+                g.replay()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            stream = torch.cuda.current_stream()
+            e0.record(stream)
+            for _ in range(args.steps):
+                g.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            el = e0.elapsed_time(e1) / 1000.0
+            results["sparse" if sparse else "dense"] = {
+                "queries_per_s": world * args.steps * nq / el,
+                "ms_per_launch": 1000.0 * el / args.steps,
+                "items_per_sm": tuned["items_per_sm"], "tuning_ms": tuned.get("ms"),
+                "tuning_cached": tuned.get("cached")}
+    dense = results["dense"]
+    line = {"metric": METRIC, "value": dense["queries_per_s"], "unit": "queries/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dense["ms_per_launch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"],
+                       "queries_per_launch": nq,
+                       "queries_per_db": [which.count(0), which.count(1)],
+                       "l2": "inputs larger than L2 (32.8 GB of packed databases); no flush"},
+            "dense": dense, "sparse": results["sparse"],
+            "gpu_launches": 3 * args.steps}
+    for d in dbs:
+        d.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_serve(args, wl, torch):
+    """Open-loop Poisson request stream through the continuous-batching
+    server, exact path and embedding path."""
+    from paper_2205_04550_gb300 import serve
+    rank, world, local = _dist_env()
+    dbs = _mix_databases(torch, wl, embed=True)
+    count = wl["requests"]
+    pool = 64
+    which_pool, pats = _mix_patients(torch, wl, 2 * pool, seed=3)
+    host = {0: [], 1: []}
+    for q in range(2 * pool):
+        host[which_pool[q]].append(pats[q].cpu().numpy())
+    rng = np.random.default_rng(7)
+    reqs = []
+    for _ in range(count):
+        d = 0 if rng.random() < wl["share"][0] else 1
+        reqs.append((host[d][rng.integers(0, len(host[d]))], d))
+    arrivals = serve.poisson_arrivals(wl["rate"], count, seed=7)
+    out = {}
+    for mode in ("exact", "embed_bf16"):
+        srv = serve.Server(dbs, mode=mode, k=wl["k"], n_candidates=wl["candidates"],
+                           max_batch=wl["max_batch"], lanes=2)
+        try:
+            serve.run_open_loop(srv, reqs[:200], serve.poisson_arrivals(wl["rate"], 200, 1))
+            srv.reset_stats()
+            t0 = time.perf_counter()
+            serve.run_open_loop(srv, reqs, arrivals)
+            out[mode] = dict(srv.stats(), wall_s=time.perf_counter() - t0)
+        finally:
+            srv.close()
+    line = {"metric": METRIC, "value": out["exact"]["queries_per_s"], "unit": "queries/s",
+            "n_gpus": world, "steps": count, "warmup": 200,
+            "ms_per_step": out["exact"]["mean_ms"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": args.workload, "desc": wl["desc"], "requests": count,
+                       "rate_per_s": wl["rate"], "max_batch": wl["max_batch"]},
+            "exact": out["exact"], "embed_bf16": out["embed_bf16"],
+            "note": "offered load 200 queries/s: queries/s is bounded by the arrival rate; "
+                    "latency is the measure"}
+    for d in dbs:
+        d.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -430,6 +580,10 @@ def main(argv=None):
     build.build()
     if wl.get("embed"):
         return run_embed(args, wl, torch)
+    if args.workload == "plan_mix":
+        return run_plan_mix(args, wl, torch)
+    if args.workload == "serve_mix":
+        return run_serve(args, wl, torch)
 
     db = build_database(torch, wl)
     k = wl["k"]
