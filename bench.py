@@ -105,6 +105,17 @@ def _traffic(kernel: str, n_entries: int):
     return t["read_bytes"] / t["entries"] * n_entries + t["write_bytes"]
 
 
+def max_over_ranks(value: float, dist=None, device=None) -> float:
+    """The largest of `value` over all ranks (the slowest rank's time); the
+    value itself when not distributed."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device or "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -636,10 +647,7 @@ def main(argv=None):
     wall1 = time.time()
     elapsed = t_start.elapsed_time(t_end) / 1000.0
     scan_s = sum(a.elapsed_time(b) for a, b in scan_ev) / 1000.0 / args.steps
-    if dist:
-        t = torch.tensor([elapsed], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed = float(t.item())
+    elapsed = max_over_ranks(elapsed, dist, "cuda")
     n_entries = wl["n"]
     value = world * args.steps * n_entries / elapsed
 
@@ -697,10 +705,7 @@ def main(argv=None):
     torch.cuda.synchronize()
     e_el = time.perf_counter() - e0
     w1 = time.time()
-    if dist:
-        t = torch.tensor([e_el], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e_el = float(t.item())
+    e_el = max_over_ranks(e_el, dist, "cuda")
     clocks.stop()
     clk = clocks.summary(wall0, max(wall1, w1))
     e2e_value = world * e2e_steps * n_entries / e_el
