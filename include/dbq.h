@@ -317,6 +317,20 @@ int db_get_embeddings(dbq_db* db, int64_t first, int64_t count, uint16_t* bf16, 
                       float* scale, float* norm_bf16, float* norm_fp8, void* stream);
 
 /*
+ * db_create_downsampled -- a bit-packed database made from `src` by
+ * nearest-neighbour downsampling by `factor` (Section 2.3's queries on a
+ * database downsampled to 64^3 or 32^3 with an order-0 spline): voxel
+ * (x, y, z) of the coarse grid is voxel (f x, f y, f z) of the source.  The
+ * new handle is built, shares nothing with `src` afterwards, keeps the same
+ * thresholds and theta, and takes patients at the SOURCE resolution in
+ * db_query / db_query_async / db_prepare_patient / db_scan_counts,
+ * downsampling them the same way.  src must be bit-packed and built, its
+ * grid divisible by factor (2..16).  Batches and plans do not accept such a
+ * handle (DBQ_ESTATE).
+ */
+int db_create_downsampled(dbq_db** out, dbq_db* src, int factor);
+
+/*
  * db_scan_packed_noalloc -- the bit-packed exact query for callers that
  * cannot allocate device memory (a memory pool that owns the whole GPU, a
  * request path that must not synchronise on an allocation, a plug-in host

@@ -17,14 +17,14 @@ from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_MODE_EMBED_BF
                    db_prepare_patient, db_query, db_query_async, db_query_batch,
                    db_query_prepared, db_scan_counts, db_scan_packed_noalloc, db_set_option,
                    db_stage_times, DBQ_OPT_SPARSE, DBQ_PLAN_ITEMS_PER_SM, db_plan_create,
-                   db_plan_set, db_plan_query, db_plan_destroy)
+                   db_plan_set, db_plan_query, db_plan_destroy, db_create_downsampled)
 
 __all__ = ["Database", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_F16", "DBQ_BITS",
            "DBQ_STORE_BITS", "DBQ_STORE_F16", "DBQ_FLAG_EMBED", "DBQ_MODE_EXACT",
            "DBQ_MODE_EMBED_BF16", "DBQ_MODE_EMBED_FP8", "db_query_batch", "db_prefilter",
            "db_get_embeddings", "db_scan_packed_noalloc", "db_set_option", "db_stage_times",
            "DBQ_OPT_SPARSE", "DBQ_PLAN_ITEMS_PER_SM", "Plan", "db_plan_create",
-           "db_plan_set", "db_plan_query", "db_plan_destroy", "db_create", "db_load_volumes",
+           "db_plan_set", "db_plan_query", "db_plan_destroy", "db_create_downsampled", "db_create", "db_load_volumes",
            "db_build_masks", "db_query", "db_query_async", "db_prepare_patient",
            "db_query_prepared", "db_scan_counts", "db_get_masks",
            "db_info", "db_destroy", "db_last_error"]
@@ -71,6 +71,20 @@ class Database:
         sizes = np.zeros((count, 2), dtype=np.uint32)
         db_get_masks(self.handle, first, count, planes, sizes)
         return planes, sizes
+
+    def downsampled(self, factor: int) -> "Database":
+        """A nearest-neighbour downsampled copy (DS64 / DS32 of Section 2.3);
+        it takes patients at this database's resolution."""
+        obj = Database.__new__(Database)
+        nx, ny, nz = self.shape
+        obj.shape = (nx // factor, ny // factor, nz // factor)
+        obj.capacity = self.capacity
+        obj.storage = self.storage
+        obj.t1, obj.t2 = self.t1, self.t2
+        obj.n_params = self.n_params
+        obj.embed = False
+        obj.handle = db_create_downsampled(self.handle, factor)
+        return obj
 
     def set_sparse(self, on: bool = True):
         """Exact scans read only the patient's support (identical results)."""

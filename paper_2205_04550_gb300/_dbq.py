@@ -99,6 +99,7 @@ _SIGS = [
     ("db_plan_set", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     ("db_plan_query", ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]),
     ("db_plan_destroy", ctypes.c_int, [_P]),
+    ("db_create_downsampled", ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.c_int]),
     ("db_scan_packed_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
                                               ctypes.c_int, _P, _P]),
     ("db_destroy", ctypes.c_int, [_P]),
@@ -315,6 +316,12 @@ def db_plan_query(plan: int, db_of_query, patients_dev, hits_dev, kind: int | No
     _check(load().db_plan_query(plan, dq.ctypes.data, len(patients_dev), pa,
                                 _kind_of(patients_dev[0]) if kind is None else kind,
                                 _ptr(a1), _ptr(a2), _ptr(hits_dev), _stream(stream)))
+
+
+def db_create_downsampled(src: int, factor: int) -> int:
+    h = _P()
+    _check(load().db_create_downsampled(ctypes.byref(h), src, factor))
+    return h.value
 
 
 def db_plan_destroy(plan: int):

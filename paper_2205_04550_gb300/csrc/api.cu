@@ -139,6 +139,11 @@ struct dbq_db {
     int* bstatus = nullptr;         // device status of the tensor-core kernel
     cudaEvent_t ev[6] = {};         // stage boundaries of the last embedding batch
     bool ev_valid = false;
+    // nearest-neighbour downsampled copy of another database (0 = none)
+    int ds_factor = 0;
+    int ds_nx = 0, ds_ny = 0, ds_nz = 0;   // source grid: patients come at this size
+    int64_t ds_v = 0, ds_words = 0, ds_wp = 0;
+    uint32_t* ds_pplanes = nullptr;        // [2][ds_wp] source-resolution patient planes
     bool sparse = false;            // DBQ_OPT_SPARSE
     uint32_t* plist = nullptr;      // [2][wp4] patient support lists
     uint32_t* plen = nullptr;       // [2]
@@ -186,6 +191,7 @@ struct dbq_db {
         cudaFree(bstatus);
         cudaFree(plist);
         cudaFree(plen);
+        cudaFree(ds_pplanes);
         cudaFree(bsup);
         cudaFree(bsuplen);
         for (cudaEvent_t e : ev)
@@ -227,13 +233,18 @@ int prepare_patient(dbq_db* db, const void* patient, int kind, float t1, float t
                     cudaStream_t s)
 {
     const bool on_dev = is_device_ptr(patient);
+    const bool ds = db->ds_factor > 0;
+    const int64_t pv = ds ? db->ds_v : db->v;            // patient grid
+    const int64_t pwords = ds ? db->ds_words : db->words;
+    const int64_t pwp = ds ? db->ds_wp : db->wp;
+    uint32_t* pplanes = ds ? db->ds_pplanes : db->pplanes;
     size_t bytes;
     if (kind == DBQ_BITS)
-        bytes = (size_t)2 * db->words * sizeof(uint32_t);
+        bytes = (size_t)2 * pwords * sizeof(uint32_t);
     else if (kind == DBQ_F32)
-        bytes = (size_t)db->v * sizeof(float);
+        bytes = (size_t)pv * sizeof(float);
     else if (kind == DBQ_F16)
-        bytes = (size_t)db->v * sizeof(uint16_t);
+        bytes = (size_t)pv * sizeof(uint16_t);
     else
         return fail(DBQ_EINVAL, "unknown patient kind %d", kind);
     const void* src = patient;
@@ -246,12 +257,18 @@ int prepare_patient(dbq_db* db, const void* patient, int kind, float t1, float t
     DBQ_CUDA(cudaMemsetAsync(db->pcount, 0, 4 * sizeof(uint32_t), s));
     cudaError_t err;
     if (kind == DBQ_BITS)
-        err = dbq::launch_import_bits(static_cast<const uint32_t*>(src), db->words, db->v, db->wp,
-                                      db->pplanes, db->pcount, s);
+        err = dbq::launch_import_bits(static_cast<const uint32_t*>(src), pwords, pv, pwp,
+                                      pplanes, db->pcount, s);
     else
-        err = dbq::launch_pack(src, kind == DBQ_F16, 1, db->v, db->wp, t1, t2, db->pplanes,
-                               db->pcount, s);
+        err = dbq::launch_pack(src, kind == DBQ_F16, 1, pv, pwp, t1, t2, pplanes, db->pcount, s);
     if (err != cudaSuccess) return cuda_fail(err, "patient packing");
+    if (ds) {   // the coarse patient, sampled like the database
+        DBQ_CUDA(cudaMemsetAsync(db->pcount, 0, 4 * sizeof(uint32_t), s));
+        err = dbq::launch_downsample(db->ds_pplanes, 2, db->ds_wp, db->ds_nx, db->ds_ny,
+                                     db->ds_nz, db->ds_factor, db->wp, db->pplanes, db->pcount,
+                                     s);
+        if (err != cudaSuccess) return cuda_fail(err, "patient downsampling");
+    }
     if (db->sparse && db->storage == DBQ_STORE_BITS) {
         err = dbq::launch_support(db->pplanes, 1, db->wp4, db->plist, db->plen, s);
         if (err != cudaSuccess) return cuda_fail(err, "support list launch");
@@ -944,6 +961,51 @@ int db_get_embeddings(dbq_db* db, int64_t first, int64_t count, uint16_t* bf16, 
     return DBQ_OK;
 }
 
+int db_create_downsampled(dbq_db** out, dbq_db* src, int factor)
+{
+    if (!out || !src) return fail(DBQ_EINVAL, "NULL pointer argument");
+    *out = nullptr;
+    std::lock_guard<std::mutex> lock(src->mu);
+    if (src->storage != DBQ_STORE_BITS || !src->built)
+        return fail(DBQ_ESTATE, "source must be a built bit-packed database");
+    if (src->ds_factor) return fail(DBQ_ESTATE, "source is itself downsampled");
+    if (factor < 2 || factor > 16 || src->nx % factor || src->ny % factor || src->nz % factor)
+        return fail(DBQ_EINVAL, "factor must be in [2, 16] and divide the grid");
+    DeviceGuard guard(src->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", src->device);
+    dbq_db* db = nullptr;
+    int rc = db_create(&db, src->nx / factor, src->ny / factor, src->nz / factor, src->n,
+                       DBQ_STORE_BITS, src->t1, src->t2, src->n_params, 0);
+    if (rc) return rc;
+    db->ds_factor = factor;
+    db->ds_nx = src->nx;
+    db->ds_ny = src->ny;
+    db->ds_nz = src->nz;
+    db->ds_v = src->v;
+    db->ds_words = src->words;
+    db->ds_wp = src->wp;
+    rc = dev_alloc(db, &db->ds_pplanes, (size_t)2 * src->wp * 4, "source-resolution patient");
+    if (rc) {
+        delete db;
+        return rc;
+    }
+    cudaError_t err = cudaMemset(db->ecount, 0, (size_t)db->n * 2 * 4);
+    if (err == cudaSuccess)
+        err = dbq::launch_downsample(src->planes, src->n * 2, src->wp, src->nx, src->ny, src->nz,
+                                     factor, db->wp, db->planes, db->ecount, nullptr);
+    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) {
+        delete db;
+        return cuda_fail(err, "downsampling");
+    }
+    db->params = src->params;
+    std::fill(db->loaded.begin(), db->loaded.end(), 1);
+    db->n_loaded = db->n;
+    db->built = true;
+    *out = db;
+    return DBQ_OK;
+}
+
 int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int mode,
                  int n_candidates, float* dist, int32_t* cand, void* stream)
 {
@@ -995,6 +1057,8 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
         dbq_db* db = dbs[dbi];
         if (!db) return fail(DBQ_EINVAL, "database %d is NULL", dbi);
         std::lock_guard<std::mutex> lock(db->mu);
+        if (db->ds_factor)
+            return fail(DBQ_ESTATE, "downsampled databases take single-patient queries only");
         DeviceGuard guard(db->device);
         if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
         for (size_t g0 = i; g0 < j; g0 += kBatchQ) {
@@ -1138,9 +1202,10 @@ int db_plan_create(dbq_plan** out, dbq_db* const* dbs, int ndb, int max_queries,
         dbq_db* db = dbs[i];
         if (!db) { delete p; return fail(DBQ_EINVAL, "database %d is NULL", i); }
         std::lock_guard<std::mutex> lock(db->mu);
-        if (db->storage != DBQ_STORE_BITS || !db->built) {
+        if (db->storage != DBQ_STORE_BITS || !db->built || db->ds_factor) {
             delete p;
-            return fail(DBQ_ESTATE, "plans need built bit-packed databases (database %d)", i);
+            return fail(DBQ_ESTATE,
+                        "plans need built full-resolution bit-packed databases (database %d)", i);
         }
         if (i == 0) p->device = db->device;
         if (db->device != p->device) {

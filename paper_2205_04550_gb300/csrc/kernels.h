@@ -168,6 +168,13 @@ size_t scan_tasks_smem();
 cudaError_t launch_scan_tasks(const QueryTask* tasks, const int2* items, int nitems,
                               unsigned int* next_item, int grid, cudaStream_t stream);
 
+// Nearest-neighbour downsampling of `rows` bit planes (rows = entries * 2)
+// of an nx x ny x nz grid by factor f: dst [rows][dst_wp], sizes [rows]
+// (mask sizes of the coarse planes; zeroed by the caller).
+cudaError_t launch_downsample(const uint32_t* src, int64_t rows, int64_t src_wp, int nx, int ny,
+                              int nz, int f, int64_t dst_wp, uint32_t* dst, uint32_t* sizes,
+                              cudaStream_t stream);
+
 // Set the calling thread's db_last_error() message; returns `code`.
 int record_error(int code, const char* msg);
 
