@@ -371,6 +371,26 @@ def run_embed(args, wl, torch):
     wall1 = time.time()
     elapsed = t0.elapsed_time(t1) / 1000.0
     stages = {a: v / args.steps for a, v in stage_sum.items()}
+    # the same launches with sparse re-ranking (patient support only)
+    db.set_sparse(True)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    sp_stage = None
+    p0.record(stream)
+    for _ in range(args.steps):
+        sp_hits, _ = step()
+        st = _dbq.db_stage_times(h)
+        sp_stage = st if sp_stage is None else {a: sp_stage[a] + st[a] for a in st}
+    p1.record(stream)
+    torch.cuda.synchronize()
+    db.set_sparse(False)
+    sp_elapsed = p0.elapsed_time(p1) / 1000.0
+    sparse_line = {"queries_per_s": world * args.steps * nq / sp_elapsed,
+                   "ms_per_step": 1000.0 * sp_elapsed / args.steps,
+                   "stages_ms": {a: v / args.steps for a, v in sp_stage.items()},
+                   "identical_hits": bool(sp_hits.tobytes() == hits.tobytes())}
     # the exact scan of the same queries, for agreement and speed-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -415,6 +435,7 @@ def run_embed(args, wl, torch):
         "exact_scan_queries_per_s": nq / exact_s,
         "speedup_vs_exact_gpu_scan": (nq / exact_s and value / (nq / exact_s)),
         "stages_ms": stages,
+        "sparse_rerank": sparse_line,
         "gemm": {"tflops": gemm_flops / (stages["gemm"] / 1000.0) / 1e12, "peak": gemm_peak,
                  "peak_kind": bf16_kind, "flops_per_launch": gemm_flops},
         "rerank": {"gbs": rr_bytes / (stages["rerank"] / 1000.0) / 1e9,

@@ -106,6 +106,8 @@ struct dbq_db {
     uint32_t* pplanes = nullptr;    // [2][wp] patient planes
     uint32_t* pcount = nullptr;     // [4] patient sizes (2 used)
     dbq::Cand* cand = nullptr;      // [grid][kMaxK]
+    dbq::Cand* group_lists = nullptr;   // [ceil(grid/8)][kMaxK] two-level merge
+    unsigned int* tickets = nullptr;    // [64] two-level merge counters
     unsigned int* ticket = nullptr;
     dbq::Hit* hits_dev = nullptr;   // [kMaxK]
     dbq::Hit* hits_host = nullptr;  // pinned [kMaxK]
@@ -164,6 +166,8 @@ struct dbq_db {
         cudaFree(pplanes);
         cudaFree(pcount);
         cudaFree(cand);
+        cudaFree(group_lists);
+        cudaFree(tickets);
         cudaFree(ticket);
         cudaFree(hits_dev);
         cudaFreeHost(hits_host);
@@ -322,6 +326,8 @@ int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaSt
         a.counts_out = counts_out;
         a.sup_list = db->sparse ? db->plist : nullptr;
         a.sup_len = db->sparse ? db->plen : nullptr;
+        a.group_lists = db->grid <= 8 * 63 ? db->group_lists : nullptr;
+        a.tickets = db->tickets;
         cudaError_t err = dbq::launch_scan_packed(a, db->grid, s);
         if (err != cudaSuccess) return cuda_fail(err, "scan_packed launch");
         return DBQ_OK;
@@ -676,6 +682,10 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
         rc = dev_alloc(db, &db->cand, (size_t)db->grid * kMaxK * sizeof(dbq::Cand),
                        "candidate lists");
     if (!rc) rc = dev_alloc(db, &db->ticket, sizeof(unsigned int), "ticket");
+    if (!rc)
+        rc = dev_alloc(db, &db->group_lists,
+                       (size_t)((db->grid + 7) / 8) * kMaxK * sizeof(dbq::Cand), "group lists");
+    if (!rc) rc = dev_alloc(db, &db->tickets, 64 * sizeof(unsigned int), "merge tickets");
     if (!rc) rc = dev_alloc(db, &db->hits_dev, (size_t)kMaxK * sizeof(dbq::Hit), "hits");
     if (!rc) {
         cudaError_t err = cudaMallocHost(reinterpret_cast<void**>(&db->hits_host),
@@ -688,6 +698,7 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
     }
     if (!rc) {
         cudaError_t err = cudaMemset(db->ticket, 0, sizeof(unsigned int));
+        if (err == cudaSuccess) err = cudaMemset(db->tickets, 0, 64 * sizeof(unsigned int));
         if (err == cudaSuccess && db->ecount)
             err = cudaMemset(db->ecount, 0, (size_t)capacity * 2 * sizeof(uint32_t));
         if (err == cudaSuccess && db->vols16)   // zero padding never reaches a threshold
@@ -1382,8 +1393,10 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
         DBQ_CUDA(cudaEventRecord(p->copied, s));
         p->copy_pending = true;
     }
+    bool any_sparse = false;
+    for (int q = 0; q < nq; ++q) any_sparse |= p->dbs[db_of_query[q]]->sparse;
     cudaError_t err = dbq::launch_scan_tasks(p->tasks_dev, p->items_dev, nitems, p->counter,
-                                             p->sms, s);
+                                             p->sms, any_sparse, s);
     if (err != cudaSuccess) return cuda_fail(err, "task scan launch");
     return DBQ_OK;
 }

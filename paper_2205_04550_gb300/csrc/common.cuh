@@ -11,7 +11,12 @@
 
 namespace dbq {
 
-constexpr double kSentinelScore = -1.0e308;         // below every score and every -distance
+// Ranking keys are unsigned 64-bit integers whose order is the ranking order:
+// a non-negative binary64 score's bit pattern (Dice scores are >= 0), or the
+// complement of a non-negative binary32 distance's bit pattern (smaller
+// distance = larger key).  Integer compares keep the top-k off the slow
+// FP64 pipe.  The sentinel key 0 with the largest index loses to everything.
+constexpr uint64_t kSentinelKey = 0ull;
 constexpr int64_t kSentinelIndex = INT64_MAX;
 
 // Device-side copy of dbq_hit (same layout as the C ABI struct).
@@ -24,15 +29,30 @@ static_assert(sizeof(Hit) == 40, "Hit must match dbq_hit");
 
 // One candidate of a per-CTA list; pay0/pay1 carry the entry's counts.
 struct Cand {
-    double score;
+    uint64_t key;
     int64_t index;
     uint64_t pay0;
     uint64_t pay1;
 };
 
-__device__ __forceinline__ bool better(double sa, int64_t ia, double sb, int64_t ib)
+__device__ __forceinline__ bool better(uint64_t ka, int64_t ia, uint64_t kb, int64_t ib)
 {
-    return sa > sb || (sa == sb && ia < ib);
+    return ka > kb || (ka == kb && ia < ib);
+}
+
+__device__ __forceinline__ uint64_t score_key(double score)   // score >= 0
+{
+    return (uint64_t)__double_as_longlong(score);
+}
+
+__device__ __forceinline__ double key_score(uint64_t key)
+{
+    return __longlong_as_double((long long)key);
+}
+
+__device__ __forceinline__ uint64_t distance_key(float d)      // d >= 0
+{
+    return (uint64_t)(~__float_as_uint(d));
 }
 
 // Streaming 128-bit load: read-only path, no L1 allocation, 256-byte L2

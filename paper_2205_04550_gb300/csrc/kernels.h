@@ -54,6 +54,8 @@ struct ScanPackedArgs {
     uint32_t* counts_out;     // [n][4] per-entry (I1, I2, E1, E2), or null
     const uint32_t* sup_list; // [2][wp4] patient support lists, or null for the dense scan
     const uint32_t* sup_len;  // [2]
+    Cand* group_lists;        // [ceil(grid / 8)][k]: two-level merge; null = one-level
+    unsigned int* tickets;    // [1 + ceil(grid / 8)] counters of the two-level merge
 };
 
 // Grid size (CTAs) the scan uses on this device, and its shared memory bytes.
@@ -163,10 +165,12 @@ struct QueryTask {
     unsigned int* ticket;       // zero between launches
     Hit* hits;                  // [k]
 };
-size_t scan_tasks_smem();
-// items[i] = (task, slice); next_item is a device counter (cleared here).
+size_t scan_tasks_smem(bool sparse);
+// items[i] = (task, slice); next_item is a device counter (cleared here);
+// any_sparse: some task has support lists.
 cudaError_t launch_scan_tasks(const QueryTask* tasks, const int2* items, int nitems,
-                              unsigned int* next_item, int grid, cudaStream_t stream);
+                              unsigned int* next_item, int grid, bool any_sparse,
+                              cudaStream_t stream);
 
 // Nearest-neighbour downsampling of `rows` bit planes (rows = entries * 2)
 // of an nx x ny x nz grid by factor f: dst [rows][dst_wp], sizes [rows]

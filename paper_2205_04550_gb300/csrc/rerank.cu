@@ -26,7 +26,10 @@ rerank_kernel(const RerankArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TopK tk;
-    uint32_t* icnt = reinterpret_cast<uint32_t*>(topk_carve(tk, smem_raw));   // [kGroupMax][2]
+    unsigned char* after_topk = topk_carve(tk, smem_raw);
+    uint32_t* icnt = reinterpret_cast<uint32_t*>(after_topk);                  // [kGroupMax][2]
+    int* next = reinterpret_cast<int*>(after_topk + (size_t)kGroupMax * 2 * sizeof(uint32_t));
+    unsigned char* cache_raw = after_topk + (size_t)kGroupMax * 2 * sizeof(uint32_t) + 16;
     const int tid = threadIdx.x;
     const int per = (a.c + a.slices - 1) / a.slices;
     const int items = a.nq * a.slices;
@@ -42,23 +45,30 @@ rerank_kernel(const RerankArgs a)
         const uint32_t P2 = a.pcounts[2 * q + 1];
         topk_init(tk);
         for (int i = tid; i < 2 * kGroupMax; i += kScanThreads) icnt[i] = 0u;
+        if (tid == 0) *next = 0;
         __syncthreads();
         if (gn > 0) {
             Support sup;
+            bool warp_mode = false;
+            SupportCache cache;
             if (kSparse) {
                 sup.list1 = a.sup_lists + (int64_t)q * 2 * a.wp4;
                 sup.list2 = sup.list1 + a.wp4;
                 sup.len = a.sup_lens + 2 * q;
+                warp_mode = load_support_cache(cache_raw, patient, a.wp4, sup, cache);
             }
-            count_group<U, EPI, kSparse>(a.planes, a.wp4, a.chunk4, a.nchunks, patient, list, 0,
-                                         gn, icnt, sup);
+            if (warp_mode)
+                count_group_warps(a.planes, a.wp4, list, 0, gn, icnt, cache, next);
+            else
+                count_group<U, EPI, kSparse>(a.planes, a.wp4, a.chunk4, a.nchunks, patient, list,
+                                             0, gn, icnt, sup);
         }
         __syncthreads();
         for (int i = tid; i < gn; i += kScanThreads) {
             const int64_t e = list[i];
             const uint32_t I1 = icnt[2 * i], I2 = icnt[2 * i + 1];
             const uint2 E = ecount2[e];
-            topk_offer(tk, a.k, score_rn(I1, I2, E.x, E.y, P1, P2), e,
+            topk_offer(tk, a.k, score_key(score_rn(I1, I2, E.x, E.y, P1, P2)), e,
                        (uint64_t)I1 | ((uint64_t)I2 << 32), (uint64_t)E.x | ((uint64_t)E.y << 32));
         }
         topk_flush(tk, a.k);
@@ -68,7 +78,7 @@ rerank_kernel(const RerankArgs a)
             for (int j = tid; j < a.k; j += kScanThreads) {
                 Hit h;
                 h.index = tk.idx[j];
-                h.score = tk.key[j];
+                h.score = key_score(tk.key[j]);
                 h.i1 = (uint32_t)(tk.pay0[j] & 0xffffffffu);
                 h.i2 = (uint32_t)(tk.pay0[j] >> 32);
                 h.e1 = (uint32_t)(tk.pay1[j] & 0xffffffffu);
@@ -89,7 +99,8 @@ cudaError_t launch_rerank(const RerankArgs& a, cudaStream_t stream)
     if (a.nq < 1 || a.c < 1 || a.k < 1 || a.k > a.c || a.slices < 1 ||
         (a.c + a.slices - 1) / a.slices > kGroupMax)
         return cudaErrorInvalidValue;
-    const size_t smem = topk_smem_bytes() + (size_t)kGroupMax * 2 * sizeof(uint32_t);
+    const size_t smem = topk_smem_bytes() + (size_t)kGroupMax * 2 * sizeof(uint32_t) + 16 +
+                        (a.sup_lists ? kSupportCacheBytes : 0);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

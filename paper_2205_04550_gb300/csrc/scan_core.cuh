@@ -96,4 +96,96 @@ __device__ __forceinline__ void count_group(const uint4* __restrict__ planes, in
     }
 }
 
+// ---- sparse scan, one warp per entry
+//
+// When the patient's support is small, a CTA-wide pass per entry leaves most
+// threads idle.  Instead the support (word offsets and the patient's words
+// there) is cached in shared memory once, and each warp scans whole entries:
+// lane l visits support positions l, l + 32, ... of both planes, four loads
+// in flight per plane, and the warp's sums go straight to the entry's
+// counters (no atomics: one warp owns an entry).
+
+// Shared-memory cache of one patient's support: 20 bytes per position.
+// Positions [0, len1) belong to plane 1, [len1, len1 + len2) to plane 2;
+// off[] holds word offsets from the start of an entry (plane 2 offsets
+// include the plane stride), pw[] the patient's words there.
+struct SupportCache {
+    const uint32_t* off;
+    const uint4* pw;
+    int len1;
+    int len2;
+};
+
+constexpr int kSupportCacheBytes = 150 * 1024;
+constexpr int kSupportCachePositions = kSupportCacheBytes / 20;
+
+// Fill the cache from the support lists (all threads; ends with a barrier).
+// Returns false, without filling, if the support does not fit.
+__device__ __forceinline__ bool load_support_cache(unsigned char* raw, const uint4* patient,
+                                                   int wp4, const Support& sup, SupportCache& c)
+{
+    const int l1 = (int)sup.len[0], l2 = (int)sup.len[1];
+    if (l1 + l2 > kSupportCachePositions) return false;
+    uint4* pw = reinterpret_cast<uint4*>(raw);                 // [l1 + l2]
+    uint32_t* off = reinterpret_cast<uint32_t*>(pw + (l1 + l2));
+    for (int j = threadIdx.x; j < l1 + l2; j += blockDim.x) {
+        const uint32_t o = j < l1 ? sup.list1[j] : (uint32_t)wp4 + sup.list2[j - l1];
+        off[j] = o;
+        pw[j] = patient[o];
+    }
+    c.off = off;
+    c.pw = pw;
+    c.len1 = l1;
+    c.len2 = l2;
+    __syncthreads();
+    return true;
+}
+
+// icnt[2 * i + k] = I_k of entry i of the group (written, not added); the
+// entries are list[g0 + i] or g0 + i.  Warps take entries from the shared
+// counter `next` (zeroed by the caller before a barrier); lane l visits
+// positions l, l + 32, ... of both planes, eight loads in flight.  Ends
+// without a barrier.
+__device__ __forceinline__ void count_group_warps(const uint4* __restrict__ planes, int wp4,
+                                                  const int32_t* __restrict__ list, int64_t g0,
+                                                  int gn, uint32_t* icnt, const SupportCache& c,
+                                                  int* next)
+{
+    const int lane = threadIdx.x & 31;
+    const int total = c.len1 + c.len2;
+    for (;;) {
+        int i = 0;
+        if (lane == 0) i = atomicAdd(next, 1);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= gn) break;
+        int64_t e = g0 + i;
+        if (list) e = list[e];
+        const uint4* base = planes + e * 2 * wp4;
+        uint32_t a1 = 0, a2 = 0;
+        int j = lane;
+        for (; j + 7 * 32 < total; j += 8 * 32) {
+            uint4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = ld_stream(base + c.off[j + 32 * u]);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t cnt = popc_and4(v[u], c.pw[j + 32 * u]);
+                if (j + 32 * u < c.len1) a1 += cnt;
+                else a2 += cnt;
+            }
+        }
+        for (; j < total; j += 32) {
+            const uint32_t cnt = popc_and4(ld_stream(base + c.off[j]), c.pw[j]);
+            if (j < c.len1) a1 += cnt;
+            else a2 += cnt;
+        }
+        const uint32_t s1 = __reduce_add_sync(0xffffffffu, a1);
+        const uint32_t s2 = __reduce_add_sync(0xffffffffu, a2);
+        if (lane == 0) {
+            icnt[2 * i] = s1;
+            icnt[2 * i + 1] = s2;
+        }
+    }
+}
+
 }  // namespace dbq

@@ -173,7 +173,7 @@ scan_f16_kernel(const ScanF16Args a)
             if (a.counts_out)
                 reinterpret_cast<uint4*>(a.counts_out)[e] = make_uint4(I1, I2, E1, E2);
             if (want_topk)
-                topk_offer(tk, k, score_rn(I1, I2, E1, E2, P1, P2), e,
+                topk_offer(tk, k, score_key(score_rn(I1, I2, E1, E2, P1, P2)), e,
                            (uint64_t)I1 | ((uint64_t)I2 << 32),
                            (uint64_t)E1 | ((uint64_t)E2 << 32));
         }
@@ -186,7 +186,7 @@ scan_f16_kernel(const ScanF16Args a)
     for (int j = tid; j < k; j += kThreads) {
         Hit h;
         h.index = tk.idx[j];
-        h.score = tk.key[j];
+        h.score = key_score(tk.key[j]);
         h.i1 = (uint32_t)(tk.pay0[j] & 0xffffffffu);
         h.i2 = (uint32_t)(tk.pay0[j] >> 32);
         h.e1 = (uint32_t)(tk.pay1[j] & 0xffffffffu);

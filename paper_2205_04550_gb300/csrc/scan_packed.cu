@@ -40,7 +40,10 @@ scan_packed_kernel(const ScanPackedArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TopK tk;
-    uint32_t* icnt = reinterpret_cast<uint32_t*>(topk_carve(tk, smem_raw));   // [kGroup][2]
+    unsigned char* after_topk = topk_carve(tk, smem_raw);
+    uint32_t* icnt = reinterpret_cast<uint32_t*>(after_topk);                  // [kGroup][2]
+    unsigned char* cache_raw = after_topk + (size_t)kGroup * 2 * sizeof(uint32_t) + 16;
+    int* next = reinterpret_cast<int*>(after_topk + (size_t)kGroup * 2 * sizeof(uint32_t));
     const int tid = threadIdx.x;
     const int k = a.k;
     const bool want_topk = a.hits != nullptr;
@@ -49,19 +52,26 @@ scan_packed_kernel(const ScanPackedArgs a)
     const uint32_t P1 = a.pcount[0];
     const uint32_t P2 = a.pcount[1];
     const uint2* ecount2 = reinterpret_cast<const uint2*>(a.ecount);
+    Support sup;
+    sup.list1 = a.sup_list;
+    sup.list2 = a.sup_list + a.wp4;
+    sup.len = a.sup_len;
+    SupportCache cache;
+    bool warp_mode = false;
+    if (kSparse) warp_mode = load_support_cache(cache_raw, a.patient, a.wp4, sup, cache);
 
     topk_init(tk);
 
     for (int64_t g0 = e_begin; g0 < e_end; g0 += kGroup) {
         const int gn = (int)((e_end - g0) < kGroup ? (e_end - g0) : kGroup);
         for (int i = tid; i < 2 * kGroup; i += kThreads) icnt[i] = 0u;
+        if (tid == 0) *next = 0;
         __syncthreads();
-        Support sup;
-        sup.list1 = a.sup_list;
-        sup.list2 = a.sup_list + a.wp4;
-        sup.len = a.sup_len;
-        count_group<U, EPI, kSparse>(a.planes, a.wp4, a.chunk4, a.nchunks, a.patient, nullptr, g0,
-                                     gn, icnt, sup);
+        if (warp_mode)
+            count_group_warps(a.planes, a.wp4, nullptr, g0, gn, icnt, cache, next);
+        else
+            count_group<U, EPI, kSparse>(a.planes, a.wp4, a.chunk4, a.nchunks, a.patient,
+                                         nullptr, g0, gn, icnt, sup);
         __syncthreads();   // the group's counters are complete
         for (int i = tid; i < gn; i += kThreads) {
             const int64_t e = g0 + i;
@@ -71,7 +81,7 @@ scan_packed_kernel(const ScanPackedArgs a)
             if (a.counts_out)
                 reinterpret_cast<uint4*>(a.counts_out)[e] = make_uint4(I1, I2, E.x, E.y);
             if (want_topk)
-                topk_offer(tk, k, score_rn(I1, I2, E.x, E.y, P1, P2), e,
+                topk_offer(tk, k, score_key(score_rn(I1, I2, E.x, E.y, P1, P2)), e,
                            (uint64_t)I1 | ((uint64_t)I2 << 32),
                            (uint64_t)E.x | ((uint64_t)E.y << 32));
         }
@@ -79,12 +89,16 @@ scan_packed_kernel(const ScanPackedArgs a)
         else __syncthreads();
     }
     if (!want_topk) return;
-    if (!topk_publish(tk, k, a.cand, a.ticket)) return;
-    topk_merge_published(tk, k, a.cand, (int64_t)gridDim.x * k);
+    if (a.group_lists) {
+        if (!topk_publish_two_level(tk, k, a.cand, a.group_lists, a.tickets)) return;
+    } else {
+        if (!topk_publish(tk, k, a.cand, a.ticket)) return;
+        topk_merge_published(tk, k, a.cand, (int64_t)gridDim.x * k);
+    }
     for (int j = tid; j < k; j += kThreads) {
         Hit h;
         h.index = tk.idx[j];
-        h.score = tk.key[j];
+        h.score = key_score(tk.key[j]);
         h.i1 = (uint32_t)(tk.pay0[j] & 0xffffffffu);
         h.i2 = (uint32_t)(tk.pay0[j] >> 32);
         h.e1 = (uint32_t)(tk.pay1[j] & 0xffffffffu);
@@ -100,7 +114,7 @@ scan_packed_kernel(const ScanPackedArgs a)
 size_t scan_packed_smem(int chunk4)
 {
     (void)chunk4;   // the patient lives in registers
-    return topk_smem_bytes() + (size_t)kGroup * 2 * sizeof(uint32_t);
+    return topk_smem_bytes() + (size_t)kGroup * 2 * sizeof(uint32_t) + 16;
 }
 
 void scan_packed_chunking(int wp4, int* chunk4, int* nchunks)
@@ -124,7 +138,8 @@ int scan_packed_grid(int device)
 
 cudaError_t launch_scan_packed(const ScanPackedArgs& a, int grid, cudaStream_t stream)
 {
-    const size_t smem = scan_packed_smem(a.chunk4);
+    // the sparse variant also holds the patient's support in shared memory
+    const size_t smem = scan_packed_smem(a.chunk4) + (a.sup_list ? kSupportCacheBytes : 0);
     auto run = [&](auto kern) -> cudaError_t {
         cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                (int)smem);

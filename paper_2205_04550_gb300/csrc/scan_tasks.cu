@@ -18,10 +18,10 @@ namespace {
 
 constexpr int kGroup = 1024;
 
-template <int U, int EPI>
+template <int U, int EPI, bool kSparse>
 __device__ __forceinline__ void count_task(const QueryTask& t, int64_t g0, int gn, uint32_t* icnt)
 {
-    if (t.sup_list) {
+    if (kSparse && t.sup_list) {
         Support sup;
         sup.list1 = t.sup_list;
         sup.list2 = t.sup_list + t.wp4;
@@ -34,13 +34,20 @@ __device__ __forceinline__ void count_task(const QueryTask& t, int64_t g0, int g
     }
 }
 
+// kSparse: the launch holds queries with support lists (warp-per-entry path
+// compiled in); the dense-only instantiation keeps its registers for the
+// CTA-wide loop.
+template <bool kSparse>
 __global__ void __launch_bounds__(kScanThreads, 1)
 scan_tasks_kernel(const QueryTask* __restrict__ tasks, const int2* __restrict__ items, int nitems,
                   unsigned int* __restrict__ next_item)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TopK tk;
-    uint32_t* icnt = reinterpret_cast<uint32_t*>(topk_carve(tk, smem_raw));   // [kGroup][2]
+    unsigned char* after_topk = topk_carve(tk, smem_raw);
+    uint32_t* icnt = reinterpret_cast<uint32_t*>(after_topk);                  // [kGroup][2]
+    int* next = reinterpret_cast<int*>(after_topk + (size_t)kGroup * 2 * sizeof(uint32_t));
+    unsigned char* cache_raw = after_topk + (size_t)kGroup * 2 * sizeof(uint32_t) + 16;
     __shared__ int item_s;
     __shared__ QueryTask task_s;
     const int tid = threadIdx.x;
@@ -60,18 +67,30 @@ scan_tasks_kernel(const QueryTask* __restrict__ tasks, const int2* __restrict__ 
         const uint32_t P1 = t.pcount[0], P2 = t.pcount[1];
         const uint2* ecount2 = reinterpret_cast<const uint2*>(t.ecount);
         topk_init(tk);
+        SupportCache cache;
+        bool warp_mode = false;
+        if (kSparse && t.sup_list) {
+            Support sup;
+            sup.list1 = t.sup_list;
+            sup.list2 = t.sup_list + t.wp4;
+            sup.len = t.sup_len;
+            warp_mode = load_support_cache(cache_raw, t.patient, t.wp4, sup, cache);
+        }
         for (int64_t g0 = e_begin; g0 < e_end; g0 += kGroup) {
             const int gn = (int)((e_end - g0) < kGroup ? (e_end - g0) : kGroup);
             for (int i = tid; i < 2 * kGroup; i += kScanThreads) icnt[i] = 0u;
+            if (tid == 0) *next = 0;
             __syncthreads();
-            if (t.chunk4 <= kScanThreads) count_task<1, 4>(t, g0, gn, icnt);
-            else count_task<2, 2>(t, g0, gn, icnt);
+            if (kSparse && warp_mode)
+                count_group_warps(t.planes, t.wp4, nullptr, g0, gn, icnt, cache, next);
+            else if (t.chunk4 <= kScanThreads) count_task<1, 4, kSparse>(t, g0, gn, icnt);
+            else count_task<2, 2, kSparse>(t, g0, gn, icnt);
             __syncthreads();
             for (int i = tid; i < gn; i += kScanThreads) {
                 const int64_t e = g0 + i;
                 const uint32_t I1 = icnt[2 * i], I2 = icnt[2 * i + 1];
                 const uint2 E = ecount2[e];
-                topk_offer(tk, t.k, score_rn(I1, I2, E.x, E.y, P1, P2), e,
+                topk_offer(tk, t.k, score_key(score_rn(I1, I2, E.x, E.y, P1, P2)), e,
                            (uint64_t)I1 | ((uint64_t)I2 << 32),
                            (uint64_t)E.x | ((uint64_t)E.y << 32));
             }
@@ -82,7 +101,7 @@ scan_tasks_kernel(const QueryTask* __restrict__ tasks, const int2* __restrict__ 
             for (int j = tid; j < t.k; j += kScanThreads) {
                 Hit h;
                 h.index = tk.idx[j];
-                h.score = tk.key[j];
+                h.score = key_score(tk.key[j]);
                 h.i1 = (uint32_t)(tk.pay0[j] & 0xffffffffu);
                 h.i2 = (uint32_t)(tk.pay0[j] >> 32);
                 h.e1 = (uint32_t)(tk.pay1[j] & 0xffffffffu);
@@ -98,19 +117,25 @@ scan_tasks_kernel(const QueryTask* __restrict__ tasks, const int2* __restrict__ 
 
 }  // namespace
 
-size_t scan_tasks_smem() { return topk_smem_bytes() + (size_t)kGroup * 2 * sizeof(uint32_t); }
+size_t scan_tasks_smem(bool sparse)
+{
+    return topk_smem_bytes() + (size_t)kGroup * 2 * sizeof(uint32_t) + 16 +
+           (sparse ? kSupportCacheBytes : 0);
+}
 
 cudaError_t launch_scan_tasks(const QueryTask* tasks, const int2* items, int nitems,
-                              unsigned int* next_item, int grid, cudaStream_t stream)
+                              unsigned int* next_item, int grid, bool any_sparse,
+                              cudaStream_t stream)
 {
     if (nitems <= 0) return cudaSuccess;
-    const size_t smem = scan_tasks_smem();
-    cudaError_t err = cudaFuncSetAttribute(scan_tasks_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = scan_tasks_smem(any_sparse);
+    auto kern = any_sparse ? scan_tasks_kernel<true> : scan_tasks_kernel<false>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
     if (err != cudaSuccess) return err;
     err = cudaMemsetAsync(next_item, 0, sizeof(unsigned int), stream);
     if (err != cudaSuccess) return err;
-    scan_tasks_kernel<<<grid, kScanThreads, smem, stream>>>(tasks, items, nitems, next_item);
+    kern<<<grid, kScanThreads, smem, stream>>>(tasks, items, nitems, next_item);
     return cudaGetLastError();
 }
 

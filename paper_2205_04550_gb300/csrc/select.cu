@@ -4,8 +4,9 @@
 // embedding query; the prefilter keeps the c smallest for exact re-ranking).
 //
 // One 512-thread CTA per query streams its row of distances and keeps a
-// running top-c with the shared-memory routines of topk.cuh; the key is -L
-// so that "better" means "closer", and ties go to the lower index.
+// running top-c with the shared-memory routines of topk.cuh; the key is the
+// complement of L's bit pattern so that "better" means "closer", and ties
+// go to the lower index.
 #include "kernels.h"
 #include "topk.cuh"
 
@@ -29,7 +30,7 @@ select_smallest_kernel(const float* __restrict__ dist, int64_t n, int c, int32_t
     const int room = kTopkCap - c;            // append slots
     for (int64_t r0 = 0; r0 < n; r0 += kSelectThreads) {
         const int64_t e = r0 + threadIdx.x;
-        if (e < n) topk_offer(tk, c, -(double)__ldcs(row + e), e, 0, 0);
+        if (e < n) topk_offer(tk, c, distance_key(__ldcs(row + e)), e, 0, 0);
         __syncthreads();
         const int added = tk.misc[0];
         __syncthreads();   // every thread has read the count before the next round appends

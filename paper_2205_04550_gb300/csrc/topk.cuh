@@ -24,7 +24,7 @@ namespace dbq {
 constexpr int kTopkCap = 2048;
 
 struct TopK {
-    double* key;      // [kTopkCap]
+    uint64_t* key;    // [kTopkCap] ranking keys (see common.cuh)
     int64_t* idx;     // [kTopkCap]
     uint64_t* pay0;   // [kTopkCap]
     uint64_t* pay1;   // [kTopkCap]
@@ -36,8 +36,8 @@ constexpr size_t topk_smem_bytes() { return (size_t)kTopkCap * 32 + 4 * sizeof(i
 // Carve a TopK from `p` (8-byte aligned); returns the first byte after it.
 __device__ __forceinline__ unsigned char* topk_carve(TopK& t, unsigned char* p)
 {
-    t.key = reinterpret_cast<double*>(p);
-    p += kTopkCap * sizeof(double);
+    t.key = reinterpret_cast<uint64_t*>(p);
+    p += kTopkCap * sizeof(uint64_t);
     t.idx = reinterpret_cast<int64_t*>(p);
     p += kTopkCap * sizeof(int64_t);
     t.pay0 = reinterpret_cast<uint64_t*>(p);
@@ -51,7 +51,7 @@ __device__ __forceinline__ unsigned char* topk_carve(TopK& t, unsigned char* p)
 
 __device__ __forceinline__ void topk_clear_slot(TopK& t, int i)
 {
-    t.key[i] = kSentinelScore;
+    t.key[i] = kSentinelKey;
     t.idx[i] = kSentinelIndex;
     t.pay0[i] = 0;
     t.pay1[i] = 0;
@@ -65,12 +65,12 @@ __device__ __forceinline__ void topk_init(TopK& t)
     __syncthreads();
 }
 
-__device__ __forceinline__ void topk_offer(TopK& t, int k, double score, int64_t index,
+__device__ __forceinline__ void topk_offer(TopK& t, int k, uint64_t key, int64_t index,
                                            uint64_t p0, uint64_t p1)
 {
-    if (better(score, index, t.key[k - 1], t.idx[k - 1])) {
+    if (better(key, index, t.key[k - 1], t.idx[k - 1])) {
         const int pos = k + atomicAdd(&t.misc[0], 1);
-        t.key[pos] = score;
+        t.key[pos] = key;
         t.idx[pos] = index;
         t.pay0[pos] = p0;
         t.pay1[pos] = p1;
@@ -87,7 +87,7 @@ __device__ __forceinline__ void bitonic_sort_topk(TopK& t, int n)
                 const bool up = (lo & size) == 0;
                 const bool hi_better = better(t.key[hi], t.idx[hi], t.key[lo], t.idx[lo]);
                 if (hi_better == up) {
-                    const double kk = t.key[lo]; t.key[lo] = t.key[hi]; t.key[hi] = kk;
+                    const uint64_t kk = t.key[lo]; t.key[lo] = t.key[hi]; t.key[hi] = kk;
                     const int64_t ii = t.idx[lo]; t.idx[lo] = t.idx[hi]; t.idx[hi] = ii;
                     const uint64_t a = t.pay0[lo]; t.pay0[lo] = t.pay0[hi]; t.pay0[hi] = a;
                     const uint64_t b = t.pay1[lo]; t.pay1[lo] = t.pay1[hi]; t.pay1[hi] = b;
@@ -123,7 +123,7 @@ __device__ __forceinline__ bool topk_publish_slot(TopK& t, int k, Cand* dst, int
     Cand* mine = dst + (int64_t)slot * k;
     for (int j = threadIdx.x; j < k; j += blockDim.x) {
         Cand c;
-        c.score = t.key[j];
+        c.key = t.key[j];
         c.index = t.idx[j];
         c.pay0 = t.pay0[j];
         c.pay1 = t.pay1[j];
@@ -159,19 +159,46 @@ __device__ __forceinline__ void topk_merge_published(TopK& t, int k, const Cand*
             const int64_t r = r0 + j;
             if (r < m) {
                 const Cand* src = cand + r;
-                const double sc = __ldcg(&src->score);
+                const unsigned long long sc =
+                    __ldcg(reinterpret_cast<const unsigned long long*>(&src->key));
                 const long long ix = __ldcg(reinterpret_cast<const long long*>(&src->index));
                 if (ix != kSentinelIndex) {
                     const unsigned long long p0 =
                         __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay0));
                     const unsigned long long p1 =
                         __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay1));
-                    topk_offer(t, k, sc, (int64_t)ix, (uint64_t)p0, (uint64_t)p1);
+                    topk_offer(t, k, (uint64_t)sc, (int64_t)ix, (uint64_t)p0, (uint64_t)p1);
                 }
             }
         }
         topk_flush(t, k);
     }
+}
+
+constexpr int kMergeGroup = 8;   // CTAs per first-level merge group
+
+// Two-level publication for a grid of CTAs: every CTA publishes its list to
+// cand[blockIdx.x * k]; the last CTA to finish in each group of kMergeGroup
+// merges its group's lists into group_lists[group * k] (while other CTAs may
+// still be scanning), and the last group merger merges the group lists.
+// tickets[0] is the top-level counter, tickets[1 + g] group g's (all zero
+// between launches).  Returns true, in every thread, in the CTA that then
+// holds the final list in slots [0, k).
+__device__ __forceinline__ bool topk_publish_two_level(TopK& t, int k, Cand* cand,
+                                                       Cand* group_lists, unsigned int* tickets)
+{
+    const int group = blockIdx.x / kMergeGroup;
+    const int first = group * kMergeGroup;
+    const int members = min(kMergeGroup, (int)gridDim.x - first);
+    const int ngroups = ((int)gridDim.x + kMergeGroup - 1) / kMergeGroup;
+    if (!topk_publish_slot(t, k, cand + (int64_t)first * k, blockIdx.x - first, members,
+                           tickets + 1 + group))
+        return false;
+    topk_merge_published(t, k, cand + (int64_t)first * k, (int64_t)members * k);
+    if (!topk_publish_slot(t, k, group_lists, group, ngroups, tickets))
+        return false;
+    topk_merge_published(t, k, group_lists, (int64_t)ngroups * k);
+    return true;
 }
 
 }  // namespace dbq
