@@ -230,3 +230,27 @@ def test_prefilter_errors(torch):
         with pytest.raises(DbqError) as e:           # 64 dims do not tile FP8's 128-byte K
             db.query_batch([pat], 1, DBQ_MODE_EMBED_FP8, 10)
         assert e.value.status == _dbq.DBQ_EINVAL
+
+
+@pytest.mark.parametrize("dup", [0, 250])
+def test_candidates_are_the_smallest_gpu_distances_with_index_ties(torch, dup):
+    """Selection property on the GPU's own distances: the candidates are the
+    c smallest under (distance, index), ascending -- including a cut inside a
+    large group of equal distances (identical entries)."""
+    shape = (64, 32, 64)
+    n, c = 1200, 64
+    vols, pats, _ = _surrogate(shape, n, 4)
+    if dup:
+        vols[300:300 + dup] = vols[299]
+    with Database(shape, n, DBQ_STORE_BITS, T1, T2, embed=True) as db:
+        db.load(0, vols)
+        db.build()
+        for mode in (DBQ_MODE_EMBED_BF16, DBQ_MODE_EMBED_FP8):
+            pq = list(pats) + [vols[299].copy()]
+            dist, cand = db.prefilter(pq, mode, c)
+            for q in range(len(pq)):
+                want = np.lexsort((np.arange(n), dist[q]))[:c]
+                np.testing.assert_array_equal(cand[q], want)
+    if dup:
+        # the copy of entry 299 sees dup + 1 equal best distances: lowest indices first
+        assert list(want[:dup + 1][:c]) == list(range(299, 299 + min(c, dup + 1)))
