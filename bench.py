@@ -75,7 +75,8 @@ DEFAULT_WORKLOAD = "exact_packed_50k_128"
 # small case (summaries in profiles/), per entry read plus fixed writes; valid
 # only while the kernel's sources hash to the captured version.
 TRAFFIC = {
-    "scan_packed_kernel": dict(files=("scan_packed.cu", "topk.cuh", "common.cuh"),
+    "scan_packed_kernel": dict(files=("scan_packed.cu", "scan_core.cuh", "topk.cuh",
+                                      "common.cuh"),
                                sha="7327dbf9102ae100", entries=2000,
                                read_bytes=1049188352, write_bytes=3352320,
                                capture="profiles/scan_packed_2k_128_ncu_full.md"),

@@ -162,22 +162,24 @@ __device__ __forceinline__ void count_group_warps(const uint4* __restrict__ plan
         if (list) e = list[e];
         const uint4* base = planes + e * 2 * wp4;
         uint32_t a1 = 0, a2 = 0;
-        int j = lane;
-        for (; j + 7 * 32 < total; j += 8 * 32) {
+        // eight predicated loads per iteration, so the last partial round
+        // also has all of its loads in flight at once
+        for (int j = lane; j < total; j += 8 * 32) {
             uint4 v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = ld_stream(base + c.off[j + 32 * u]);
+            for (int u = 0; u < 8; ++u) {
+                const int p = j + 32 * u;
+                v[u] = p < total ? ld_stream(base + c.off[p]) : make_uint4(0, 0, 0, 0);
+            }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
-                const uint32_t cnt = popc_and4(v[u], c.pw[j + 32 * u]);
-                if (j + 32 * u < c.len1) a1 += cnt;
-                else a2 += cnt;
+                const int p = j + 32 * u;
+                if (p < total) {
+                    const uint32_t cnt = popc_and4(v[u], c.pw[p]);
+                    if (p < c.len1) a1 += cnt;
+                    else a2 += cnt;
+                }
             }
-        }
-        for (; j < total; j += 32) {
-            const uint32_t cnt = popc_and4(ld_stream(base + c.off[j]), c.pw[j]);
-            if (j < c.len1) a1 += cnt;
-            else a2 += cnt;
         }
         const uint32_t s1 = __reduce_add_sync(0xffffffffu, a1);
         const uint32_t s2 = __reduce_add_sync(0xffffffffu, a2);
