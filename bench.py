@@ -81,8 +81,8 @@ TRAFFIC = {
                                read_bytes=1049188352, write_bytes=3352320,
                                capture="profiles/scan_packed_2k_128_ncu_full.md"),
     "scan_f16_kernel": dict(files=("scan_f16.cu", "topk.cuh", "common.cuh"),
-                            sha="0d144eaf8bf7f42c", entries=4000,
-                            read_bytes=2097310464, write_bytes=3112192,
+                            sha="96842491439226c1", entries=4000,
+                            read_bytes=2097512192, write_bytes=3325440,
                             capture="profiles/scan_f16_4k_64_ncu_full.md"),
 }
 METRIC = "DB entries/s per query (HBM GB/s vs peak); batched queries/s at top-1 match"
