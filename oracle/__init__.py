@@ -96,6 +96,13 @@ def _load():
         lib.oracle_e4m3_code.restype = ctypes.c_uint8
         lib.oracle_embed.argtypes = [P, i32, i32, i32, i32, P, P, P]
         lib.oracle_embed.restype = i32
+        lib.oracle_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.oracle_splitmix64.restype = ctypes.c_uint64
+        lib.oracle_sketch.argtypes = [P, i64, i32, P]
+        lib.oracle_sketch.restype = i32
+        lib.oracle_sign_code.argtypes = [P, i32, P]
+        lib.oracle_hamming.argtypes = [P, P, i64]
+        lib.oracle_hamming.restype = i64
         _lib = lib
         return lib
 
@@ -275,6 +282,46 @@ def embed(mask: np.ndarray, nx: int, ny: int, nz: int, f: int = 8):
     if lib.oracle_embed(_p(m), nx, ny, nz, f, _p(b), _p(q), _p(sc)) != d:
         raise ValueError("grid not divisible by block size")
     return b, q, np.float32(sc[0])
+
+
+def splitmix64(key: int, i: int) -> int:
+    return _load().oracle_splitmix64(key, i)
+
+
+def sketch(mask: np.ndarray, d: int = 4096) -> np.ndarray:
+    """Count sketch [d] int32 of one byte mask [V] (see oracle.c)."""
+    lib = _load()
+    m = _c(mask.reshape(-1), np.uint8)
+    out = np.empty(d, dtype=np.int32)
+    if lib.oracle_sketch(_p(m), m.size, d, _p(out)) != 0:
+        raise ValueError("d must be a power of two")
+    return out
+
+
+def sign_code(sk: np.ndarray) -> np.ndarray:
+    lib = _load()
+    a = _c(sk, np.int32)
+    out = np.empty(a.size // 32, dtype=np.uint32)
+    lib.oracle_sign_code(_p(a), a.size, _p(out))
+    return out
+
+
+def hamming(a: np.ndarray, b: np.ndarray) -> int:
+    lib = _load()
+    x = _c(a, np.uint32)
+    y = _c(b, np.uint32)
+    return int(lib.oracle_hamming(_p(x), _p(y), x.size))
+
+
+def encode_values(vals: np.ndarray):
+    """bf16 bits, e4m3 codes and the row scale of an integer-valued row,
+    with the same rules as the block-mean embedding (scale = max|v| / 448)."""
+    v = np.asarray(vals, dtype=np.float32)
+    bf = np.array([bf16_bits(float(x)) for x in v], dtype=np.uint16)
+    m = np.float32(np.max(np.abs(v))) if v.size else np.float32(0)
+    s = np.float32(1.0) if m == 0 else np.float32(m / np.float32(448.0))
+    q = np.array([e4m3_code(float(np.float32(x / s))) for x in v], dtype=np.uint8)
+    return bf, q, s
 
 
 def bf16_to_f64(bits: np.ndarray) -> np.ndarray:

@@ -45,6 +45,16 @@
  * decisions that produce those codes are taken in binary32, as the kernels
  * take them.
  *
+ * The random-projection prefilter uses a count sketch of each binary mask
+ * (a sparse random projection with one +-1 per voxel): voxel x goes to
+ * bucket h(x) mod D with sign s(x), where h is the SplitMix64 output
+ * function (Steele, Lea & Flood 2014) applied to (x + 1) * golden-ratio
+ * increment; the sketch's squared L2 between two masks is an unbiased
+ * estimate of the size of their symmetric difference.  The Hamming-code
+ * prefilter keeps the sign bit [v > 0] of every bucket (a sign random
+ * projection, the popcount analogue of the paper's hashing baseline) and
+ * compares codes by the number of differing bits.
+ *
  * The nearest-neighbour downsampling of Section 2.3 (an order-0 spline
  * resampling to 64^3 or 32^3) is out[i] = in[f*i] along each axis.
  *
@@ -382,6 +392,55 @@ int oracle_embed(const uint8_t* mask, int nx, int ny, int nz, int f,
     *out_scale = s;
     free(mean);
     return d;
+}
+
+/* SplitMix64 output for counter value i of a stream with key k: the
+   finaliser applied to k + (i + 1) * 0x9E3779B97F4A7C15. */
+uint64_t oracle_splitmix64(uint64_t key, uint64_t i)
+{
+    uint64_t z = key + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* Count sketch of one byte mask [v] into d buckets (d a power of two):
+   out[h mod d] += (bit 31 of h ? -1 : +1) for every set voxel x, with
+   h = oracle_splitmix64(0, x) >> 32 for the bucket and the whole h for the
+   sign.  Returns 0, or -1 if d is not a power of two. */
+int oracle_sketch(const uint8_t* mask, int64_t v, int d, int32_t* out)
+{
+    if (d <= 0 || (d & (d - 1))) return -1;
+    for (int j = 0; j < d; ++j) out[j] = 0;
+    for (int64_t x = 0; x < v; ++x) {
+        if (!mask[x]) continue;
+        const uint64_t h = oracle_splitmix64(0, (uint64_t)x);
+        const int bucket = (int)((h >> 32) & (uint64_t)(d - 1));
+        out[bucket] += ((h >> 31) & 1u) ? -1 : 1;
+    }
+    return 0;
+}
+
+/* Sign code of a sketch: bit j of word j/32 is [v_j > 0]. */
+void oracle_sign_code(const int32_t* sk, int d, uint32_t* code /* [d/32] */)
+{
+    for (int w = 0; w < d / 32; ++w) code[w] = 0;
+    for (int j = 0; j < d; ++j)
+        if (sk[j] > 0) code[j / 32] |= 1u << (j % 32);
+}
+
+/* Number of differing bits of two codes of `words` words. */
+int64_t oracle_hamming(const uint32_t* a, const uint32_t* b, int64_t words)
+{
+    int64_t h = 0;
+    for (int64_t w = 0; w < words; ++w) {
+        uint32_t x = a[w] ^ b[w];
+        while (x) {
+            h += x & 1u;
+            x >>= 1;
+        }
+    }
+    return h;
 }
 
 /* Euclidean distance between two vectors of length d, in binary64. */

@@ -30,6 +30,11 @@ MUTANTS = {
     "e4m3_scale_wrong_max": ("float s = (m == 0.0f) ? 1.0f : m / 448.0f;",
                              "float s = (m == 0.0f) ? 1.0f : m / 240.0f;"),
     "e4m3_subnormal_exponent": ("mag = ldexp((double)frac, -9);", "mag = ldexp((double)frac, -10);"),
+    "sketch_bucket_bits": ("const int bucket = (int)((h >> 32) & (uint64_t)(d - 1));",
+                           "const int bucket = (int)((h >> 33) & (uint64_t)(d - 1));"),
+    "sketch_sign_flipped": ("out[bucket] += ((h >> 31) & 1u) ? -1 : 1;",
+                            "out[bucket] += ((h >> 31) & 1u) ? 1 : -1;"),
+    "sign_code_ge_zero": ("if (sk[j] > 0) code[j / 32]", "if (sk[j] >= 0) code[j / 32]"),
     "patient_flair_at_t1": ("        mask[v + x] = (uint8_t)in_mask_f32(vol[x], t2);",
                             "        mask[v + x] = (uint8_t)in_mask_f32(vol[x], t1);"),
 }
@@ -48,6 +53,7 @@ def test_pins_catch_mutant(name, tmp_path):
     env = dict(os.environ, DBQ_ORACLE_LIB=str(lib))
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_embed_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_embed_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_sketch_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
