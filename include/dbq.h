@@ -78,6 +78,7 @@ enum dbq_storage {
 
 /* db_create flags. */
 #define DBQ_FLAG_EMBED 1u  /* also build the prefilter embeddings (see db_query_batch) */
+#define DBQ_FLAG_SKETCH 2u /* build count-sketch embeddings and sign codes instead  */
 
 /* Options of db_set_option. */
 enum dbq_option {
@@ -90,7 +91,8 @@ enum dbq_option {
 enum dbq_mode {
     DBQ_MODE_EXACT = 0,       /* the brute-force loop over every entry           */
     DBQ_MODE_EMBED_BF16 = 1,  /* bfloat16 embedding prefilter + exact re-ranking  */
-    DBQ_MODE_EMBED_FP8 = 2    /* FP8 E4M3 embedding prefilter + exact re-ranking  */
+    DBQ_MODE_EMBED_FP8 = 2,   /* FP8 E4M3 embedding prefilter + exact re-ranking  */
+    DBQ_MODE_HASH = 3         /* Hamming prefilter on sign codes + re-ranking     */
 };
 
 /* One ranked result.  p1/p2 are the patient's mask sizes. */
@@ -118,6 +120,16 @@ typedef struct dbq_hit {
  *                and ny, nz multiples of 8; db_build_masks() then also builds
  *                the prefilter embeddings (2 x (nx/8)(ny/8)(nz/8) values per
  *                entry, bfloat16 and FP8 E4M3 with per-row scales).
+ *                Or DBQ_FLAG_SKETCH: BITS storage, any grid; the embedding of
+ *                each mask is instead a count sketch, a random projection of
+ *                the mask onto D = 4096 values per segmentation: voxel x adds
+ *                s(x) = +-1 to bucket b(x), where h = SplitMix64 (Steele, Lea &
+ *                Flood 2014) of counter x, b(x) = (h >> 32) mod D and s(x) =
+ *                -1 iff bit 31 of h is set.  |sk(A) - sk(B)|^2 is an unbiased
+ *                estimate of |A xor B|.  The sketch is encoded like the block
+ *                means (bf16, FP8 with scale max|v|/448), and its sign code
+ *                (bit j = [v_j > 0], 32 buckets per word) is kept for
+ *                DBQ_MODE_HASH.  The two flags exclude each other.
  * Returns DBQ_OK and *out, or DBQ_EINVAL / DBQ_ENOMEM / DBQ_ECUDA.
  */
 int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storage,
@@ -229,6 +241,10 @@ int db_info(const dbq_db* db, int64_t out[8]);
  *                 keeps the `n_candidates` closest entries per query (ties to
  *                 the lower index), which are re-ranked by the exact Dice
  *                 loop; the hits are exact for the entries they name.
+ *                 DBQ_MODE_HASH: for databases built with DBQ_FLAG_SKETCH,
+ *                 the same with the Hamming distance between the sign codes
+ *                 (summed over both segmentations; the binary-code queries of
+ *                 Section 2.3) as the prefilter distance.
  *   n_candidates  1 <= k <= n_candidates <= min(N, 1024) (embedding modes).
  *   hits          host [nq][k]; params host [nq][k][n_params] or NULL.
  * Queries are processed in groups of up to 256 per database.  Returns after
@@ -273,7 +289,8 @@ int db_plan_destroy(dbq_plan* plan);
  * measurement and checking: distances dist [nq][N] (host or device, or
  * NULL) and the n_candidates closest entries per query, ascending, cand
  * [nq][n_candidates] int32 (host or device, or NULL).  nq <= 256; bit-packed
- * databases built with DBQ_FLAG_EMBED only.
+ * databases built with DBQ_FLAG_EMBED or DBQ_FLAG_SKETCH only.  In
+ * DBQ_MODE_HASH the distances are the Hamming distances (exact integers).
  */
 int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int mode,
                  int n_candidates, float* dist, int32_t* cand, void* stream);
@@ -301,7 +318,8 @@ int db_last_support(dbq_db* db, int64_t out[2]);
 /*
  * db_stage_times -- GPU milliseconds of the stages of the handle's last
  * embedding-mode db_query_batch group: ms[0] patient thresholding, ms[1]
- * query embeddings, ms[2] tensor-core distances, ms[3] candidate selection,
+ * query embeddings, ms[2] distances (tensor-core GEMM, or Hamming in
+ * DBQ_MODE_HASH), ms[3] candidate selection,
  * ms[4] exact re-ranking.  n <= 5 values are written; DBQ_ESTATE if no such
  * batch has run.
  */
@@ -315,6 +333,13 @@ int db_stage_times(dbq_db* db, float* ms, int n);
  */
 int db_get_embeddings(dbq_db* db, int64_t first, int64_t count, uint16_t* bf16, uint8_t* e4m3,
                       float* scale, float* norm_bf16, float* norm_fp8, void* stream);
+
+/*
+ * db_get_codes -- copy the sign codes of entries [first, first+count) to
+ * `codes` [count][2][128] uint32 (host or device).  Databases built with
+ * DBQ_FLAG_SKETCH only (DBQ_ESTATE otherwise).
+ */
+int db_get_codes(dbq_db* db, int64_t first, int64_t count, uint32_t* codes, void* stream);
 
 /*
  * db_create_downsampled -- a bit-packed database made from `src` by

@@ -10,8 +10,9 @@ from __future__ import annotations
 import numpy as np
 
 from . import _dbq
-from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_MODE_EMBED_BF16,
-                   DBQ_MODE_EMBED_FP8, DBQ_MODE_EXACT, DBQ_STORE_BITS, DBQ_STORE_F16, HIT_DTYPE,
+from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_FLAG_SKETCH,
+                   DBQ_MODE_EMBED_BF16, DBQ_MODE_EMBED_FP8, DBQ_MODE_EXACT, DBQ_MODE_HASH,
+                   SKETCH_DIMS, db_get_codes, DBQ_STORE_BITS, DBQ_STORE_F16, HIT_DTYPE,
                    DbqError, db_build_masks, db_create, db_destroy, db_get_embeddings,
                    db_get_masks, db_info, db_last_error, db_load_volumes, db_prefilter,
                    db_prepare_patient, db_query, db_query_async, db_query_batch,
@@ -20,8 +21,9 @@ from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_MODE_EMBED_BF
                    db_plan_set, db_plan_query, db_plan_destroy, db_create_downsampled)
 
 __all__ = ["Database", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_F16", "DBQ_BITS",
-           "DBQ_STORE_BITS", "DBQ_STORE_F16", "DBQ_FLAG_EMBED", "DBQ_MODE_EXACT",
-           "DBQ_MODE_EMBED_BF16", "DBQ_MODE_EMBED_FP8", "db_query_batch", "db_prefilter",
+           "DBQ_STORE_BITS", "DBQ_STORE_F16", "DBQ_FLAG_EMBED", "DBQ_FLAG_SKETCH",
+           "DBQ_MODE_EXACT", "DBQ_MODE_EMBED_BF16", "DBQ_MODE_EMBED_FP8", "DBQ_MODE_HASH",
+           "SKETCH_DIMS", "db_get_codes", "db_query_batch", "db_prefilter",
            "db_get_embeddings", "db_scan_packed_noalloc", "db_set_option", "db_stage_times",
            "DBQ_OPT_SPARSE", "DBQ_PLAN_ITEMS_PER_SM", "Plan", "db_plan_create",
            "db_plan_set", "db_plan_query", "db_plan_destroy", "db_create_downsampled", "db_create", "db_load_volumes",
@@ -34,7 +36,8 @@ class Database:
     """Owns one libdbq handle; methods map one-to-one onto the C calls."""
 
     def __init__(self, shape, capacity: int, storage: int = DBQ_STORE_BITS,
-                 t1: float = 0.6, t2: float = 0.25, n_params: int = 0, embed: bool = False):
+                 t1: float = 0.6, t2: float = 0.25, n_params: int = 0, embed: bool = False,
+                 sketch: bool = False):
         nx, ny, nz = shape
         self.shape = (int(nx), int(ny), int(nz))
         self.capacity = int(capacity)
@@ -42,8 +45,9 @@ class Database:
         self.t1, self.t2 = float(np.float32(t1)), float(np.float32(t2))
         self.n_params = int(n_params)
         self.embed = bool(embed)
-        self.handle = db_create(nx, ny, nz, capacity, storage, t1, t2, n_params,
-                                DBQ_FLAG_EMBED if embed else 0)
+        self.sketch = bool(sketch)
+        flags = (DBQ_FLAG_EMBED if embed else 0) | (DBQ_FLAG_SKETCH if sketch else 0)
+        self.handle = db_create(nx, ny, nz, capacity, storage, t1, t2, n_params, flags)
 
     def load(self, first: int, vols, params=None, stream=None):
         db_load_volumes(self.handle, first, int(vols.shape[0]), vols, params=params,
@@ -83,6 +87,7 @@ class Database:
         obj.t1, obj.t2 = self.t1, self.t2
         obj.n_params = self.n_params
         obj.embed = False
+        obj.sketch = False
         obj.handle = db_create_downsampled(self.handle, factor)
         return obj
 
@@ -94,12 +99,18 @@ class Database:
         """-> dict of bf16 bits [count,2,d] uint16, e4m3 codes [count,2,d] uint8,
         scale, norm_bf16, norm_fp8 [count,2] float32."""
         nx, ny, nz = self.shape
-        d = (nx // 8) * (ny // 8) * (nz // 8)
+        d = SKETCH_DIMS if self.sketch else (nx // 8) * (ny // 8) * (nz // 8)
         out = dict(bf16=np.zeros((count, 2, d), np.uint16), e4m3=np.zeros((count, 2, d), np.uint8),
                    scale=np.zeros((count, 2), np.float32),
                    norm_bf16=np.zeros((count, 2), np.float32),
                    norm_fp8=np.zeros((count, 2), np.float32))
         db_get_embeddings(self.handle, first, count, **out)
+        return out
+
+    def codes(self, first: int, count: int):
+        """Sign codes of a sketch database -> uint32 [count, 2, SKETCH_DIMS/32]."""
+        out = np.zeros((count, 2, SKETCH_DIMS // 32), np.uint32)
+        db_get_codes(self.handle, first, count, out)
         return out
 
     def prefilter(self, patients, mode: int, n_candidates: int = 0, kind=None):

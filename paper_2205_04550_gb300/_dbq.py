@@ -32,6 +32,8 @@ DBQ_STORE_BITS = 0
 DBQ_STORE_F16 = 1
 
 DBQ_FLAG_EMBED = 1
+DBQ_FLAG_SKETCH = 2
+SKETCH_DIMS = 4096
 
 DBQ_OPT_SPARSE = 1
 
@@ -40,6 +42,7 @@ DBQ_PLAN_ITEMS_PER_SM = 1
 DBQ_MODE_EXACT = 0
 DBQ_MODE_EMBED_BF16 = 1
 DBQ_MODE_EMBED_FP8 = 2
+DBQ_MODE_HASH = 3
 
 STATUS_NAMES = {0: "DBQ_OK", -1: "DBQ_EINVAL", -2: "DBQ_ENOMEM", -3: "DBQ_ESTATE",
                 -4: "DBQ_ECUDA", -5: "DBQ_ETIMEOUT", -6: "DBQ_ERANGE"}
@@ -91,6 +94,7 @@ _SIGS = [
                                     ctypes.c_int, _P, _P, _P]),
     ("db_get_embeddings", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P, _P, _P, _P,
                                          _P]),
+    ("db_get_codes", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int64, _P, _P]),
     ("db_stage_times", ctypes.c_int, [_P, _P, ctypes.c_int]),
     ("db_set_option", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     ("db_last_support", ctypes.c_int, [_P, _P]),
@@ -287,6 +291,10 @@ def db_get_embeddings(db: int, first: int, count: int, bf16=None, e4m3=None, sca
                                     _ptr(norm_bf16), _ptr(norm_fp8), _stream(stream)))
 
 
+def db_get_codes(db: int, first: int, count: int, codes, stream=None):
+    _check(load().db_get_codes(db, first, count, _ptr(codes), _stream(stream)))
+
+
 def db_set_option(db: int, option: int, value: int):
     _check(load().db_set_option(db, option, value))
 
@@ -339,7 +347,7 @@ def db_stage_times(db: int) -> dict:
     """GPU ms per stage of the handle's last embedding-mode batch."""
     ms = np.zeros(5, dtype=np.float32)
     _check(load().db_stage_times(db, ms.ctypes.data, 5))
-    keys = ("patients", "query_embed", "gemm", "select", "rerank")
+    keys = ("patients", "query_embed", "distances", "select", "rerank")
     return dict(zip(keys, (float(x) for x in ms)))
 
 

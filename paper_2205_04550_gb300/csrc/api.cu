@@ -119,6 +119,8 @@ struct dbq_db {
     float* emb_scale = nullptr;     // [n][2]
     float* emb_nb = nullptr;        // [n][2] squared norms, bf16 rows
     float* emb_nf = nullptr;        // [n][2] squared norms, fp8 rows
+    bool sketch = false;            // DBQ_FLAG_SKETCH: count sketches instead of block means
+    uint32_t* codes = nullptr;      // [n][2][dims/32] sign codes (DBQ_FLAG_SKETCH)
     // batch workspace (allocated on first use)
     int bq = 0;                     // capacity in queries
     int bk = 0;                     // capacity in hits per query
@@ -132,6 +134,7 @@ struct dbq_db {
     float* bq_scale = nullptr;
     float* bq_nb = nullptr;
     float* bq_nf = nullptr;
+    uint32_t* bq_codes = nullptr;   // [bq][2][dims/32]
     float* bdist = nullptr;         // [bq][n]
     int32_t* bcand = nullptr;       // [bq][1024]
     dbq::Cand* brr = nullptr;       // [bq][slices][bk]
@@ -177,6 +180,8 @@ struct dbq_db {
         cudaFree(emb_scale);
         cudaFree(emb_nb);
         cudaFree(emb_nf);
+        cudaFree(codes);
+        cudaFree(bq_codes);
         cudaFree(bstage);
         cudaFree(bptrs);
         cudaFree(bplanes);
@@ -397,6 +402,8 @@ int ensure_batch(dbq_db* db, int k)
             if (!rc) rc = grow(db, &db->bq_scale, rows * 4, "query scales");
             if (!rc) rc = grow(db, &db->bq_nb, rows * 4, "query bf16 norms");
             if (!rc) rc = grow(db, &db->bq_nf, rows * 4, "query fp8 norms");
+            if (!rc && db->sketch)
+                rc = grow(db, &db->bq_codes, rows * (db->dims / 32) * 4, "query sign codes");
             if (!rc) rc = grow(db, &db->bdist, q * (size_t)db->n * 4, "prefilter distances");
             if (!rc) rc = grow(db, &db->bcand, q * 1024 * 4, "prefilter candidates");
             if (!rc) rc = grow(db, &db->brr, q * kRerankSlices * kMaxK * sizeof(dbq::Cand),
@@ -490,30 +497,39 @@ void mark(dbq_db* db, int i, cudaStream_t s)
     if (db->ev[i]) cudaEventRecord(db->ev[i], s);
 }
 
-int run_prefilter(dbq_db* db, int nq, int fp8, int c, cudaStream_t s)
+int run_prefilter(dbq_db* db, int nq, int mode, int c, cudaStream_t s)
 {
     mark(db, 1, s);
-    cudaError_t err = dbq::launch_embed(db->bplanes, nq, db->wp, db->nx, db->ny, db->nz,
-                                        db->bq_bf16, db->bq_f8, db->bq_scale, db->bq_nb,
-                                        db->bq_nf, s);
+    cudaError_t err =
+        db->sketch
+            ? dbq::launch_sketch(db->bplanes, nq, db->wp, db->words, db->bq_bf16, db->bq_f8,
+                                 db->bq_scale, db->bq_nb, db->bq_nf, db->bq_codes, s)
+            : dbq::launch_embed(db->bplanes, nq, db->wp, db->nx, db->ny, db->nz, db->bq_bf16,
+                                db->bq_f8, db->bq_scale, db->bq_nb, db->bq_nf, s);
     if (err != cudaSuccess) return cuda_fail(err, "query embedding launch");
     mark(db, 2, s);
-    dbq::GemmArgs g;
-    g.e_bf16 = db->emb_bf16;
-    g.e_f8 = db->emb_f8;
-    g.enorm = fp8 ? db->emb_nf : db->emb_nb;
-    g.escale = db->emb_scale;
-    g.q_bf16 = db->bq_bf16;
-    g.q_f8 = db->bq_f8;
-    g.qnorm = fp8 ? db->bq_nf : db->bq_nb;
-    g.qscale = db->bq_scale;
-    g.n = db->n;
-    g.nq = nq;
-    g.dims = db->dims;
-    g.dist = db->bdist;
-    g.status = db->bstatus;
-    err = dbq::launch_prefilter_gemm(g, fp8, db->grid, s);
-    if (err != cudaSuccess) return cuda_fail(err, "prefilter GEMM launch");
+    if (mode == DBQ_MODE_HASH) {
+        err = dbq::launch_hamming(db->codes, db->n, db->bq_codes, nq, db->bdist, s);
+        if (err != cudaSuccess) return cuda_fail(err, "Hamming distance launch");
+    } else {
+        const int fp8 = mode == DBQ_MODE_EMBED_FP8;
+        dbq::GemmArgs g;
+        g.e_bf16 = db->emb_bf16;
+        g.e_f8 = db->emb_f8;
+        g.enorm = fp8 ? db->emb_nf : db->emb_nb;
+        g.escale = db->emb_scale;
+        g.q_bf16 = db->bq_bf16;
+        g.q_f8 = db->bq_f8;
+        g.qnorm = fp8 ? db->bq_nf : db->bq_nb;
+        g.qscale = db->bq_scale;
+        g.n = db->n;
+        g.nq = nq;
+        g.dims = db->dims;
+        g.dist = db->bdist;
+        g.status = db->bstatus;
+        err = dbq::launch_prefilter_gemm(g, fp8, db->grid, s);
+        if (err != cudaSuccess) return cuda_fail(err, "prefilter GEMM launch");
+    }
     mark(db, 3, s);
     if (c > 0) {
         err = dbq::launch_select_smallest(db->bdist, nq, db->n, c, db->bcand, s);
@@ -539,9 +555,12 @@ int check_status(dbq_db* db, cudaStream_t s)
 int check_prefilter_args(dbq_db* db, int mode, int c, int k)
 {
     if (!db->built) return fail(DBQ_ESTATE, "database not built (call db_build_masks)");
-    if (!db->dims) return fail(DBQ_ESTATE, "database has no embeddings (DBQ_FLAG_EMBED)");
-    if (mode != DBQ_MODE_EMBED_BF16 && mode != DBQ_MODE_EMBED_FP8)
+    if (!db->dims)
+        return fail(DBQ_ESTATE, "database has no embeddings (DBQ_FLAG_EMBED or DBQ_FLAG_SKETCH)");
+    if (mode != DBQ_MODE_EMBED_BF16 && mode != DBQ_MODE_EMBED_FP8 && mode != DBQ_MODE_HASH)
         return fail(DBQ_EINVAL, "unknown prefilter mode %d", mode);
+    if (mode == DBQ_MODE_HASH && !db->sketch)
+        return fail(DBQ_ESTATE, "hash codes need a database built with DBQ_FLAG_SKETCH");
     if (mode == DBQ_MODE_EMBED_FP8 && db->dims % 128)
         return fail(DBQ_EINVAL, "FP8 prefilter needs a multiple of 128 embedding dims");
     if (mode == DBQ_MODE_EMBED_BF16 && db->dims % 64)
@@ -614,7 +633,12 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
     if (storage == DBQ_STORE_BITS && (!threshold_ok(t1) || !threshold_ok(t2)))
         return fail(DBQ_EINVAL, "build thresholds must be finite and in (0, 1]");
     if (n_params < 0 || n_params > 64) return fail(DBQ_EINVAL, "n_params must be in [0, 64]");
-    if (flags & ~DBQ_FLAG_EMBED) return fail(DBQ_EINVAL, "unknown flags 0x%x", flags);
+    if (flags & ~(DBQ_FLAG_EMBED | DBQ_FLAG_SKETCH))
+        return fail(DBQ_EINVAL, "unknown flags 0x%x", flags);
+    if ((flags & DBQ_FLAG_EMBED) && (flags & DBQ_FLAG_SKETCH))
+        return fail(DBQ_EINVAL, "DBQ_FLAG_EMBED and DBQ_FLAG_SKETCH exclude each other");
+    if ((flags & DBQ_FLAG_SKETCH) && storage != DBQ_STORE_BITS)
+        return fail(DBQ_EINVAL, "sketch embeddings need bit-packed storage");
     if ((flags & DBQ_FLAG_EMBED) &&
         (storage != DBQ_STORE_BITS || !dbq::embed_supported(nx, ny, nz)))
         return fail(DBQ_EINVAL,
@@ -663,14 +687,17 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
         rc = dev_alloc(db, &db->vols16, (size_t)capacity * db->vp * sizeof(uint16_t),
                        "binary16 volumes");
     }
-    if (!rc && (flags & DBQ_FLAG_EMBED)) {
-        db->dims = dbq::embed_dims(nx, ny, nz);
+    if (!rc && (flags & (DBQ_FLAG_EMBED | DBQ_FLAG_SKETCH))) {
+        db->sketch = (flags & DBQ_FLAG_SKETCH) != 0;
+        db->dims = db->sketch ? dbq::sketch_dims() : dbq::embed_dims(nx, ny, nz);
         const size_t rows = (size_t)capacity * 2;
         rc = dev_alloc(db, &db->emb_bf16, rows * db->dims * 2, "bf16 embeddings");
         if (!rc) rc = dev_alloc(db, &db->emb_f8, rows * db->dims, "fp8 embeddings");
         if (!rc) rc = dev_alloc(db, &db->emb_scale, rows * 4, "fp8 scales");
         if (!rc) rc = dev_alloc(db, &db->emb_nb, rows * 4, "bf16 norms");
         if (!rc) rc = dev_alloc(db, &db->emb_nf, rows * 4, "fp8 norms");
+        if (!rc && db->sketch)
+            rc = dev_alloc(db, &db->codes, rows * (db->dims / 32) * 4, "sign codes");
     }
     db->grid = dbq::scan_packed_grid(dev);
     dbq::scan_packed_chunking(db->wp4, &db->chunk4, &db->nchunks);
@@ -797,6 +824,11 @@ int db_build_masks(dbq_db* db, void* stream)
                                             db->emb_bf16, db->emb_f8, db->emb_scale, db->emb_nb,
                                             db->emb_nf, s);
         if (err != cudaSuccess) return cuda_fail(err, "embedding launch");
+    } else if (db->flags & DBQ_FLAG_SKETCH) {
+        cudaError_t err = dbq::launch_sketch(db->planes, db->n, db->wp, db->words, db->emb_bf16,
+                                             db->emb_f8, db->emb_scale, db->emb_nb, db->emb_nf,
+                                             db->codes, s);
+        if (err != cudaSuccess) return cuda_fail(err, "sketch launch");
     }
     DBQ_CUDA(cudaStreamSynchronize(s));
     db->built = true;
@@ -947,7 +979,8 @@ int db_get_embeddings(dbq_db* db, int64_t first, int64_t count, uint16_t* bf16, 
 {
     if (!db) return fail(DBQ_EINVAL, "db is NULL");
     std::lock_guard<std::mutex> lock(db->mu);
-    if (!db->dims) return fail(DBQ_ESTATE, "database has no embeddings (DBQ_FLAG_EMBED)");
+    if (!db->dims)
+        return fail(DBQ_ESTATE, "database has no embeddings (DBQ_FLAG_EMBED or DBQ_FLAG_SKETCH)");
     if (!db->built) return fail(DBQ_ESTATE, "database not built (call db_build_masks)");
     if (first < 0 || count < 0 || first + count > db->n)
         return fail(DBQ_ERANGE, "entries outside [0, N)");
@@ -968,6 +1001,26 @@ int db_get_embeddings(dbq_db* db, int64_t first, int64_t count, uint16_t* bf16, 
         DBQ_CUDA(cudaMemcpyAsync(norm_bf16, db->emb_nb + r0, rows * 4, cudaMemcpyDefault, s));
     if (norm_fp8)
         DBQ_CUDA(cudaMemcpyAsync(norm_fp8, db->emb_nf + r0, rows * 4, cudaMemcpyDefault, s));
+    DBQ_CUDA(cudaStreamSynchronize(s));
+    return DBQ_OK;
+}
+
+int db_get_codes(dbq_db* db, int64_t first, int64_t count, uint32_t* codes, void* stream)
+{
+    if (!db) return fail(DBQ_EINVAL, "db is NULL");
+    std::lock_guard<std::mutex> lock(db->mu);
+    if (!db->sketch) return fail(DBQ_ESTATE, "database has no sign codes (DBQ_FLAG_SKETCH)");
+    if (!db->built) return fail(DBQ_ESTATE, "database not built (call db_build_masks)");
+    if (first < 0 || count < 0 || first + count > db->n)
+        return fail(DBQ_ERANGE, "entries outside [0, N)");
+    if (count == 0) return DBQ_OK;
+    if (!codes) return fail(DBQ_EINVAL, "codes is NULL");
+    DeviceGuard guard(db->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const size_t row_words = (size_t)db->dims / 32;
+    DBQ_CUDA(cudaMemcpyAsync(codes, db->codes + (size_t)first * 2 * row_words,
+                             (size_t)count * 2 * row_words * 4, cudaMemcpyDefault, s));
     DBQ_CUDA(cudaStreamSynchronize(s));
     return DBQ_OK;
 }
@@ -1033,7 +1086,7 @@ int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int 
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     rc = ensure_batch(db, 1);
     if (!rc) rc = prepare_batch(db, nq, patients, kind, db->t1, db->t2, s);
-    if (!rc) rc = run_prefilter(db, nq, mode == DBQ_MODE_EMBED_FP8, cand ? n_candidates : 0, s);
+    if (!rc) rc = run_prefilter(db, nq, mode, cand ? n_candidates : 0, s);
     if (rc) return rc;
     if (dist)
         DBQ_CUDA(cudaMemcpyAsync(dist, db->bdist, (size_t)nq * db->n * 4, cudaMemcpyDefault, s));
@@ -1050,7 +1103,8 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
 {
     if (!dbs || !db_of_query || !patients || !hits) return fail(DBQ_EINVAL, "NULL argument");
     if (nq < 0) return fail(DBQ_EINVAL, "nq < 0");
-    if (mode != DBQ_MODE_EXACT && mode != DBQ_MODE_EMBED_BF16 && mode != DBQ_MODE_EMBED_FP8)
+    if (mode != DBQ_MODE_EXACT && mode != DBQ_MODE_EMBED_BF16 && mode != DBQ_MODE_EMBED_FP8 &&
+        mode != DBQ_MODE_HASH)
         return fail(DBQ_EINVAL, "unknown mode %d", mode);
     if (kind != DBQ_F32 && kind != DBQ_F16 && kind != DBQ_BITS)
         return fail(DBQ_EINVAL, "unknown patient kind %d", kind);
@@ -1103,7 +1157,7 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
                 }
                 mark(db, 0, s);
                 rc = prepare_batch(db, gn, pp.data(), kind, db->t1, db->t2, s);
-                if (!rc) rc = run_prefilter(db, gn, mode == DBQ_MODE_EMBED_FP8, n_candidates, s);
+                if (!rc) rc = run_prefilter(db, gn, mode, n_candidates, s);
                 if (rc) return rc;
                 dbq::RerankArgs r;
                 r.planes = reinterpret_cast<const uint4*>(db->planes);

@@ -104,6 +104,19 @@ cudaError_t launch_embed(const uint32_t* planes, int64_t count, int64_t wp, int 
                          int nz, uint16_t* out_bf16, uint8_t* out_f8, float* out_scale,
                          float* out_norm_bf16, float* out_norm_f8, cudaStream_t stream);
 
+// Count-sketch embeddings (sketch.cu): D = sketch_dims() buckets per
+// segmentation, the same encodings as launch_embed, plus the sign code
+// [count][2][D/32] (bit j of a row = bucket j > 0).  Any grid; `words`
+// meaningful words of each wp-word plane.
+int sketch_dims();
+cudaError_t launch_sketch(const uint32_t* planes, int64_t count, int64_t wp, int64_t words,
+                          uint16_t* out_bf16, uint8_t* out_f8, float* out_scale, float* out_nb,
+                          float* out_nf, uint32_t* out_code, cudaStream_t stream);
+// Hamming distances of sign codes (2 * D/32 words per entry and per query):
+// dist [nq][n] binary32 (exact integers).
+cudaError_t launch_hamming(const uint32_t* codes, int64_t n, const uint32_t* qcodes, int nq,
+                           float* dist, cudaStream_t stream);
+
 struct GemmArgs {
     const uint16_t* e_bf16;   // [n][2*dims] entry embeddings (bf16 bits)
     const uint8_t* e_f8;      // [n][2*dims] entry embeddings (e4m3 codes)

@@ -12,8 +12,9 @@ Two query paths, matching the library's modes:
 
 * ``exact``: one persistent launch (``db_plan_query``) per batch over all of
   its queries, whatever database each query names;
-* ``embed_bf16`` / ``embed_fp8``: per database in the batch, the tensor-core
-  embedding prefilter plus exact re-ranking (``db_query_batch``); a database
+* ``embed_bf16`` / ``embed_fp8`` / ``hash``: per database in the batch, the
+  tensor-core embedding prefilter (or the Hamming prefilter on sign codes of
+  a sketch database) plus exact re-ranking (``db_query_batch``); a database
   handle serialises its own batches (its prefilter workspace is shared), so
   embedding batches overlap across databases.
 
@@ -32,10 +33,11 @@ from concurrent.futures import Future
 import numpy as np
 
 from . import _dbq
-from ._dbq import DBQ_MODE_EMBED_BF16, DBQ_MODE_EMBED_FP8, DBQ_MODE_EXACT, HIT_DTYPE
+from ._dbq import (DBQ_MODE_EMBED_BF16, DBQ_MODE_EMBED_FP8, DBQ_MODE_EXACT, DBQ_MODE_HASH,
+                   HIT_DTYPE)
 
 MODES = {"exact": DBQ_MODE_EXACT, "embed_bf16": DBQ_MODE_EMBED_BF16,
-         "embed_fp8": DBQ_MODE_EMBED_FP8}
+         "embed_fp8": DBQ_MODE_EMBED_FP8, "hash": DBQ_MODE_HASH}
 
 
 class AdmissionError(RuntimeError):
@@ -79,7 +81,7 @@ class Server:
 
     databases   list of ``Database`` (bit-packed; built with ``embed=True`` for
                 the embedding modes), resident for the server's lifetime.
-    mode        "exact", "embed_bf16" or "embed_fp8".
+    mode        "exact", "embed_bf16", "embed_fp8" or "hash".
     budget      device bytes the server may hold for requests in flight
                 (patient slots and hit buffers); None = 90 % of the free
                 memory at start.
