@@ -14,8 +14,9 @@ library and never imports it.
 
 Pinned functions (the pins live in ``tests/test_oracle_*.py``):
 counts, Dice, score, ranking, thresholding (f32 and f16), the binary16
-decoder, bit-plane unpacking, block means, L2 distance and nearest-neighbour
-downsampling.
+decoder, bit-plane unpacking, block means, L2 distance, nearest-neighbour
+downsampling, count sketches and sign codes, and the reaction-diffusion
+forward model of Section 2.1.
 """
 from __future__ import annotations
 
@@ -103,6 +104,10 @@ def _load():
         lib.oracle_sign_code.argtypes = [P, i32, P]
         lib.oracle_hamming.argtypes = [P, P, i64]
         lib.oracle_hamming.restype = i64
+        lib.oracle_rd_steps.argtypes = [f64, f64, f64, f64, f64]
+        lib.oracle_rd_steps.restype = i64
+        lib.oracle_rd_simulate.argtypes = [P, i32, i32, i32, P, f64, f64, P]
+        lib.oracle_rd_simulate.restype = i64
         _lib = lib
         return lib
 
@@ -352,3 +357,24 @@ def downsample_nn(mask: np.ndarray, nx: int, ny: int, nz: int, f: int) -> np.nda
     if lib.oracle_downsample_nn_u8(_p(m), nx, ny, nz, f, _p(out)) != 0:
         raise ValueError("grid not divisible by factor")
     return out
+
+
+# ---------------------------------------------------------------- forward model
+def rd_steps(t_end: float, d_w: float, rho: float, m_max: float, cfl: float) -> int:
+    """Explicit-Euler step count n = ceil(T_end (6 D_w max(m) + rho) / cfl)."""
+    return int(_load().oracle_rd_steps(t_end, d_w, rho, m_max, cfl))
+
+
+def rd_simulate(tissue: np.ndarray, theta, u0: float = 1.0, cfl: float = 0.9):
+    """u(T_end) [nz, ny, nx] binary64 of Eq. 1-2 for one theta =
+    (x, y, z, D_w, rho, T_end) on the tissue map m [nz, ny, nx] (float32,
+    Omega = {m > 0}); returns (u, steps).  See oracle.c for the scheme."""
+    lib = _load()
+    m = _c(tissue, np.float32)
+    nz, ny, nx = m.shape
+    th = _c(theta, np.float64).reshape(6)
+    out = np.empty((nz, ny, nx), dtype=np.float64)
+    n = lib.oracle_rd_simulate(_p(m), nx, ny, nz, _p(th), u0, cfl, _p(out))
+    if n < 0:
+        raise ValueError("seed outside the grid or the domain, or invalid parameters")
+    return out, int(n)

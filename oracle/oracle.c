@@ -55,6 +55,10 @@
  * projection, the popcount analogue of the paper's hashing baseline) and
  * compares codes by the number of differing bits.
  *
+ * The forward model of Section 2.1 (Eq. 1-2, reaction-diffusion with no-flux
+ * boundary) is an explicit finite-difference scheme; its reading is stated
+ * with its code at the end of this file.
+ *
  * The nearest-neighbour downsampling of Section 2.3 (an order-0 spline
  * resampling to 64^3 or 32^3) is out[i] = in[f*i] along each axis.
  *
@@ -475,4 +479,92 @@ int oracle_num_threads(void)
 #else
     return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------------
+ * Forward model of Section 2.1 (Eq. 1-2): the reaction-diffusion equation
+ *   du/dt = div(D grad u) + rho u (1 - u)   in the brain Omega,
+ *   n . grad u = 0                           on its boundary,
+ *   u(r, 0) = u0 at the seed voxel r*, 0 elsewhere.
+ *
+ * The paper names no discretisation; the reading taken here:
+ *   * a voxel grid of unit spacing; D(x) = D_w m(x) with m the tissue's
+ *     relative diffusivity (the caller's map; Omega = {m > 0});
+ *   * the flux through the face between neighbours i and j is
+ *     D_w h(m_i, m_j) (u_j - u_i), h the harmonic mean 2 m_i m_j / (m_i + m_j);
+ *     h = 0 when either voxel is outside Omega, which is the no-flux
+ *     condition of Eq. 2 on the domain's boundary; faces on the edge of the
+ *     grid carry no flux either;
+ *   * explicit Euler in time, every voxel from the previous step's values:
+ *     u_i <- u_i + dt (D_w sum_j h(m_i, m_j) (u_j - u_i) + rho u_i (1 - u_i)),
+ *     the six neighbours taken in the order -x, +x, -y, +y, -z, +z;
+ *   * n = ceil(T_end (6 D_w max(m) + rho) / cfl) steps of dt = T_end / n
+ *     (n = 0 for T_end = 0; 0 < cfl <= 1 keeps 0 <= u <= 1);
+ *   * the seed voxel is the nearest voxel to (x, y, z): floor(c + 0.5).
+ * Everything is binary64.
+ * ------------------------------------------------------------------------ */
+static double rd_face(double a, double b)
+{
+    return (a + b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;
+}
+
+int64_t oracle_rd_steps(double t_end, double dw, double rho, double m_max, double cfl)
+{
+    if (!(t_end > 0.0)) return 0;
+    double rate = 6.0 * dw * m_max + rho;
+    double n = ceil(t_end * rate / cfl);
+    return n < 1.0 ? 1 : (int64_t)n;
+}
+
+/* theta = (x, y, z, D_w, rho, T_end).  out [nz][ny][nx] binary64 = u(T_end).
+   Returns the number of steps, or -1 for a seed outside the grid or the
+   domain, or an invalid parameter. */
+int64_t oracle_rd_simulate(const float* tissue, int nx, int ny, int nz, const double* theta,
+                           double u0, double cfl, double* out)
+{
+    const int64_t v = (int64_t)nx * ny * nz;
+    const double dw = theta[3], rho = theta[4], t_end = theta[5];
+    if (!(cfl > 0.0 && cfl <= 1.0) || !(dw >= 0.0) || !(rho >= 0.0) || !(t_end >= 0.0))
+        return -1;
+    const double fx = floor(theta[0] + 0.5), fy = floor(theta[1] + 0.5), fz = floor(theta[2] + 0.5);
+    if (fx < 0 || fy < 0 || fz < 0 || fx >= nx || fy >= ny || fz >= nz) return -1;
+    const int64_t seed = (int64_t)fx + (int64_t)nx * ((int64_t)fy + (int64_t)ny * (int64_t)fz);
+    if (!(tissue[seed] > 0.0f)) return -1;
+    double m_max = 0.0;
+    for (int64_t i = 0; i < v; ++i)
+        if ((double)tissue[i] > m_max) m_max = (double)tissue[i];
+    const int64_t n = oracle_rd_steps(t_end, dw, rho, m_max, cfl);
+    const double dt = n ? t_end / (double)n : 0.0;
+    double* u = (double*)calloc((size_t)v, sizeof(double));
+    double* w = (double*)calloc((size_t)v, sizeof(double));
+    if (!u || !w) {
+        free(u);
+        free(w);
+        return -1;
+    }
+    u[seed] = u0;
+    const int64_t sy = nx, sz = (int64_t)nx * ny;
+    for (int64_t step = 0; step < n; ++step) {
+        for (int z = 0; z < nz; ++z)
+            for (int y = 0; y < ny; ++y)
+                for (int x = 0; x < nx; ++x) {
+                    const int64_t i = x + sy * y + sz * z;
+                    const double ui = u[i], mi = tissue[i];
+                    double flux = 0.0;
+                    if (x > 0) flux += rd_face(mi, tissue[i - 1]) * (u[i - 1] - ui);
+                    if (x < nx - 1) flux += rd_face(mi, tissue[i + 1]) * (u[i + 1] - ui);
+                    if (y > 0) flux += rd_face(mi, tissue[i - sy]) * (u[i - sy] - ui);
+                    if (y < ny - 1) flux += rd_face(mi, tissue[i + sy]) * (u[i + sy] - ui);
+                    if (z > 0) flux += rd_face(mi, tissue[i - sz]) * (u[i - sz] - ui);
+                    if (z < nz - 1) flux += rd_face(mi, tissue[i + sz]) * (u[i + sz] - ui);
+                    w[i] = ui + dt * (dw * flux + rho * ui * (1.0 - ui));
+                }
+        double* t = u;
+        u = w;
+        w = t;
+    }
+    memcpy(out, u, (size_t)v * sizeof(double));
+    free(u);
+    free(w);
+    return n;
 }

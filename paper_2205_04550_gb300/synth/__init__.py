@@ -220,6 +220,80 @@ def patients_np(shape, qs, seed: int = DB_SEED, dtype=np.float32):
     return generate_np(shape, seed, qs + _U64(PATIENT_BASE), dtype)
 
 
+# ------------------------------------------------- reaction-diffusion inputs
+# Inputs of the forward model of Section 2.1 (Eq. 1-2).  The paper simulates
+# in the SRI24 atlas (white matter, grey matter, CSF); without it, a
+# synthetic atlas stands in: the brain ellipsoid above, white matter inside
+# the same ellipsoid scaled by 0.72, grey matter in the rest of the brain,
+# and one CSF-filled ventricle ellipsoid at the centre with semi-axes
+# (0.08 nx, 0.16 ny, 0.07 nz).  The tissue map holds the relative
+# diffusivity m(x): 1 in white matter, 0.1 in grey matter, 0 in CSF and
+# outside the brain (the simulation domain is {m > 0}).
+TISSUE_WM, TISSUE_GM = 1.0, 0.1
+RD_PARAM_NAMES = ("x", "y", "z", "D_w", "rho", "T_end")
+N_RD_PARAMS = 6
+
+
+def brain_tissue(shape) -> np.ndarray:
+    """Relative diffusivity m [nz, ny, nx] float32 of the synthetic atlas."""
+    nx, ny, nz = shape
+    (bx, by, bz), (sx, sy, sz) = brain_axes(shape)
+    x = np.arange(nx, dtype=np.float64)[None, None, :]
+    y = np.arange(ny, dtype=np.float64)[None, :, None]
+    z = np.arange(nz, dtype=np.float64)[:, None, None]
+
+    def inside(ax, ay, az):
+        return ((x - bx) / ax) ** 2 + ((y - by) / ay) ** 2 + ((z - bz) / az) ** 2 <= 1.0
+
+    m = np.zeros((nz, ny, nx), dtype=np.float32)
+    m[inside(sx, sy, sz)] = np.float32(TISSUE_GM)
+    m[inside(0.72 * sx, 0.72 * sy, 0.72 * sz)] = np.float32(TISSUE_WM)
+    m[inside(0.08 * nx, 0.16 * ny, 0.07 * nz)] = 0.0
+    return m
+
+
+def rd_params(shape, seed: int, entries) -> np.ndarray:
+    """theta = (x, y, z, D_w, rho, T_end) [len(entries), 6] float64 per entry
+    id, in voxel and day units.  The seed point is uniform in the brain
+    ellipsoid scaled by 0.6 and must round to a voxel of the domain
+    (rejection over draw slots 300..491, three per attempt; fallback: the
+    white-matter point 0.4 semi-axes right of the centre).  D_w ~ U(0.05, 0.5)
+    voxel^2/day (draw 500), rho ~ U(0.025, 0.25) /day (draw 501); the paper
+    discards simulations of unrealistic size, so instead of drawing T_end
+    freely the visible radius R ~ U(6, 30) voxels is drawn (draw 502) and
+    T_end = R / (2 sqrt(D_w rho)), the time a Fisher-KPP front of speed
+    2 sqrt(D_w rho) needs to travel R."""
+    keys = stream_keys(seed, entries)
+    n = keys.shape[0]
+    tissue = brain_tissue(shape)
+    (bx, by, bz), (sx, sy, sz) = brain_axes(shape)
+    nx, ny, nz = shape
+    pos = np.empty((n, 3))
+    pos[:] = (bx + 0.4 * sx, by, bz)
+    done = np.zeros(n, dtype=bool)
+    for attempt in range(64):
+        p = np.stack([2.0 * _uniform(keys, 300 + 3 * attempt + j) - 1.0 for j in range(3)],
+                     axis=1)
+        c = np.stack([bx + 0.6 * sx * p[:, 0], by + 0.6 * sy * p[:, 1], bz + 0.6 * sz * p[:, 2]],
+                     axis=1)
+        v = np.floor(c + 0.5).astype(np.int64)
+        v[:, 0] = np.clip(v[:, 0], 0, nx - 1)
+        v[:, 1] = np.clip(v[:, 1], 0, ny - 1)
+        v[:, 2] = np.clip(v[:, 2], 0, nz - 1)
+        ok = (~done) & ((p * p).sum(axis=1) <= 1.0) & (tissue[v[:, 2], v[:, 1], v[:, 0]] > 0)
+        pos[ok] = c[ok]
+        done |= ok
+        if done.all():
+            break
+    theta = np.empty((n, N_RD_PARAMS), dtype=np.float64)
+    theta[:, 0:3] = pos
+    theta[:, 3] = 0.05 + 0.45 * _uniform(keys, 500)
+    theta[:, 4] = 0.025 + 0.225 * _uniform(keys, 501)
+    radius = 6.0 + 24.0 * _uniform(keys, 502)
+    theta[:, 5] = radius / (2.0 * np.sqrt(theta[:, 3] * theta[:, 4]))
+    return theta
+
+
 # ---------------------------------------------------------------- CUDA generator
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "synth.cu")

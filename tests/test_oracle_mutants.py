@@ -35,6 +35,14 @@ MUTANTS = {
     "sketch_sign_flipped": ("out[bucket] += ((h >> 31) & 1u) ? -1 : 1;",
                             "out[bucket] += ((h >> 31) & 1u) ? 1 : -1;"),
     "sign_code_ge_zero": ("if (sk[j] > 0) code[j / 32]", "if (sk[j] >= 0) code[j / 32]"),
+    "rd_face_arithmetic_mean": ("return (a + b > 0.0) ? 2.0 * a * b / (a + b) : 0.0;",
+                                "return 0.5 * (a + b);"),
+    "rd_reaction_sign": ("rho * ui * (1.0 - ui)", "rho * ui * (1.0 + ui)"),
+    "rd_drops_plus_z_flux": ("                    if (z < nz - 1) flux += rd_face(mi, tissue[i + sz]) * (u[i + sz] - ui);\n", ""),
+    "rd_dt_off_by_one": ("t_end / (double)n : 0.0;", "t_end / (double)(n + 1) : 0.0;"),
+    "rd_y_stride_is_ny": ("const int64_t sy = nx, sz = (int64_t)nx * ny;",
+                          "const int64_t sy = ny, sz = (int64_t)nx * ny;"),
+    "rd_steps_ignore_m_max": ("double rate = 6.0 * dw * m_max + rho;", "double rate = 6.0 * dw + rho;"),
     "patient_flair_at_t1": ("        mask[v + x] = (uint8_t)in_mask_f32(vol[x], t2);",
                             "        mask[v + x] = (uint8_t)in_mask_f32(vol[x], t1);"),
 }
@@ -54,6 +62,7 @@ def test_pins_catch_mutant(name, tmp_path):
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                         os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                         os.path.join(ROOT, "tests", "test_oracle_embed_pins.py"),
-                        os.path.join(ROOT, "tests", "test_oracle_sketch_pins.py")],
+                        os.path.join(ROOT, "tests", "test_oracle_sketch_pins.py"),
+                        os.path.join(ROOT, "tests", "test_oracle_rd_pins.py")],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
     assert r.returncode != 0, f"mutant {name} survived the pins:\n{r.stdout[-2000:]}"
