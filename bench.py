@@ -63,6 +63,11 @@ WORKLOADS = {
                                  desc="100,000 x 128^3 bit-packed + bf16 count sketches "
                                       "(2x4096); L2 prefilter 512, exact re-rank, 256 queries, "
                                       "top-15"),
+    "pde_db_128": dict(shape=(128, 128, 128), sims=64, batch=16, u0=1.0, cfl=0.9, t1=0.6, t2=0.25,
+                       desc="forward model (Eq. 1-2) on the 128^3 synthetic atlas: 64 seeded "
+                            "parameter sets per step (D_w~U(0.05,0.5), rho~U(0.025,0.25), "
+                            "T_end for a 6-30 voxel front), 16 advanced together, u(T_end) "
+                            "thresholded and bit-packed into a database"),
     "plan_mix": dict(mix=[dict(shape=(64, 64, 64), n=100_000), dict(shape=(128, 128, 128), n=50_000)],
                      share=[0.7, 0.3], queries=128, k=10, t1=0.6, t2=0.25,
                      desc="128 queries per launch, 70% vs 100,000 x 64^3 and 30% vs 50,000 x "
@@ -478,6 +483,100 @@ def run_embed(args, wl, torch):
     return 0
 
 
+def run_pde(args, wl, torch):
+    """Database generation by the GPU forward model: simulate, threshold and
+    pack.  Timed per step: rd_simulate of `sims` parameter sets into device
+    memory, then db_load_volumes of those volumes into a bit-packed database."""
+    from paper_2205_04550_gb300 import DBQ_STORE_BITS, Database, ForwardModel, _dbq, synth
+    rank, world, local = _dist_env()
+    shape, sims = wl["shape"], wl["sims"]
+    nx, ny, nz = shape
+    tissue = synth.brain_tissue(shape)
+    total = sims * (args.warmup + args.steps)
+    theta = synth.rd_params(shape, synth.DB_SEED + rank, np.arange(total))
+    fm = ForwardModel(tissue, batch=wl["batch"])
+    db = Database(shape, sims * args.steps, DBQ_STORE_BITS, wl["t1"], wl["t2"], synth.N_RD_PARAMS)
+    out = torch.empty((sims, nz, ny, nx), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step(i, load_at=None):
+        th = theta[i * sims:(i + 1) * sims]
+        _, steps = fm.simulate(th, out=out, u0=wl["u0"], cfl=wl["cfl"], stream=stream)
+        if load_at is not None:
+            _dbq.db_load_volumes(db.handle, load_at, sims, out, params=th, stream=stream)
+        return steps, fm.stats()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    first_vis = vis.split(",")[local] if vis and len(vis.split(",")) > local else ""
+    clocks = ClockSampler(int(first_vis) if first_vis.isdigit() else local)
+    clocks.start()
+    time.sleep(0.5)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    step_ms = launches = updates = 0.0
+    all_steps = []
+    wall0 = time.time()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for i in range(args.steps):
+        st, stats = step(args.warmup + i, load_at=i * sims)
+        all_steps.append(st)
+        step_ms += stats["step_ms"]
+        launches += stats["step_launches"]
+        updates += stats["voxel_updates"]
+    t1.record(stream)
+    torch.cuda.synchronize()
+    wall1 = time.time()
+    import torch.distributed as tdist
+    elapsed = max_over_ranks(t0.elapsed_time(t1) / 1000.0, tdist, "cuda")
+    clocks.stop()
+    db.build()
+    # a query of the generated database (its own entry 0 as the patient)
+    hits, _ = db.query(out[0].contiguous(), 5)
+    _, sizes = db.masks(0, sims * args.steps)
+    visible = {"t1gd_nonempty": float(np.mean(sizes[:, 0] > 0)),
+               "flair_nonempty": float(np.mean(sizes[:, 1] > 0)),
+               "t1gd_median_voxels": float(np.median(sizes[:, 0])),
+               "flair_median_voxels": float(np.median(sizes[:, 1]))}
+    n_steps = np.concatenate(all_steps)
+    peak, peak_kind = _peaks()
+    ach = updates * 8.0 / (step_ms / 1000.0) / 1e9
+    roof = {"bound": "hbm", "kernel": "rd_step_kernel", "achieved": ach, "peak": peak,
+            "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+            "algorithmic_bytes_per_launch": updates * 8.0 / max(launches, 1),
+            "note": "8 B per voxel update (read u, write u); the face coefficients "
+                    "(12 B/voxel, shared by the batch) are L2-resident re-reads",
+            "kernel_ms_per_launch": step_ms / max(launches, 1)}
+    value = world * sims * args.steps / elapsed
+    line = {
+        "metric": "forward-model simulations/s (database generation)", "value": value,
+        "unit": "simulations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * elapsed / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "desc": wl["desc"], "grid": list(shape),
+                   "sims_per_step": sims, "batch": wl["batch"], "cfl": wl["cfl"],
+                   "l2": "fields of a batch (2 x 16 x 8 MiB) stream through HBM; no flush"},
+        "explicit_steps": {"mean": float(n_steps.mean()), "min": int(n_steps.min()),
+                           "max": int(n_steps.max())},
+        "step_kernel": {"ms_total": step_ms, "launches": int(launches),
+                        "voxel_updates": int(updates),
+                        "updates_per_s": updates / (step_ms / 1000.0)},
+        "generated_masks": visible,
+        "query_of_generated_db": {"index": int(hits["index"][0]),
+                                  "score": float(hits["score"][0])},
+        "gpu_launches": int(launches) + 4 * args.steps,
+        "roofline": roof,
+        "clocks": clocks.summary(wall0, wall1),
+    }
+    fm.close()
+    db.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
 def _mix_databases(torch, wl, embed=False):
     dbs = []
     for part in wl["mix"]:
@@ -702,6 +801,8 @@ def main(argv=None):
     build.build()
     if wl.get("embed") or wl.get("sketch"):
         return run_embed(args, wl, torch)
+    if args.workload == "pde_db_128":
+        return run_pde(args, wl, torch)
     if args.workload == "plan_mix":
         return run_plan_mix(args, wl, torch)
     if args.workload == "serve_mix":

@@ -545,6 +545,8 @@ int64_t oracle_rd_simulate(const float* tissue, int nx, int ny, int nz, const do
     u[seed] = u0;
     const int64_t sy = nx, sz = (int64_t)nx * ny;
     for (int64_t step = 0; step < n; ++step) {
+        /* voxels of one step are independent: spread the planes over cores */
+#pragma omp parallel for schedule(static)
         for (int z = 0; z < nz; ++z)
             for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < nx; ++x) {

@@ -20,7 +20,7 @@ from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_FLAG_SKETCH,
                    db_stage_times, DBQ_OPT_SPARSE, DBQ_PLAN_ITEMS_PER_SM, db_plan_create,
                    db_plan_set, db_plan_query, db_plan_destroy, db_create_downsampled)
 
-__all__ = ["Database", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_F16", "DBQ_BITS",
+__all__ = ["Database", "ForwardModel", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_F16", "DBQ_BITS",
            "DBQ_STORE_BITS", "DBQ_STORE_F16", "DBQ_FLAG_EMBED", "DBQ_FLAG_SKETCH",
            "DBQ_MODE_EXACT", "DBQ_MODE_EMBED_BF16", "DBQ_MODE_EMBED_FP8", "DBQ_MODE_HASH",
            "SKETCH_DIMS", "db_get_codes", "db_query_batch", "db_prefilter",
@@ -30,6 +30,44 @@ __all__ = ["Database", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_F16", "DBQ_BITS"
            "db_build_masks", "db_query", "db_query_async", "db_prepare_patient",
            "db_query_prepared", "db_scan_counts", "db_get_masks",
            "db_info", "db_destroy", "db_last_error"]
+
+
+class ForwardModel:
+    """The tumour forward model of Section 2.1 (Eq. 1-2) on one grid and
+    tissue map; ``simulate`` returns u(T_end) for rows of theta =
+    (x, y, z, D_w, rho, T_end).  See include/rd.h for the scheme."""
+
+    def __init__(self, tissue, batch: int = 0):
+        t = tissue
+        nz, ny, nx = (int(d) for d in t.shape)
+        self.shape = (nx, ny, nz)
+        self.handle = _dbq.rd_create(nx, ny, nz, t if not isinstance(t, np.ndarray)
+                                     else np.ascontiguousarray(t, dtype=np.float32), batch)
+
+    def simulate(self, theta, out=None, u0: float = 1.0, cfl: float = 0.9, stream=None):
+        """-> (u [count, nz, ny, nx] float32 (``out`` if given: host array or
+        device tensor), steps [count] int64)."""
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, 6)
+        nx, ny, nz = self.shape
+        if out is None:
+            out = np.zeros((th.shape[0], nz, ny, nx), dtype=np.float32)
+        steps = np.zeros(th.shape[0], dtype=np.int64)
+        _dbq.rd_simulate(self.handle, th, out, u0, cfl, steps, stream)
+        return out, steps
+
+    def stats(self) -> dict:
+        return _dbq.rd_stats(self.handle)
+
+    def close(self):
+        if self.handle:
+            _dbq.rd_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 class Database:

@@ -110,7 +110,17 @@ _SIGS = [
     ("db_last_error", ctypes.c_char_p, []),
 ]
 
-EXPORTED = [name for name, _, _ in _SIGS]
+# the forward model (include/rd.h)
+_SIGS += [
+    ("rd_create", ctypes.c_int, [ctypes.POINTER(_P), ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                 ctypes.c_int]),
+    ("rd_simulate", ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_float, ctypes.c_double, _P, _P,
+                                   _P]),
+    ("rd_stats", ctypes.c_int, [_P, _P]),
+    ("rd_destroy", ctypes.c_int, [_P]),
+]
+EXPORTED = [name for name, _, _ in _SIGS if name.startswith("db_")]
+EXPORTED_RD = [name for name, _, _ in _SIGS if name.startswith("rd_")]
 
 
 def library_path() -> str:
@@ -372,3 +382,28 @@ def db_last_error() -> str:
 def hits_from_device(t) -> np.ndarray:
     """View a device buffer of dbq_hit records (copied to host) as HIT_DTYPE."""
     return t.cpu().numpy().view(HIT_DTYPE).reshape(-1)
+
+
+# ---------------------------------------------------------------- forward model
+def rd_create(nx: int, ny: int, nz: int, tissue, batch: int = 0) -> int:
+    h = _P()
+    _check(load().rd_create(ctypes.byref(h), nx, ny, nz, _ptr(tissue), batch))
+    return h.value
+
+
+def rd_simulate(rs: int, theta, out, u0: float = 1.0, cfl: float = 0.9, steps=None, stream=None):
+    th = np.ascontiguousarray(theta, dtype=np.float64).reshape(-1, 6)
+    _check(load().rd_simulate(rs, th.shape[0], th.ctypes.data, u0, cfl, _ptr(out), _ptr(steps),
+                              _stream(stream)))
+
+
+def rd_stats(rs: int) -> dict:
+    out = np.zeros(4, dtype=np.float64)
+    _check(load().rd_stats(rs, out.ctypes.data))
+    return {"step_ms": float(out[0]), "step_launches": int(out[1]),
+            "voxel_updates": int(out[2]), "slots": int(out[3])}
+
+
+def rd_destroy(rs: int):
+    if rs:
+        load().rd_destroy(rs)

@@ -16,6 +16,7 @@
 
 #include "dbq.h"
 #include "kernels.h"
+#include "rd.h"
 
 namespace {
 
@@ -613,6 +614,71 @@ struct dbq_plan {
         if (copied) cudaEventDestroy(copied);
     }
 };
+
+// Forward-model solver (rd.h): the tissue map, its face coefficients and
+// the ping-pong fields of one batch of simulations.
+struct rd_solver {
+    int device = 0;
+    int nx = 0, ny = 0, nz = 0;
+    int64_t v = 0;
+    int batch = 0;
+    std::vector<float> tissue;      // host copy (seed checks, max)
+    double m_max = 0.0;
+    float* m_dev = nullptr;
+    float* hx = nullptr;
+    float* hy = nullptr;
+    float* hz = nullptr;
+    float* hym = nullptr;
+    unsigned int* tile_any = nullptr;
+    dbq::RdSim* sims = nullptr;     // [batch]
+    float* buf0 = nullptr;          // [batch][V]
+    float* buf1 = nullptr;
+    unsigned long long* updates = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    double stats[4] = {0, 0, 0, 0};
+    bool ran = false;
+    std::mutex mu;
+
+    ~rd_solver()
+    {
+        cudaFree(m_dev);
+        cudaFree(hx);
+        cudaFree(hy);
+        cudaFree(hz);
+        cudaFree(hym);
+        cudaFree(tile_any);
+        cudaFree(sims);
+        cudaFree(buf0);
+        cudaFree(buf1);
+        cudaFree(updates);
+        if (ev0) cudaEventDestroy(ev0);
+        if (ev1) cudaEventDestroy(ev1);
+    }
+};
+
+namespace {
+
+template <typename T>
+int rd_alloc(T** p, size_t bytes, const char* what)
+{
+    if (cudaMalloc(reinterpret_cast<void**>(p), bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(DBQ_ENOMEM, "device allocation of %zu bytes for %s failed", bytes, what);
+    }
+    return DBQ_OK;
+}
+
+// Explicit-Euler step count of the scheme in rd.h (binary64, no contraction).
+int64_t rd_step_count(double t_end, double dw, double rho, double m_max, double cfl)
+{
+    if (!(t_end > 0.0)) return 0;
+    const double rate = 6.0 * dw * m_max + rho;
+    const double n = std::ceil(t_end * rate / cfl);
+    return n < 1.0 ? 1 : (int64_t)n;
+}
+
+}  // namespace
 
 extern "C" {
 
@@ -1486,6 +1552,236 @@ int db_destroy(dbq_db* db)
         cudaDeviceSynchronize();
         delete db;
     }
+    return DBQ_OK;
+}
+
+int rd_create(rd_solver** out, int nx, int ny, int nz, const float* tissue, int batch)
+{
+    if (!out) return fail(DBQ_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return fail(DBQ_EINVAL, "grid dimensions must be >= 1");
+    const int64_t v = (int64_t)nx * ny * nz;
+    if (v >= (int64_t(1) << 31)) return fail(DBQ_EINVAL, "grid too large");
+    if (!tissue) return fail(DBQ_EINVAL, "tissue is NULL");
+    if (batch == 0) batch = 16;
+    if (batch < 1 || batch > 1024) return fail(DBQ_EINVAL, "batch must be in [1, 1024]");
+    int dev = 0;
+    DBQ_CUDA(cudaGetDevice(&dev));
+    rd_solver* rs = new (std::nothrow) rd_solver;
+    if (!rs) return fail(DBQ_ENOMEM, "host allocation failed");
+    rs->device = dev;
+    rs->nx = nx;
+    rs->ny = ny;
+    rs->nz = nz;
+    rs->v = v;
+    rs->batch = batch;
+    try {
+        rs->tissue.resize((size_t)v);
+    } catch (...) {
+        delete rs;
+        return fail(DBQ_ENOMEM, "host allocation of the tissue copy failed");
+    }
+    cudaError_t err = cudaMemcpy(rs->tissue.data(), tissue, (size_t)v * 4, cudaMemcpyDefault);
+    if (err != cudaSuccess) {
+        delete rs;
+        return cuda_fail(err, "tissue copy");
+    }
+    for (int64_t i = 0; i < v; ++i) {
+        const float m = rs->tissue[(size_t)i];
+        if (!(m >= 0.0f) || !std::isfinite(m)) {
+            delete rs;
+            return fail(DBQ_EINVAL, "tissue value %lld is negative or not finite", (long long)i);
+        }
+        rs->m_max = std::max(rs->m_max, (double)m);
+    }
+    int rc = rd_alloc(&rs->m_dev, (size_t)v * 4, "tissue map");
+    if (!rc) rc = rd_alloc(&rs->hx, (size_t)v * 4, "x faces");
+    if (!rc) rc = rd_alloc(&rs->hy, (size_t)v * 4, "y faces");
+    if (!rc) rc = rd_alloc(&rs->hz, (size_t)v * 4, "z faces");
+    if (!rc) rc = rd_alloc(&rs->hym, (size_t)v * 4, "-y faces");
+    if (!rc) rc = rd_alloc(&rs->tile_any, (size_t)dbq::rd_tiles(nx, ny, nz) * 4, "tile flags");
+    if (!rc) rc = rd_alloc(&rs->sims, (size_t)batch * sizeof(dbq::RdSim), "simulation table");
+    if (!rc) rc = rd_alloc(&rs->buf0, (size_t)batch * v * 4, "fields (even steps)");
+    if (!rc) rc = rd_alloc(&rs->buf1, (size_t)batch * v * 4, "fields (odd steps)");
+    if (!rc) rc = rd_alloc(&rs->updates, sizeof(unsigned long long), "update counter");
+    if (rc) {
+        delete rs;
+        return rc;
+    }
+    err = cudaMemcpy(rs->m_dev, rs->tissue.data(), (size_t)v * 4, cudaMemcpyHostToDevice);
+    if (err == cudaSuccess)
+        err = dbq::launch_rd_faces(rs->m_dev, nx, ny, nz, rs->hx, rs->hy, rs->hz, rs->hym,
+                                   rs->tile_any, nullptr);
+    if (err == cudaSuccess) err = cudaEventCreate(&rs->ev0);
+    if (err == cudaSuccess) err = cudaEventCreate(&rs->ev1);
+    if (err == cudaSuccess) err = cudaDeviceSynchronize();
+    if (err != cudaSuccess) {
+        delete rs;
+        return cuda_fail(err, "face coefficients");
+    }
+    *out = rs;
+    return DBQ_OK;
+}
+
+int rd_simulate(rd_solver* rs, int count, const double* theta, float u0, double cfl,
+                float* out, int64_t* steps, void* stream)
+{
+    if (!rs) return fail(DBQ_EINVAL, "solver is NULL");
+    std::lock_guard<std::mutex> lock(rs->mu);
+    if (count < 0) return fail(DBQ_EINVAL, "count < 0");
+    if (count == 0) return DBQ_OK;
+    if (!theta || !out) return fail(DBQ_EINVAL, "NULL pointer argument");
+    if (!(u0 > 0.0f && u0 <= 1.0f)) return fail(DBQ_EINVAL, "u0 must be in (0, 1]");
+    if (!(cfl > 0.0 && cfl <= 1.0)) return fail(DBQ_EINVAL, "cfl must be in (0, 1]");
+    std::vector<dbq::RdSim> sims((size_t)count);
+    for (int j = 0; j < count; ++j) {
+        const double* t = theta + (size_t)j * 6;
+        for (int q = 0; q < 6; ++q)
+            if (!std::isfinite(t[q])) return fail(DBQ_EINVAL, "theta[%d] is not finite", j);
+        if (t[3] < 0.0 || t[4] < 0.0 || t[5] < 0.0)
+            return fail(DBQ_EINVAL, "theta[%d]: D_w, rho and T_end must be >= 0", j);
+        const double fx = std::floor(t[0] + 0.5), fy = std::floor(t[1] + 0.5),
+                     fz = std::floor(t[2] + 0.5);
+        if (fx < 0 || fy < 0 || fz < 0 || fx >= rs->nx || fy >= rs->ny || fz >= rs->nz)
+            return fail(DBQ_EINVAL, "theta[%d]: seed outside the grid", j);
+        const int64_t seed = (int64_t)fx + (int64_t)rs->nx * ((int64_t)fy + (int64_t)rs->ny * (int64_t)fz);
+        if (!(rs->tissue[(size_t)seed] > 0.0f))
+            return fail(DBQ_EINVAL, "theta[%d]: seed outside the domain (tissue 0)", j);
+        const int64_t n = rd_step_count(t[5], t[3], t[4], rs->m_max, cfl);
+        if (n > 0x7fffffff) return fail(DBQ_EINVAL, "theta[%d]: too many steps", j);
+        const double dt = n ? t[5] / (double)n : 0.0;
+        dbq::RdSim& p = sims[(size_t)j];
+        p.a = (float)(dt * t[3]);
+        p.b = (float)(dt * t[4]);
+        p.steps = (int32_t)n;
+        p.sx = (int32_t)fx;
+        p.sy = (int32_t)fy;
+        p.sz = (int32_t)fz;
+        p.start = 0;
+    }
+    DeviceGuard guard(rs->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", rs->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // Continuous batching over `slots` slots: longest simulations first, a
+    // slot is refilled (fields zeroed, seed set, table entry replaced) in
+    // stream order right after the launch that ends its simulation.
+    std::vector<int> order((size_t)count);
+    for (int j = 0; j < count; ++j) order[(size_t)j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return sims[(size_t)x].steps > sims[(size_t)y].steps;
+    });
+    const int slots = std::min(rs->batch, count);
+    std::vector<dbq::RdSim> table((size_t)slots);
+    std::vector<int> slot_sim((size_t)slots, -1);
+    for (dbq::RdSim& e : table) e = dbq::RdSim{0.f, 0.f, 0, 0, 0, 0, 0};
+    size_t next = 0;
+    int launch = 0;
+    const size_t vbytes = (size_t)rs->v * 4;
+    auto copy_out = [&](int sl) -> cudaError_t {
+        const dbq::RdSim& e = table[(size_t)sl];
+        const float* src = (e.steps & 1 ? rs->buf1 : rs->buf0) + (size_t)sl * rs->v;
+        return cudaMemcpyAsync(out + (size_t)slot_sim[(size_t)sl] * rs->v, src, vbytes,
+                               cudaMemcpyDefault, s);
+    };
+    // put the next simulation with steps > 0 in slot sl (those with none are
+    // their initial condition: seeded and copied out at once)
+    auto fill = [&](int sl) -> cudaError_t {
+        table[(size_t)sl].steps = 0;
+        slot_sim[(size_t)sl] = -1;
+        while (next < order.size()) {
+            const int j = order[next++];
+            dbq::RdSim e = sims[(size_t)j];
+            e.start = launch;
+            float* b0 = rs->buf0 + (size_t)sl * rs->v;
+            cudaError_t err = cudaMemsetAsync(b0, 0, vbytes, s);
+            if (err == cudaSuccess)
+                err = cudaMemsetAsync(rs->buf1 + (size_t)sl * rs->v, 0, vbytes, s);
+            const int64_t seed = e.sx + (int64_t)rs->nx * (e.sy + (int64_t)rs->ny * e.sz);
+            if (err == cudaSuccess)
+                err = cudaMemcpyAsync(b0 + seed, &u0, sizeof(float), cudaMemcpyHostToDevice, s);
+            if (err != cudaSuccess) return err;
+            table[(size_t)sl] = e;
+            slot_sim[(size_t)sl] = j;
+            if (e.steps > 0) return cudaSuccess;
+            err = copy_out(sl);
+            if (err != cudaSuccess) return err;
+            table[(size_t)sl].steps = 0;
+            slot_sim[(size_t)sl] = -1;
+        }
+        return cudaSuccess;
+    };
+    dbq::RdStepArgs g;
+    g.sims = rs->sims;
+    g.hx = rs->hx;
+    g.hy = rs->hy;
+    g.hz = rs->hz;
+    g.hym = rs->hym;
+    g.tile_any = rs->tile_any;
+    g.buf0 = rs->buf0;
+    g.buf1 = rs->buf1;
+    g.updates = rs->updates;
+    g.nx = rs->nx;
+    g.ny = rs->ny;
+    g.nz = rs->nz;
+    DBQ_CUDA(cudaMemsetAsync(rs->updates, 0, sizeof(unsigned long long), s));
+    DBQ_CUDA(cudaEventRecord(rs->ev0, s));
+    for (int sl = 0; sl < slots; ++sl) {
+        cudaError_t err = fill(sl);
+        if (err != cudaSuccess) return cuda_fail(err, "slot fill");
+    }
+    DBQ_CUDA(cudaMemcpyAsync(rs->sims, table.data(), (size_t)slots * sizeof(dbq::RdSim),
+                             cudaMemcpyHostToDevice, s));
+    for (;;) {
+        bool busy = false;
+        for (const dbq::RdSim& e : table) busy |= e.steps > 0;
+        if (!busy) break;
+        cudaError_t err = dbq::launch_rd_step(g, slots, launch, s);
+        if (err != cudaSuccess) return cuda_fail(err, "step launch");
+        ++launch;
+        bool changed = false;
+        for (int sl = 0; sl < slots; ++sl) {
+            const dbq::RdSim& e = table[(size_t)sl];
+            if (e.steps > 0 && e.start + e.steps == launch) {
+                err = copy_out(sl);
+                if (err == cudaSuccess) err = fill(sl);
+                if (err != cudaSuccess) return cuda_fail(err, "slot refill");
+                changed = true;
+            }
+        }
+        if (changed)
+            DBQ_CUDA(cudaMemcpyAsync(rs->sims, table.data(), (size_t)slots * sizeof(dbq::RdSim),
+                                     cudaMemcpyHostToDevice, s));
+    }
+    DBQ_CUDA(cudaEventRecord(rs->ev1, s));
+    unsigned long long updates = 0;
+    DBQ_CUDA(cudaMemcpyAsync(&updates, rs->updates, sizeof updates, cudaMemcpyDeviceToHost, s));
+    DBQ_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.0f;
+    DBQ_CUDA(cudaEventElapsedTime(&ms, rs->ev0, rs->ev1));
+    if (steps)
+        for (int j = 0; j < count; ++j) steps[j] = sims[(size_t)j].steps;
+    rs->stats[0] = ms;
+    rs->stats[1] = launch;
+    rs->stats[2] = (double)updates;
+    rs->stats[3] = slots;
+    rs->ran = true;
+    return DBQ_OK;
+}
+
+int rd_stats(const rd_solver* rs, double out[4])
+{
+    if (!rs || !out) return fail(DBQ_EINVAL, "NULL pointer argument");
+    if (!rs->ran) return fail(DBQ_ESTATE, "no simulation has run on this solver");
+    for (int i = 0; i < 4; ++i) out[i] = rs->stats[i];
+    return DBQ_OK;
+}
+
+int rd_destroy(rd_solver* rs)
+{
+    if (!rs) return DBQ_OK;
+    DeviceGuard guard(rs->device);
+    cudaDeviceSynchronize();
+    delete rs;
     return DBQ_OK;
 }
 

@@ -112,6 +112,33 @@ int sketch_dims();
 cudaError_t launch_sketch(const uint32_t* planes, int64_t count, int64_t wp, int64_t words,
                           uint16_t* out_bf16, uint8_t* out_f8, float* out_scale, float* out_nb,
                           float* out_nf, uint32_t* out_code, cudaStream_t stream);
+// Reaction-diffusion forward model (rd.cu).
+struct RdSim {
+    float a;        // dt * D_w
+    float b;        // dt * rho
+    int32_t steps;  // explicit steps of the simulation in this slot (0: slot idle)
+    int32_t sx, sy, sz;   // seed voxel
+    int32_t start;  // launch index of the slot's step 0
+};
+struct RdStepArgs {
+    const RdSim* sims;               // [count]
+    const float* hx;                 // [V] face coefficient to the +x neighbour
+    const float* hy;
+    const float* hz;
+    const float* hym;                // [V] face coefficient to the -y neighbour
+    const unsigned int* tile_any;    // [rd_tiles] 1 if the tile holds a domain voxel
+    float* buf0;                     // [slots][V] u at even steps of each slot
+    float* buf1;                     // [slots][V] u at odd steps
+    unsigned long long* updates;     // voxel updates computed (or NULL)
+    int nx, ny, nz;
+};
+int rd_tiles(int nx, int ny, int nz);
+cudaError_t launch_rd_faces(const float* m, int nx, int ny, int nz, float* hx, float* hy,
+                            float* hz, float* hym, unsigned int* tile_any, cudaStream_t stream);
+// One launch: every slot with start <= launch < start + steps advances by one
+// step (its local step launch - start).
+cudaError_t launch_rd_step(const RdStepArgs& g, int slots, int launch, cudaStream_t stream);
+
 // Hamming distances of sign codes (2 * D/32 words per entry and per query):
 // dist [nq][n] binary32 (exact integers).
 cudaError_t launch_hamming(const uint32_t* codes, int64_t n, const uint32_t* qcodes, int nq,

@@ -260,9 +260,12 @@ def rd_params(shape, seed: int, entries) -> np.ndarray:
     white-matter point 0.4 semi-axes right of the centre).  D_w ~ U(0.05, 0.5)
     voxel^2/day (draw 500), rho ~ U(0.025, 0.25) /day (draw 501); the paper
     discards simulations of unrealistic size, so instead of drawing T_end
-    freely the visible radius R ~ U(6, 30) voxels is drawn (draw 502) and
-    T_end = R / (2 sqrt(D_w rho)), the time a Fisher-KPP front of speed
-    2 sqrt(D_w rho) needs to travel R."""
+    freely the front radius R ~ U(6, 30) voxels is drawn (draw 502) and
+    T_end is the time at which a Fisher-KPP front from a point source reaches
+    it: in three dimensions the front sits near c t - (5 / (2 lambda)) ln t
+    with c = 2 sqrt(D_w rho), lambda = sqrt(rho / D_w) (the logarithmic delay
+    of a radial front from a point source), solved for t by 30
+    fixed-point steps from t = R / c (t >= 1)."""
     keys = stream_keys(seed, entries)
     n = keys.shape[0]
     tissue = brain_tissue(shape)
@@ -290,7 +293,12 @@ def rd_params(shape, seed: int, entries) -> np.ndarray:
     theta[:, 3] = 0.05 + 0.45 * _uniform(keys, 500)
     theta[:, 4] = 0.025 + 0.225 * _uniform(keys, 501)
     radius = 6.0 + 24.0 * _uniform(keys, 502)
-    theta[:, 5] = radius / (2.0 * np.sqrt(theta[:, 3] * theta[:, 4]))
+    c = 2.0 * np.sqrt(theta[:, 3] * theta[:, 4])
+    lam = np.sqrt(theta[:, 4] / theta[:, 3])
+    t = radius / c
+    for _ in range(30):
+        t = (radius + 2.5 / lam * np.log(np.maximum(t, 1.0))) / c
+    theta[:, 5] = t
     return theta
 
 

@@ -9,9 +9,9 @@ from paper_2205_04550_gb300 import _dbq, build
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared(header):
+def _declared(header, prefix="db_"):
     text = open(os.path.join(ROOT, "include", header)).read()
-    return set(re.findall(r"^\s*(?:int|const char\*)\s+(db_\w+)\s*\(", text, re.M))
+    return set(re.findall(r"^\s*(?:int|const char\*)\s+(" + prefix + r"\w+)\s*\(", text, re.M))
 
 
 def test_libdbq_exports_every_declared_symbol():
@@ -21,6 +21,11 @@ def test_libdbq_exports_every_declared_symbol():
     for name in sorted(declared):
         assert hasattr(lib, name), name
     assert declared == set(_dbq.EXPORTED)
+    rd = _declared("rd.h", "rd_")
+    assert rd == {"rd_create", "rd_simulate", "rd_stats", "rd_destroy"}
+    for name in sorted(rd):
+        assert hasattr(lib, name), name
+    assert rd == set(_dbq.EXPORTED_RD)
 
 
 def test_binding_loads_and_reports_no_error():
