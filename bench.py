@@ -58,6 +58,10 @@ WORKLOADS = {
                                  desc="100,000 x 128^3 bit-packed + count sketches (2x4096) and "
                                       "their sign codes; Hamming prefilter 512, exact re-rank, "
                                       "256 queries, top-15"),
+    "sketch_10k_128_hash": dict(shape=(128, 128, 128), n=10_000, k=15, t1=0.6, t2=0.25,
+                                sketch=True, queries=256, candidates=512, mode="hash",
+                                desc="10,000 x 128^3 + count sketches and sign codes, Hamming "
+                                     "prefilter (profiling size)"),
     "sketch_100k_128_bf16": dict(shape=(128, 128, 128), n=100_000, k=15, t1=0.6, t2=0.25,
                                  sketch=True, queries=256, candidates=512, mode="bf16",
                                  desc="100,000 x 128^3 bit-packed + bf16 count sketches "
@@ -533,9 +537,12 @@ def run_pde(args, wl, torch):
     elapsed = max_over_ranks(t0.elapsed_time(t1) / 1000.0, tdist, "cuda")
     clocks.stop()
     db.build()
-    # a query of the generated database (its own entry 0 as the patient)
-    hits, _ = db.query(out[0].contiguous(), 5)
     _, sizes = db.masks(0, sims * args.steps)
+    # a query of the generated database: the last step's entry with the
+    # largest FLAIR mask as the patient (it must find itself at score 1)
+    last = sizes[-sims:, 1]
+    q = int(np.argmax(last))
+    hits, _ = db.query(out[q].contiguous(), 5)
     visible = {"t1gd_nonempty": float(np.mean(sizes[:, 0] > 0)),
                "flair_nonempty": float(np.mean(sizes[:, 1] > 0)),
                "t1gd_median_voxels": float(np.median(sizes[:, 0])),
@@ -564,7 +571,8 @@ def run_pde(args, wl, torch):
                         "voxel_updates": int(updates),
                         "updates_per_s": updates / (step_ms / 1000.0)},
         "generated_masks": visible,
-        "query_of_generated_db": {"index": int(hits["index"][0]),
+        "query_of_generated_db": {"patient_entry": sims * (args.steps - 1) + q,
+                                  "index": int(hits["index"][0]),
                                   "score": float(hits["score"][0])},
         "gpu_launches": int(launches) + 4 * args.steps,
         "roofline": roof,
