@@ -96,8 +96,8 @@ DEFAULT_WORKLOAD = "exact_packed_50k_128"
 TRAFFIC = {
     "scan_packed_kernel": dict(files=("scan_packed.cu", "scan_core.cuh", "topk.cuh",
                                       "common.cuh"),
-                               sha="7327dbf9102ae100", entries=2000,
-                               read_bytes=1049188352, write_bytes=3352320,
+                               sha="6c56322f5d16fbf3", entries=2000,
+                               read_bytes=1049182208, write_bytes=3328256,
                                capture="profiles/scan_packed_2k_128_ncu_full.md"),
     "scan_f16_kernel": dict(files=("scan_f16.cu", "topk.cuh", "common.cuh"),
                             sha="96842491439226c1", entries=4000,

@@ -3,9 +3,10 @@
 // Section 2.3 of Ezhov et al. (2022): the simulated concentration u is
 // thresholded at u_T1Gd and u_FLAIR to give the two binary segmentations
 // compared with the patient's.  A voxel is in mask k when (float)u >= t_k.
-// Each warp turns 32 consecutive voxels into one 32-bit word per mask with
-// two ballots (bit b of word w = voxel 32w + b) and accumulates the mask
-// sizes |E_1|, |E_2| with popcounts.
+// Bit b of word w of a plane is voxel 32w + b.  Each lane tests the voxels
+// of one 16-byte load and the lanes sharing a word OR their bits together
+// (or, for unaligned sources, a warp tests 32 voxels and ballots); the mask
+// sizes |E_1|, |E_2| are popcounts of the words.
 #include <cuda_fp16.h>
 
 #include "kernels.h"
@@ -26,19 +27,68 @@ __device__ __forceinline__ float load_value(const void* base, int64_t i)
     return __ldg(reinterpret_cast<const float*>(base) + i);
 }
 
+// One volume: a warp-strided loop over the planes' words.  When the source
+// is 16-byte aligned and V is a multiple of the voxels in 16 bytes, each lane
+// loads 16 bytes (4 binary32 or 8 binary16 voxels), builds their bits for
+// both thresholds, and the LPW lanes of one 32-voxel word OR their pieces
+// together by shuffles; otherwise one voxel per lane and two ballots per word.
 template <bool kHalf>
-__global__ void __launch_bounds__(kPackThreads)
-pack_kernel(const void* __restrict__ vols, int64_t v, int64_t wp, float t1, float t2,
-            uint32_t* __restrict__ planes, uint32_t* __restrict__ ecount, int64_t e_base)
+__device__ __forceinline__ void pack_volume(const void* __restrict__ src, int64_t v, int64_t wp,
+                                            float t1, float t2, uint32_t* __restrict__ p1,
+                                            uint32_t* __restrict__ p2, int64_t warp,
+                                            int64_t nwarps, uint32_t& c1, uint32_t& c2)
 {
-    const int64_t e = e_base + blockIdx.y;
     const int lane = threadIdx.x & 31;
-    const int64_t warp = ((int64_t)blockIdx.x * kPackThreads + threadIdx.x) >> 5;
-    const int64_t nwarps = ((int64_t)gridDim.x * kPackThreads) >> 5;
-    const char* src = reinterpret_cast<const char*>(vols) + e * v * (kHalf ? 2 : 4);
-    uint32_t* p1 = planes + e * 2 * wp;
-    uint32_t* p2 = p1 + wp;
-    uint32_t c1 = 0, c2 = 0;
+    constexpr int VPL = kHalf ? 8 : 4;      // voxels per lane per 16-byte load
+    constexpr int LPW = 32 / VPL;           // lanes per 32-bit word
+    constexpr int WPL = 32 / LPW;           // words per warp-wide load
+    const bool vec = (reinterpret_cast<uintptr_t>(src) & 15u) == 0 && v % VPL == 0;
+    if (vec) {
+        const int64_t groups = (wp + WPL - 1) / WPL;
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        for (int64_t g0 = warp * kPackUnroll; g0 < groups; g0 += nwarps * kPackUnroll) {
+            uint4 raw[kPackUnroll];
+#pragma unroll
+            for (int u = 0; u < kPackUnroll; ++u) {
+                const int64_t vox = (g0 + u) * (WPL * 32) + (int64_t)lane * VPL;
+                raw[u] = (g0 + u < groups && vox < v) ? __ldg(s4 + vox / VPL) : make_uint4(0, 0, 0, 0);
+            }
+#pragma unroll
+            for (int u = 0; u < kPackUnroll; ++u) {
+                const int64_t g = g0 + u;
+                const int64_t vox = g * (WPL * 32) + (int64_t)lane * VPL;
+                const uint32_t r[4] = {raw[u].x, raw[u].y, raw[u].z, raw[u].w};
+                uint32_t m1 = 0, m2 = 0;
+#pragma unroll
+                for (int j = 0; j < VPL; ++j) {
+                    float val;
+                    if (kHalf)
+                        val = __half2float(__ushort_as_half(
+                            (unsigned short)((r[j / 2] >> (16 * (j % 2))) & 0xffffu)));
+                    else
+                        val = __uint_as_float(r[j]);
+                    m1 |= (uint32_t)(val >= t1) << j;
+                    m2 |= (uint32_t)(val >= t2) << j;
+                }
+                if (vox >= v) m1 = m2 = 0;
+                m1 <<= VPL * (lane % LPW);
+                m2 <<= VPL * (lane % LPW);
+#pragma unroll
+                for (int off = 1; off < LPW; off <<= 1) {
+                    m1 |= __shfl_xor_sync(0xffffffffu, m1, off);
+                    m2 |= __shfl_xor_sync(0xffffffffu, m2, off);
+                }
+                const int64_t w = g * WPL + lane / LPW;
+                if (lane % LPW == 0 && g < groups && w < wp) {
+                    p1[w] = m1;
+                    p2[w] = m2;
+                    c1 += __popc(m1);
+                    c2 += __popc(m2);
+                }
+            }
+        }
+        return;
+    }
     for (int64_t w0 = warp * kPackUnroll; w0 < wp; w0 += nwarps * kPackUnroll) {
         float val[kPackUnroll];
 #pragma unroll
@@ -61,7 +111,23 @@ pack_kernel(const void* __restrict__ vols, int64_t v, int64_t wp, float t1, floa
             }
         }
     }
-    if (lane == 0 && (c1 | c2)) {
+}
+
+template <bool kHalf>
+__global__ void __launch_bounds__(kPackThreads)
+pack_kernel(const void* __restrict__ vols, int64_t v, int64_t wp, float t1, float t2,
+            uint32_t* __restrict__ planes, uint32_t* __restrict__ ecount, int64_t e_base)
+{
+    const int64_t e = e_base + blockIdx.y;
+    const int64_t warp = ((int64_t)blockIdx.x * kPackThreads + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * kPackThreads) >> 5;
+    const char* src = reinterpret_cast<const char*>(vols) + e * v * (kHalf ? 2 : 4);
+    uint32_t* p1 = planes + e * 2 * wp;
+    uint32_t c1 = 0, c2 = 0;
+    pack_volume<kHalf>(src, v, wp, t1, t2, p1, p1 + wp, warp, nwarps, c1, c2);
+    c1 = __reduce_add_sync(0xffffffffu, c1);
+    c2 = __reduce_add_sync(0xffffffffu, c2);
+    if ((threadIdx.x & 31) == 0 && (c1 | c2)) {
         atomicAdd(&ecount[2 * e], c1);
         atomicAdd(&ecount[2 * e + 1], c2);
     }
@@ -74,35 +140,14 @@ pack_ptrs_kernel(const void* const* __restrict__ srcs, int64_t v, int64_t wp, fl
                  uint32_t* __restrict__ planes, uint32_t* __restrict__ ecount)
 {
     const int64_t e = blockIdx.y;
-    const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * kPackThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kPackThreads) >> 5;
-    const void* src = srcs[e];
     uint32_t* p1 = planes + e * 2 * wp;
-    uint32_t* p2 = p1 + wp;
     uint32_t c1 = 0, c2 = 0;
-    for (int64_t w0 = warp * kPackUnroll; w0 < wp; w0 += nwarps * kPackUnroll) {
-        float val[kPackUnroll];
-#pragma unroll
-        for (int u = 0; u < kPackUnroll; ++u) {
-            const int64_t x = (w0 + u) * 32 + lane;
-            val[u] = (x < v) ? load_value<kHalf>(src, x) : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < kPackUnroll; ++u) {
-            const int64_t w = w0 + u;
-            const bool in = w * 32 + lane < v;
-            const uint32_t b1 = __ballot_sync(0xffffffffu, in && val[u] >= t1);
-            const uint32_t b2 = __ballot_sync(0xffffffffu, in && val[u] >= t2);
-            if (lane == 0 && w < wp) {
-                p1[w] = b1;
-                p2[w] = b2;
-                c1 += __popc(b1);
-                c2 += __popc(b2);
-            }
-        }
-    }
-    if (lane == 0 && (c1 | c2)) {
+    pack_volume<kHalf>(srcs[e], v, wp, t1, t2, p1, p1 + wp, warp, nwarps, c1, c2);
+    c1 = __reduce_add_sync(0xffffffffu, c1);
+    c2 = __reduce_add_sync(0xffffffffu, c2);
+    if ((threadIdx.x & 31) == 0 && (c1 | c2)) {
         atomicAdd(&ecount[2 * e], c1);
         atomicAdd(&ecount[2 * e + 1], c2);
     }
@@ -155,6 +200,19 @@ __global__ void rows_to_f16_kernel(const void* __restrict__ src, int64_t v, int6
     }
 }
 
+// Blocks per volume: enough warps for the words of one volume (4 words per
+// warp-iteration at least), 64 per volume for many volumes, and enough to
+// fill the GPU (about 8 blocks per SM) when there are few.
+int64_t pack_blocks(int64_t wp, int64_t count)
+{
+    const int64_t warps_needed = (wp + kPackUnroll * 4 - 1) / (kPackUnroll * 4);
+    const int64_t most = (warps_needed * 32 + kPackThreads - 1) / kPackThreads;
+    int64_t bx = (1216 + count - 1) / count;
+    if (bx < 64) bx = 64;
+    if (bx > most) bx = most;
+    return bx < 1 ? 1 : bx;
+}
+
 }  // namespace
 
 cudaError_t launch_rows_to_f16(const void* src, int src_f16, int64_t count, int64_t v,
@@ -192,10 +250,7 @@ cudaError_t launch_pack(const void* vols, int src_f16, int64_t count, int64_t v,
                         cudaStream_t stream)
 {
     if (count <= 0) return cudaSuccess;
-    const int64_t warps_needed = (wp + kPackUnroll - 1) / kPackUnroll;
-    int64_t bx = (warps_needed * 32 + kPackThreads - 1) / kPackThreads;
-    if (bx > 64) bx = 64;
-    if (bx < 1) bx = 1;
+    const int64_t bx = pack_blocks(wp, count);
     for (int64_t e0 = 0; e0 < count; e0 += 65535) {
         const int64_t ce = (count - e0) < 65535 ? (count - e0) : 65535;
         dim3 grid((unsigned)bx, (unsigned)ce);
@@ -216,10 +271,7 @@ cudaError_t launch_pack_ptrs(const void* const* srcs, int src_f16, int count, in
                              cudaStream_t stream)
 {
     if (count <= 0) return cudaSuccess;
-    const int64_t warps_needed = (wp + kPackUnroll - 1) / kPackUnroll;
-    int64_t bx = (warps_needed * 32 + kPackThreads - 1) / kPackThreads;
-    if (bx > 64) bx = 64;
-    if (bx < 1) bx = 1;
+    const int64_t bx = pack_blocks(wp, count);
     dim3 grid((unsigned)bx, (unsigned)count);
     if (src_f16)
         pack_ptrs_kernel<true><<<grid, kPackThreads, 0, stream>>>(srcs, v, wp, t1, t2, planes, ecount);
