@@ -58,10 +58,10 @@ WORKLOADS = {
                                  desc="100,000 x 128^3 bit-packed + count sketches (2x4096) and "
                                       "their sign codes; Hamming prefilter 512, exact re-rank, "
                                       "256 queries, top-15"),
-    "sketch_10k_128_hash": dict(shape=(128, 128, 128), n=10_000, k=15, t1=0.6, t2=0.25,
-                                sketch=True, queries=256, candidates=512, mode="hash",
-                                desc="10,000 x 128^3 + count sketches and sign codes, Hamming "
-                                     "prefilter (profiling size)"),
+    "sketch_2k_128_hash": dict(shape=(128, 128, 128), n=2000, k=15, t1=0.6, t2=0.25,
+                               sketch=True, queries=256, candidates=512, mode="hash",
+                               desc="2,000 x 128^3 + count sketches and sign codes, Hamming "
+                                    "prefilter (profiling size, 1.1 GB on the device)"),
     "sketch_100k_128_bf16": dict(shape=(128, 128, 128), n=100_000, k=15, t1=0.6, t2=0.25,
                                  sketch=True, queries=256, candidates=512, mode="bf16",
                                  desc="100,000 x 128^3 bit-packed + bf16 count sketches "
