@@ -62,6 +62,15 @@ WORKLOADS = {
                                sketch=True, queries=256, candidates=512, mode="hash",
                                desc="2,000 x 128^3 + count sketches and sign codes, Hamming "
                                     "prefilter (profiling size, 1.1 GB on the device)"),
+    "sketch_100k_32_bf16": dict(shape=(32, 32, 32), n=100_000, k=15, t1=0.6, t2=0.25,
+                                sketch=True, queries=256, candidates=512, mode="bf16",
+                                desc="100,000 x 32^3 + bf16 count sketches (2x4096): the "
+                                     "full-size prefilter GEMM (256 x 100,000 x 8,192) with "
+                                     "3.3 GB on the device (profiling size)"),
+    "sketch_100k_32_hash": dict(shape=(32, 32, 32), n=100_000, k=15, t1=0.6, t2=0.25,
+                                sketch=True, queries=256, candidates=512, mode="hash",
+                                desc="100,000 x 32^3 + sign codes: the full-size Hamming "
+                                     "prefilter with 3.3 GB on the device (profiling size)"),
     "sketch_100k_128_bf16": dict(shape=(128, 128, 128), n=100_000, k=15, t1=0.6, t2=0.25,
                                  sketch=True, queries=256, candidates=512, mode="bf16",
                                  desc="100,000 x 128^3 bit-packed + bf16 count sketches "
