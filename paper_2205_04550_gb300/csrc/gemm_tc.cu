@@ -16,8 +16,13 @@
 //     (M = 128 entries, N = 256 queries, K = 16 bf16 or 32 fp8 per
 //     instruction): columns [0, 256) accumulate q_1 . e_1, [256, 512)
 //     q_2 . e_2; tcgen05.commit frees each stage and signals the epilogue;
-//   * warps 2-5 read the accumulators with tcgen05.ld (each warp its 32-lane
-//     quarter), form L in binary32 and store L[q][e] coalesced.
+//   * warps 2-9 read the accumulators with tcgen05.ld (a warp may only touch
+//     its 32-lane quarter, warp % 4; two warps share a quarter and take 128
+//     query columns each), form L in binary32 and store L[q][e] coalesced.  The square
+//     roots use the SFU's sqrt.approx.f32 (relative error about 2^-23): the
+//     epilogue runs while the tensor cores wait for TMEM, and the correctly
+//     rounded square root with its special-case path doubled the launch time;
+//     the error is far inside the tolerance of the binary32 accumulation.
 // Every mbarrier wait is bounded (iteration count and %globaltimer); on a
 // timeout the CTA records an error code in `status`, stops issuing work,
 // waits (bounded) for the copies and MMAs it has in flight, frees its TMEM
@@ -35,7 +40,8 @@ constexpr int kStages = 4;
 constexpr int kTileABytes = kBM * 128;   // 128 rows x 128 bytes (one swizzle atom wide)
 constexpr int kTileBBytes = kBN * 128;
 constexpr int kStageBytes = kTileABytes + kTileBBytes;
-constexpr int kThreads = 192;            // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int kEpiWarps = 8;             // two per TMEM lane quarter, 128 columns each
+constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -157,6 +163,13 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
         : "r"(taddr));
 }
 
+__device__ __forceinline__ float sqrt_approx(float x)
+{
+    float y;
+    asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ void tmem_wait_ld()
 {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
@@ -211,7 +224,7 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             mbar_init(empty0 + 8 * s, 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 128);
+        mbar_init(acc_empty, 32 * kEpiWarps);
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -299,8 +312,9 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             if (!mbar_wait(drain, 0, nullptr)) a.status[0] = 3;
         }
     } else {
-        // epilogue warps 2..5: TMEM lane quarter = warp % 4
+        // epilogue warps 2..9: TMEM lane quarter = warp % 4, column half by warp
         const int quarter = warp & 3;
+        const int c_begin = ((warp - 2) / 4) * (kBN / 2);
         const int row = quarter * 32 + lane;
         uint32_t tiles_done = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tiles_done) {
@@ -321,13 +335,14 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                     es1 = a.escale[2 * e + 1];
                 }
             }
-            for (int c = 0; c < kBN; c += 32) {
+            for (int c = c_begin; c < c_begin + kBN / 2; c += 32) {
                 uint32_t r0[32], r1[32];
                 const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + c;
                 tmem_ld32(taddr, r0);
                 tmem_ld32(taddr + kBN, r1);
                 tmem_wait_ld();
                 if (valid) {
+                    float* out = a.dist + (int64_t)c * a.n + e;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int q = c + j;
@@ -340,7 +355,7 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                             }
                             const float s0 = fmaxf(qnorm[q] + en0 - 2.0f * dot0, 0.0f);
                             const float s1 = fmaxf(qnorm[kBN + q] + en1 - 2.0f * dot1, 0.0f);
-                            a.dist[(int64_t)q * a.n + e] = sqrtf(s0) + sqrtf(s1);
+                            out[(int64_t)j * a.n] = sqrt_approx(s0) + sqrt_approx(s1);
                         }
                     }
                 }
