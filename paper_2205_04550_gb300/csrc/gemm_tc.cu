@@ -8,10 +8,16 @@
 // segmentation), so they run as a tcgen05 GEMM with fp32 accumulation in
 // tensor memory:
 //
-//   * one CTA per SM, persistent over tiles of 128 entries;
+//   * one CTA per SM, clusters of two CTAs on neighbouring SMs, persistent
+//     over pairs of 128-entry tiles (CTA rank r of the pair takes tile
+//     2p + r; both walk the same pairs so their K-slices stay in step);
 //   * warp 0 (one thread) issues TMA loads of 128-byte-swizzled K-slices of
-//     the entry tile (128 rows) and of all queries (256 rows) into a 4-stage
-//     shared-memory ring guarded by full/empty mbarriers;
+//     its entry tile (128 rows) into a 4-stage shared-memory ring guarded by
+//     full/empty mbarriers; the 256 query rows, which every tile needs, are
+//     loaded once per pair: each CTA loads 128 of them and multicasts them
+//     into the same stage of both CTAs, so L2 serves a third fewer bytes.  A
+//     stage is free again only when both CTAs' MMAs have read it (each MMA
+//     commit arrives on the stage's empty barrier in both CTAs);
 //   * warp 1 owns 512 TMEM columns and one thread issues tcgen05.mma
 //     (M = 128 entries, N = 256 queries, K = 16 bf16 or 32 fp8 per
 //     instruction): columns [0, 256) accumulate q_1 . e_1, [256, 512)
@@ -43,6 +49,8 @@ constexpr int kStageBytes = kTileABytes + kTileBBytes;
 constexpr int kEpiWarps = 8;             // two per TMEM lane quarter, 128 columns each
 constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
+constexpr int kCluster = 2;                               // CTAs sharing the query tiles
+constexpr int kHalfBBytes = kTileBBytes / kCluster;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -109,6 +117,30 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
+// TMA load whose data and completion go to the same shared-memory offsets in
+// every CTA of `mask` (this cluster's CTAs).
+__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                               int x, int y, uint16_t mask)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t cluster_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ void cluster_sync()
+{
+    asm volatile("barrier.cluster.arrive.release;\n barrier.cluster.wait.acquire;" ::: "memory");
+}
+
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
 // 1024 bytes apart.
 __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
@@ -139,6 +171,16 @@ __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t b
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
     }
+}
+
+// Arrives on the mbarrier at this offset in every CTA of `mask` once the
+// MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask)
+{
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"(mask)
+        : "memory");
 }
 
 __device__ __forceinline__ void umma_commit(uint32_t bar)
@@ -191,7 +233,7 @@ __host__ __device__ constexpr uint32_t instr_desc()
 }
 
 template <bool kFp8>
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
 prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                       const __grid_constant__ CUtensorMap tm_q, GemmArgs a)
 {
@@ -211,6 +253,10 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
     const int lane = threadIdx.x & 31;
     const int ktiles = a.dims / (kFp8 ? 128 : 64);                 // K-slices per segmentation
     const int ntiles = (int)((a.n + kBM - 1) / kBM);
+    const int rank = (int)cluster_rank();
+    const int pair0 = blockIdx.x / kCluster, npairs_grid = gridDim.x / kCluster;
+    const int npairs = (ntiles + kCluster - 1) / kCluster;
+    const uint16_t cluster_mask = (uint16_t)((1u << kCluster) - 1u);
 
     const uint32_t full0 = smem_u32(bars);
     const uint32_t empty0 = smem_u32(bars + kStages);
@@ -221,7 +267,7 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, 1);
+            mbar_init(empty0 + 8 * s, kCluster);     // one MMA commit per CTA of the pair
         }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 32 * kEpiWarps);
@@ -242,6 +288,8 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
     }
     tc_fence_before();
     __syncthreads();
+    // the peer's barriers must be initialised before anything is multicast
+    cluster_sync();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
@@ -251,7 +299,9 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
         if (lane == 0) {
             uint32_t it = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+            for (int pair = pair0; pair < npairs && ok; pair += npairs_grid) {
+                // a tile past the last entry reads zeros (out-of-range TMA rows)
+                const int tile = pair * kCluster + rank;
                 for (int seg = 0; seg < 2 && ok; ++seg) {
                     for (int kt = 0; kt < ktiles; ++kt, ++it) {
                         const int s = it % kStages;
@@ -259,10 +309,13 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                         if (!mbar_wait(empty0 + 8 * s, ph, abort_flag)) { ok = false; break; }
                         const uint32_t sa = smem_u32(ring + s * kStageBytes);
                         const uint32_t sb = sa + kTileABytes;
+                        // own entry tile + both halves of the query tile (one
+                        // from this CTA, one multicast by the peer)
                         mbar_arrive_expect_tx(full0 + 8 * s, kStageBytes);
                         const int x = seg * a.dims + kt * (kFp8 ? 128 : 64);
                         tma_load_2d(sa, &tm_e, full0 + 8 * s, x, tile * kBM);
-                        tma_load_2d(sb, &tm_q, full0 + 8 * s, x, 0);
+                        tma_load_2d_mc(sb + rank * kHalfBBytes, &tm_q, full0 + 8 * s, x,
+                                       rank * (kBN / kCluster), cluster_mask);
                         ++issued;
                     }
                 }
@@ -277,7 +330,7 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             constexpr uint32_t idesc = instr_desc<kFp8>();
             uint32_t it = 0, tiles_done = 0;
             bool ok = true;
-            for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++tiles_done) {
+            for (int pair = pair0; pair < npairs && ok; pair += npairs_grid, ++tiles_done) {
                 if (!mbar_wait(acc_empty, (tiles_done & 1) ^ 1, abort_flag)) { ok = false; break; }
                 tc_fence_after();
                 for (int seg = 0; seg < 2 && ok; ++seg) {
@@ -297,7 +350,8 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                             umma<kFp8>(d_tmem, sw128_desc(sa + 32 * kk), sw128_desc(sb + 32 * kk),
                                        idesc, (kt > 0 || kk > 0) ? 1u : 0u);
                         }
-                        umma_commit(empty0 + 8 * s);   // frees the stage when these MMAs finish
+                        // frees the stage in both CTAs when these MMAs finish
+                        umma_commit_mc(empty0 + 8 * s, cluster_mask);
                     }
                 }
                 if (ok) umma_commit(acc_full);
@@ -317,7 +371,8 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
         const int c_begin = ((warp - 2) / 4) * (kBN / 2);
         const int row = quarter * 32 + lane;
         uint32_t tiles_done = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tiles_done) {
+        for (int pair = pair0; pair < npairs; pair += npairs_grid, ++tiles_done) {
+            const int tile = pair * kCluster + rank;
             if (!mbar_wait(acc_full, tiles_done & 1, abort_flag)) {
                 a.status[0] = 4;
                 *abort_flag = 1;
@@ -381,6 +436,9 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
                      : "memory");
     }
+    // neither CTA leaves while the other may still multicast into its shared
+    // memory or arrive on its barriers
+    cluster_sync();
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -433,11 +491,15 @@ cudaError_t launch_prefilter_gemm(const GemmArgs& a, int fp8, int grid, cudaStre
     const void* eb = fp8 ? (const void*)a.e_f8 : (const void*)a.e_bf16;
     const void* qb = fp8 ? (const void*)a.q_f8 : (const void*)a.q_bf16;
     if (!make_map(&tm_e, eb, fp8, a.n, 2 * (int64_t)a.dims, kBM) ||
-        !make_map(&tm_q, qb, fp8, a.nq, 2 * (int64_t)a.dims, kBN))
+        !make_map(&tm_q, qb, fp8, a.nq, 2 * (int64_t)a.dims, kBN / kCluster))
         return cudaErrorInvalidValue;
     const size_t smem = gemm_smem_bytes();
     const int ntiles = (int)((a.n + kBM - 1) / kBM);
-    if (grid > ntiles) grid = ntiles;
+    const int npairs = (ntiles + kCluster - 1) / kCluster;
+    grid = grid / kCluster;                       // clusters, one CTA per SM
+    if (grid > npairs) grid = npairs;
+    if (grid < 1) grid = 1;
+    grid *= kCluster;
     cudaError_t err;
     if (fp8) {
         err = cudaFuncSetAttribute(prefilter_gemm_kernel<true>,
