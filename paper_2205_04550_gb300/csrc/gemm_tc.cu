@@ -21,13 +21,16 @@
 //   * warp 1 owns 512 TMEM columns and one thread issues tcgen05.mma
 //     (M = 128 entries, N = 256 queries, K = 16 bf16 or 32 fp8 per
 //     instruction): columns [0, 256) accumulate q_1 . e_1, [256, 512)
-//     q_2 . e_2; tcgen05.commit frees each stage and signals the epilogue;
+//     q_2 . e_2; tcgen05.commit frees each stage and, per segmentation,
+//     tells the epilogue that its columns are complete;
 //   * warps 2-9 read the accumulators with tcgen05.ld (a warp may only touch
 //     its 32-lane quarter, warp % 4; two warps share a quarter and take 128
-//     query columns each), form L in binary32 and store L[q][e] coalesced.  The square
+//     query columns each), form L in binary32 and store L[q][e] coalesced.
+//     Each segmentation's columns are handed back as soon as they are read,
+//     so the epilogue of one tile runs under the MMAs of the next.  The square
 //     roots use the SFU's sqrt.approx.f32 (relative error about 2^-23): the
-//     epilogue runs while the tensor cores wait for TMEM, and the correctly
-//     rounded square root with its special-case path doubled the launch time;
+//     correctly rounded square root with its special-case path doubled the
+//     launch time;
 //     the error is far inside the tolerance of the binary32 accumulation.
 // Every mbarrier wait is bounded (iteration count and %globaltimer); on a
 // timeout the CTA records an error code in `status`, stops issuing work,
@@ -243,8 +246,8 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* ring = base;                                   // kStages x kStageBytes
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + kStages * kStageBytes);
-    // bars: full[kStages], empty[kStages], acc_full, acc_empty, drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 3);
+    // bars: full[kStages], empty[kStages], seg_full[2], seg_free[2], drain
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kStages + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     float* qnorm = reinterpret_cast<float*>(tmem_slot + 4);       // [2][kBN]
     float* qscale = qnorm + 2 * kBN;                               // [2][kBN]
@@ -260,17 +263,21 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
 
     const uint32_t full0 = smem_u32(bars);
     const uint32_t empty0 = smem_u32(bars + kStages);
-    const uint32_t acc_full = smem_u32(bars + 2 * kStages);
-    const uint32_t acc_empty = smem_u32(bars + 2 * kStages + 1);
-    const uint32_t drain = smem_u32(bars + 2 * kStages + 2);
+    // seg_full[k]: the MMAs of segmentation k of the current tile are done;
+    // seg_free[k]: the epilogue has read TMEM columns [k*256, k*256+256)
+    const uint32_t seg_full0 = smem_u32(bars + 2 * kStages);
+    const uint32_t seg_free0 = smem_u32(bars + 2 * kStages + 2);
+    const uint32_t drain = smem_u32(bars + 2 * kStages + 4);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(full0 + 8 * s, 1);
             mbar_init(empty0 + 8 * s, kCluster);     // one MMA commit per CTA of the pair
         }
-        mbar_init(acc_full, 1);
-        mbar_init(acc_empty, 32 * kEpiWarps);
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(seg_full0 + 8 * k, 1);
+            mbar_init(seg_free0 + 8 * k, 32 * kEpiWarps);
+        }
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -331,9 +338,13 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             uint32_t it = 0, tiles_done = 0;
             bool ok = true;
             for (int pair = pair0; pair < npairs && ok; pair += npairs_grid, ++tiles_done) {
-                if (!mbar_wait(acc_empty, (tiles_done & 1) ^ 1, abort_flag)) { ok = false; break; }
-                tc_fence_after();
                 for (int seg = 0; seg < 2 && ok; ++seg) {
+                    // the previous tile's columns of this segmentation are read
+                    if (!mbar_wait(seg_free0 + 8 * seg, (tiles_done & 1) ^ 1, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
                     const uint32_t d_tmem = tmem + seg * kBN;
                     for (int kt = 0; kt < ktiles; ++kt, ++it) {
                         const int s = it % kStages;
@@ -353,8 +364,8 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                         // frees the stage in both CTAs when these MMAs finish
                         umma_commit_mc(empty0 + 8 * s, cluster_mask);
                     }
+                    if (ok) umma_commit(seg_full0 + 8 * seg);
                 }
-                if (ok) umma_commit(acc_full);
             }
             if (!ok) {
                 a.status[0] = 2;
@@ -366,19 +377,18 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             if (!mbar_wait(drain, 0, nullptr)) a.status[0] = 3;
         }
     } else {
-        // epilogue warps 2..9: TMEM lane quarter = warp % 4, column half by warp
+        // epilogue warps 2..9: TMEM lane quarter = warp % 4, column half by
+        // warp.  The first segmentation's distances are taken into registers
+        // as soon as its MMAs finish (the second's run meanwhile), which frees
+        // its columns for the next tile; the second's are combined and stored
+        // while the next tile's first segmentation is being accumulated.
         const int quarter = warp & 3;
         const int c_begin = ((warp - 2) / 4) * (kBN / 2);
         const int row = quarter * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + c_begin;
         uint32_t tiles_done = 0;
         for (int pair = pair0; pair < npairs; pair += npairs_grid, ++tiles_done) {
             const int tile = pair * kCluster + rank;
-            if (!mbar_wait(acc_full, tiles_done & 1, abort_flag)) {
-                a.status[0] = 4;
-                *abort_flag = 1;
-                break;
-            }
-            tc_fence_after();
             const int64_t e = (int64_t)tile * kBM + row;
             const bool valid = e < a.n;
             float en0 = 0.f, en1 = 0.f, es0 = 1.f, es1 = 1.f;
@@ -390,33 +400,56 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                     es1 = a.escale[2 * e + 1];
                 }
             }
-            for (int c = c_begin; c < c_begin + kBN / 2; c += 32) {
-                uint32_t r0[32], r1[32];
-                const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + c;
-                tmem_ld32(taddr, r0);
-                tmem_ld32(taddr + kBN, r1);
+            if (!mbar_wait(seg_full0, tiles_done & 1, abort_flag)) {
+                a.status[0] = 4;
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+            float d0[kBN / 2];
+#pragma unroll
+            for (int cc = 0; cc < kBN / 64; ++cc) {
+                uint32_t r[32];
+                tmem_ld32(lane_base + 32 * cc, r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const int q = c_begin + 32 * cc + j;
+                    float dot = __uint_as_float(r[j]);
+                    if (kFp8) dot = dot * (qscale[q] * es0);
+                    d0[32 * cc + j] = sqrt_approx(fmaxf(qnorm[q] + en0 - 2.0f * dot, 0.0f));
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(seg_free0);
+            if (!mbar_wait(seg_full0 + 8, tiles_done & 1, abort_flag)) {
+                a.status[0] = 4;
+                *abort_flag = 1;
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int cc = 0; cc < kBN / 64; ++cc) {
+                uint32_t r[32];
+                tmem_ld32(lane_base + kBN + 32 * cc, r);
                 tmem_wait_ld();
                 if (valid) {
+                    const int c = c_begin + 32 * cc;
                     float* out = a.dist + (int64_t)c * a.n + e;
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         const int q = c + j;
                         if (q < a.nq) {
-                            float dot0 = __uint_as_float(r0[j]);
-                            float dot1 = __uint_as_float(r1[j]);
-                            if (kFp8) {
-                                dot0 = dot0 * (qscale[q] * es0);
-                                dot1 = dot1 * (qscale[kBN + q] * es1);
-                            }
-                            const float s0 = fmaxf(qnorm[q] + en0 - 2.0f * dot0, 0.0f);
-                            const float s1 = fmaxf(qnorm[kBN + q] + en1 - 2.0f * dot1, 0.0f);
-                            out[(int64_t)j * a.n] = sqrt_approx(s0) + sqrt_approx(s1);
+                            float dot = __uint_as_float(r[j]);
+                            if (kFp8) dot = dot * (qscale[kBN + q] * es1);
+                            const float s1 = fmaxf(qnorm[kBN + q] + en1 - 2.0f * dot, 0.0f);
+                            out[(int64_t)j * a.n] = d0[32 * cc + j] + sqrt_approx(s1);
                         }
                     }
                 }
             }
             tc_fence_before();
-            mbar_arrive(acc_empty);
+            mbar_arrive(seg_free0 + 8);
         }
     }
 
@@ -478,7 +511,7 @@ bool make_map(CUtensorMap* m, const void* base, bool fp8, int64_t rows, int64_t 
 
 size_t gemm_smem_bytes()
 {
-    return 1024 + (size_t)kStages * kStageBytes + (2 * kStages + 3) * 8 + 16 + 4 * kBN * 4;
+    return 1024 + (size_t)kStages * kStageBytes + (2 * kStages + 5) * 8 + 16 + 4 * kBN * 4;
 }
 
 int gemm_max_queries() { return kBN; }
