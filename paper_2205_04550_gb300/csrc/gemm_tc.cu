@@ -23,8 +23,8 @@
 //     instruction): columns [0, 256) accumulate q_1 . e_1, [256, 512)
 //     q_2 . e_2; tcgen05.commit frees each stage and, per segmentation,
 //     tells the epilogue that its columns are complete;
-//   * warps 2-9 read the accumulators with tcgen05.ld (a warp may only touch
-//     its 32-lane quarter, warp % 4; two warps share a quarter and take 128
+//   * warps 2-17 read the accumulators with tcgen05.ld (a warp may only touch
+//     its 32-lane quarter, warp % 4; four warps share a quarter and take 64
 //     query columns each), form L in binary32 and store L[q][e] coalesced.
 //     Each segmentation's columns are handed back as soon as they are read,
 //     so the epilogue of one tile runs under the MMAs of the next.  The square
@@ -49,8 +49,9 @@ constexpr int kStages = 4;
 constexpr int kTileABytes = kBM * 128;   // 128 rows x 128 bytes (one swizzle atom wide)
 constexpr int kTileBBytes = kBN * 128;
 constexpr int kStageBytes = kTileABytes + kTileBBytes;
-constexpr int kEpiWarps = 8;             // two per TMEM lane quarter, 128 columns each
-constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, warps 2-9 epilogue
+constexpr int kEpiWarps = 16;            // four per TMEM lane quarter, 64 columns each
+constexpr int kEpiCols = kBN / (kEpiWarps / 4);
+constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, warps 2-17 epilogue
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
 constexpr int kCluster = 2;                               // CTAs sharing the query tiles
 constexpr int kHalfBBytes = kTileBBytes / kCluster;
@@ -193,26 +194,22 @@ __device__ __forceinline__ void umma_commit(uint32_t bar)
         : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-        "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-        "%28, %29, %30, %31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-}
-
 __device__ __forceinline__ float sqrt_approx(float x)
 {
     float y;
     asm("sqrt.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
     return y;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+        "%11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+          "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
 }
 
 __device__ __forceinline__ void tmem_wait_ld()
@@ -377,13 +374,13 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             if (!mbar_wait(drain, 0, nullptr)) a.status[0] = 3;
         }
     } else {
-        // epilogue warps 2..9: TMEM lane quarter = warp % 4, column half by
+        // epilogue warps 2..17: TMEM lane quarter = warp % 4, column half by
         // warp.  The first segmentation's distances are taken into registers
         // as soon as its MMAs finish (the second's run meanwhile), which frees
         // its columns for the next tile; the second's are combined and stored
         // while the next tile's first segmentation is being accumulated.
         const int quarter = warp & 3;
-        const int c_begin = ((warp - 2) / 4) * (kBN / 2);
+        const int c_begin = ((warp - 2) / 4) * kEpiCols;
         const int row = quarter * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + c_begin;
         uint32_t tiles_done = 0;
@@ -406,18 +403,18 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                 break;
             }
             tc_fence_after();
-            float d0[kBN / 2];
+            float d0[kEpiCols];
 #pragma unroll
-            for (int cc = 0; cc < kBN / 64; ++cc) {
-                uint32_t r[32];
-                tmem_ld32(lane_base + 32 * cc, r);
+            for (int cc = 0; cc < kEpiCols / 16; ++cc) {
+                uint32_t r[16];
+                tmem_ld16(lane_base + 16 * cc, r);
                 tmem_wait_ld();
 #pragma unroll
-                for (int j = 0; j < 32; ++j) {
-                    const int q = c_begin + 32 * cc + j;
+                for (int j = 0; j < 16; ++j) {
+                    const int q = c_begin + 16 * cc + j;
                     float dot = __uint_as_float(r[j]);
                     if (kFp8) dot = dot * (qscale[q] * es0);
-                    d0[32 * cc + j] = sqrt_approx(fmaxf(qnorm[q] + en0 - 2.0f * dot, 0.0f));
+                    d0[16 * cc + j] = sqrt_approx(fmaxf(qnorm[q] + en0 - 2.0f * dot, 0.0f));
                 }
             }
             tc_fence_before();
@@ -429,21 +426,21 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             }
             tc_fence_after();
 #pragma unroll
-            for (int cc = 0; cc < kBN / 64; ++cc) {
-                uint32_t r[32];
-                tmem_ld32(lane_base + kBN + 32 * cc, r);
+            for (int cc = 0; cc < kEpiCols / 16; ++cc) {
+                uint32_t r[16];
+                tmem_ld16(lane_base + kBN + 16 * cc, r);
                 tmem_wait_ld();
                 if (valid) {
-                    const int c = c_begin + 32 * cc;
+                    const int c = c_begin + 16 * cc;
                     float* out = a.dist + (int64_t)c * a.n + e;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
+                    for (int j = 0; j < 16; ++j) {
                         const int q = c + j;
                         if (q < a.nq) {
                             float dot = __uint_as_float(r[j]);
                             if (kFp8) dot = dot * (qscale[kBN + q] * es1);
                             const float s1 = fmaxf(qnorm[kBN + q] + en1 - 2.0f * dot, 0.0f);
-                            out[(int64_t)j * a.n] = d0[32 * cc + j] + sqrt_approx(s1);
+                            out[(int64_t)j * a.n] = d0[16 * cc + j] + sqrt_approx(s1);
                         }
                     }
                 }
