@@ -481,8 +481,11 @@ def run_embed(args, wl, torch):
         "gemm": ({"tflops": gemm_flops / (stages["distances"] / 1000.0) / 1e12, "peak": gemm_peak,
                   "peak_kind": bf16_kind, "flops_per_launch": gemm_flops}
                  if mode != DBQ_MODE_HASH else None),
-        "hamming": ({"ms": stages["distances"], "code_bytes": wl["n"] * 2 * dims // 8,
-                     "pairs_per_s": nq * wl["n"] / (stages["distances"] / 1000.0)}
+        "hamming": ({"ms": stages["distances"], "code_bytes": wl["n"] * 2 * dims,
+                     "pairs_per_s": nq * wl["n"] / (stages["distances"] / 1000.0),
+                     "tensor_tflops": gemm_flops / (stages["distances"] / 1000.0) / 1e12,
+                     "note": "sign codes as E4M3 0/1 bytes on the tensor cores (FP8 GEMM), "
+                             "|q|+|e|-2q.e exact"}
                     if mode == DBQ_MODE_HASH else None),
         "rerank": {"gbs": rr_bytes / (stages["rerank"] / 1000.0) / 1e9,
                    "bytes_per_launch": rr_bytes},

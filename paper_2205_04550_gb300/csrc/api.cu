@@ -122,6 +122,8 @@ struct dbq_db {
     float* emb_nf = nullptr;        // [n][2] squared norms, fp8 rows
     bool sketch = false;            // DBQ_FLAG_SKETCH: count sketches instead of block means
     uint32_t* codes = nullptr;      // [n][2][dims/32] sign codes (DBQ_FLAG_SKETCH)
+    uint8_t* codes8 = nullptr;      // [n][2][dims] the same codes as E4M3 0/1 bytes
+    float* code_norm = nullptr;     // [n][2] their popcounts
     // batch workspace (allocated on first use)
     int bq = 0;                     // capacity in queries
     int bk = 0;                     // capacity in hits per query
@@ -136,6 +138,8 @@ struct dbq_db {
     float* bq_nb = nullptr;
     float* bq_nf = nullptr;
     uint32_t* bq_codes = nullptr;   // [bq][2][dims/32]
+    uint8_t* bq_codes8 = nullptr;   // [bq][2][dims]
+    float* bq_code_norm = nullptr;  // [bq][2]
     float* bdist = nullptr;         // [bq][n]
     int32_t* bcand = nullptr;       // [bq][1024]
     dbq::Cand* brr = nullptr;       // [bq][slices][bk]
@@ -182,7 +186,11 @@ struct dbq_db {
         cudaFree(emb_nb);
         cudaFree(emb_nf);
         cudaFree(codes);
+        cudaFree(codes8);
+        cudaFree(code_norm);
         cudaFree(bq_codes);
+        cudaFree(bq_codes8);
+        cudaFree(bq_code_norm);
         cudaFree(bstage);
         cudaFree(bptrs);
         cudaFree(bplanes);
@@ -405,6 +413,10 @@ int ensure_batch(dbq_db* db, int k)
             if (!rc) rc = grow(db, &db->bq_nf, rows * 4, "query fp8 norms");
             if (!rc && db->sketch)
                 rc = grow(db, &db->bq_codes, rows * (db->dims / 32) * 4, "query sign codes");
+            if (!rc && db->sketch)
+                rc = grow(db, &db->bq_codes8, rows * db->dims, "query code bytes");
+            if (!rc && db->sketch)
+                rc = grow(db, &db->bq_code_norm, rows * 4, "query code popcounts");
             if (!rc) rc = grow(db, &db->bdist, q * (size_t)db->n * 4, "prefilter distances");
             if (!rc) rc = grow(db, &db->bcand, q * 1024 * 4, "prefilter candidates");
             if (!rc) rc = grow(db, &db->brr, q * kRerankSlices * kMaxK * sizeof(dbq::Cand),
@@ -504,31 +516,31 @@ int run_prefilter(dbq_db* db, int nq, int mode, int c, cudaStream_t s)
     cudaError_t err =
         db->sketch
             ? dbq::launch_sketch(db->bplanes, nq, db->wp, db->words, db->bq_bf16, db->bq_f8,
-                                 db->bq_scale, db->bq_nb, db->bq_nf, db->bq_codes, s)
+                                 db->bq_scale, db->bq_nb, db->bq_nf, db->bq_codes, db->bq_codes8,
+                                 db->bq_code_norm, s)
             : dbq::launch_embed(db->bplanes, nq, db->wp, db->nx, db->ny, db->nz, db->bq_bf16,
                                 db->bq_f8, db->bq_scale, db->bq_nb, db->bq_nf, s);
     if (err != cudaSuccess) return cuda_fail(err, "query embedding launch");
     mark(db, 2, s);
-    if (mode == DBQ_MODE_HASH) {
-        err = dbq::launch_hamming(db->codes, db->n, db->bq_codes, nq, db->bdist, s);
-        if (err != cudaSuccess) return cuda_fail(err, "Hamming distance launch");
-    } else {
+    {
+        const bool ham = mode == DBQ_MODE_HASH;
         const int fp8 = mode == DBQ_MODE_EMBED_FP8;
         dbq::GemmArgs g;
         g.e_bf16 = db->emb_bf16;
-        g.e_f8 = db->emb_f8;
-        g.enorm = fp8 ? db->emb_nf : db->emb_nb;
+        g.e_f8 = ham ? db->codes8 : db->emb_f8;
+        g.enorm = ham ? db->code_norm : (fp8 ? db->emb_nf : db->emb_nb);
         g.escale = db->emb_scale;
         g.q_bf16 = db->bq_bf16;
-        g.q_f8 = db->bq_f8;
-        g.qnorm = fp8 ? db->bq_nf : db->bq_nb;
+        g.q_f8 = ham ? db->bq_codes8 : db->bq_f8;
+        g.qnorm = ham ? db->bq_code_norm : (fp8 ? db->bq_nf : db->bq_nb);
         g.qscale = db->bq_scale;
         g.n = db->n;
         g.nq = nq;
         g.dims = db->dims;
         g.dist = db->bdist;
         g.status = db->bstatus;
-        err = dbq::launch_prefilter_gemm(g, fp8, db->grid, s);
+        const int kind = ham ? dbq::kGemmHamming : (fp8 ? dbq::kGemmFp8 : dbq::kGemmBf16);
+        err = dbq::launch_prefilter_gemm(g, kind, db->grid, s);
         if (err != cudaSuccess) return cuda_fail(err, "prefilter GEMM launch");
     }
     mark(db, 3, s);
@@ -764,6 +776,8 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
         if (!rc) rc = dev_alloc(db, &db->emb_nf, rows * 4, "fp8 norms");
         if (!rc && db->sketch)
             rc = dev_alloc(db, &db->codes, rows * (db->dims / 32) * 4, "sign codes");
+        if (!rc && db->sketch) rc = dev_alloc(db, &db->codes8, rows * db->dims, "code bytes");
+        if (!rc && db->sketch) rc = dev_alloc(db, &db->code_norm, rows * 4, "code popcounts");
     }
     db->grid = dbq::scan_packed_grid(dev);
     dbq::scan_packed_chunking(db->wp4, &db->chunk4, &db->nchunks);
@@ -893,7 +907,7 @@ int db_build_masks(dbq_db* db, void* stream)
     } else if (db->flags & DBQ_FLAG_SKETCH) {
         cudaError_t err = dbq::launch_sketch(db->planes, db->n, db->wp, db->words, db->emb_bf16,
                                              db->emb_f8, db->emb_scale, db->emb_nb, db->emb_nf,
-                                             db->codes, s);
+                                             db->codes, db->codes8, db->code_norm, s);
         if (err != cudaSuccess) return cuda_fail(err, "sketch launch");
     }
     DBQ_CUDA(cudaStreamSynchronize(s));

@@ -6,7 +6,10 @@
 // following the paper's L2_T1Gd + L2_FLAIR combination (Section 2.3).  The
 // dot products are a dense contraction (Q queries x N entries x D dims per
 // segmentation), so they run as a tcgen05 GEMM with fp32 accumulation in
-// tensor memory:
+// tensor memory.  The same kernel gives the Hamming distance of binary codes
+// stored as E4M3 0/1 bytes: with the popcounts as norms, |q| + |e| - 2 q.e
+// summed over the two segmentations is exact (integer products and sums
+// below 2^24 in binary32), so no square root is taken.
 //
 //   * one CTA per SM, clusters of two CTAs on neighbouring SMs, persistent
 //     over pairs of 128-entry tiles (CTA rank r of the pair takes tile
@@ -232,7 +235,7 @@ __host__ __device__ constexpr uint32_t instr_desc()
            | ((uint32_t)(kBM >> 4) << 24);             // M / 16
 }
 
-template <bool kFp8>
+template <bool kFp8, bool kHam>
 __global__ void __cluster_dims__(kCluster, 1, 1) __launch_bounds__(kThreads, 1)
 prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                       const __grid_constant__ CUtensorMap tm_q, GemmArgs a)
@@ -282,7 +285,7 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
     for (int i = threadIdx.x; i < 2 * kBN; i += blockDim.x) {
         const int q = i % kBN, k = i / kBN;
         qnorm[i] = q < a.nq ? a.qnorm[2 * q + k] : 0.0f;
-        qscale[i] = (kFp8 && q < a.nq) ? a.qscale[2 * q + k] : 1.0f;
+        qscale[i] = (kFp8 && !kHam && q < a.nq) ? a.qscale[2 * q + k] : 1.0f;
     }
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
@@ -392,7 +395,7 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             if (valid) {
                 en0 = a.enorm[2 * e];
                 en1 = a.enorm[2 * e + 1];
-                if (kFp8) {
+                if (kFp8 && !kHam) {
                     es0 = a.escale[2 * e];
                     es1 = a.escale[2 * e + 1];
                 }
@@ -413,6 +416,11 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                 for (int j = 0; j < 16; ++j) {
                     const int q = c_begin + 16 * cc + j;
                     float dot = __uint_as_float(r[j]);
+                    if (kHam) {
+                        // 0/1 codes: |q| + |e| - 2 q.e, exact in binary32
+                        d0[16 * cc + j] = qnorm[q] + en0 - 2.0f * dot;
+                        continue;
+                    }
                     if (kFp8) dot = dot * (qscale[q] * es0);
                     d0[16 * cc + j] = sqrt_approx(fmaxf(qnorm[q] + en0 - 2.0f * dot, 0.0f));
                 }
@@ -438,6 +446,11 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                         const int q = c + j;
                         if (q < a.nq) {
                             float dot = __uint_as_float(r[j]);
+                            if (kHam) {
+                                out[(int64_t)j * a.n] =
+                                    d0[16 * cc + j] + (qnorm[kBN + q] + en1 - 2.0f * dot);
+                                continue;
+                            }
                             if (kFp8) dot = dot * (qscale[kBN + q] * es1);
                             const float s1 = fmaxf(qnorm[kBN + q] + en1 - 2.0f * dot, 0.0f);
                             out[(int64_t)j * a.n] = d0[16 * cc + j] + sqrt_approx(s1);
@@ -513,8 +526,21 @@ size_t gemm_smem_bytes()
 
 int gemm_max_queries() { return kBN; }
 
-cudaError_t launch_prefilter_gemm(const GemmArgs& a, int fp8, int grid, cudaStream_t stream)
+template <bool kFp8, bool kHam>
+cudaError_t launch_kind(const CUtensorMap& tm_e, const CUtensorMap& tm_q, const GemmArgs& a,
+                        int grid, size_t smem, cudaStream_t stream)
 {
+    cudaError_t err = cudaFuncSetAttribute(prefilter_gemm_kernel<kFp8, kHam>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    prefilter_gemm_kernel<kFp8, kHam><<<grid, kThreads, smem, stream>>>(tm_e, tm_q, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prefilter_gemm(const GemmArgs& a, int kind, int grid, cudaStream_t stream)
+{
+    const bool fp8 = kind != kGemmBf16;
+    if (kind < kGemmBf16 || kind > kGemmHamming) return cudaErrorInvalidValue;
     if (a.nq < 1 || a.nq > kBN || a.n < 1 || a.dims % (fp8 ? 128 : 64) != 0)
         return cudaErrorInvalidValue;
     CUtensorMap tm_e, tm_q;
@@ -530,19 +556,9 @@ cudaError_t launch_prefilter_gemm(const GemmArgs& a, int fp8, int grid, cudaStre
     if (grid > npairs) grid = npairs;
     if (grid < 1) grid = 1;
     grid *= kCluster;
-    cudaError_t err;
-    if (fp8) {
-        err = cudaFuncSetAttribute(prefilter_gemm_kernel<true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        prefilter_gemm_kernel<true><<<grid, kThreads, smem, stream>>>(tm_e, tm_q, a);
-    } else {
-        err = cudaFuncSetAttribute(prefilter_gemm_kernel<false>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (err != cudaSuccess) return err;
-        prefilter_gemm_kernel<false><<<grid, kThreads, smem, stream>>>(tm_e, tm_q, a);
-    }
-    return cudaGetLastError();
+    if (kind == kGemmHamming) return launch_kind<true, true>(tm_e, tm_q, a, grid, smem, stream);
+    if (kind == kGemmFp8) return launch_kind<true, false>(tm_e, tm_q, a, grid, smem, stream);
+    return launch_kind<false, false>(tm_e, tm_q, a, grid, smem, stream);
 }
 
 }  // namespace dbq

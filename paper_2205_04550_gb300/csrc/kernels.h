@@ -106,12 +106,14 @@ cudaError_t launch_embed(const uint32_t* planes, int64_t count, int64_t wp, int 
 
 // Count-sketch embeddings (sketch.cu): D = sketch_dims() buckets per
 // segmentation, the same encodings as launch_embed, plus the sign code
-// [count][2][D/32] (bit j of a row = bucket j > 0).  Any grid; `words`
-// meaningful words of each wp-word plane.
+// [count][2][D/32] (bit j of a row = bucket j > 0), the same code as E4M3
+// 0/1 bytes [count][2][D] and its popcount per row [count][2] (binary32).
+// Any grid; `words` meaningful words of each wp-word plane.
 int sketch_dims();
 cudaError_t launch_sketch(const uint32_t* planes, int64_t count, int64_t wp, int64_t words,
                           uint16_t* out_bf16, uint8_t* out_f8, float* out_scale, float* out_nb,
-                          float* out_nf, uint32_t* out_code, cudaStream_t stream);
+                          float* out_nf, uint32_t* out_code, uint8_t* out_code8, float* out_cnorm,
+                          cudaStream_t stream);
 // Reaction-diffusion forward model (rd.cu).
 struct RdSim {
     float a;        // dt * D_w
@@ -139,11 +141,6 @@ cudaError_t launch_rd_faces(const float* m, int nx, int ny, int nz, float* hx, f
 // step (its local step launch - start).
 cudaError_t launch_rd_step(const RdStepArgs& g, int slots, int launch, cudaStream_t stream);
 
-// Hamming distances of sign codes (2 * D/32 words per entry and per query):
-// dist [nq][n] binary32 (exact integers).
-cudaError_t launch_hamming(const uint32_t* codes, int64_t n, const uint32_t* qcodes, int nq,
-                           float* dist, cudaStream_t stream);
-
 struct GemmArgs {
     const uint16_t* e_bf16;   // [n][2*dims] entry embeddings (bf16 bits)
     const uint8_t* e_f8;      // [n][2*dims] entry embeddings (e4m3 codes)
@@ -161,7 +158,11 @@ struct GemmArgs {
 };
 size_t gemm_smem_bytes();
 int gemm_max_queries();
-cudaError_t launch_prefilter_gemm(const GemmArgs& a, int fp8, int grid, cudaStream_t stream);
+// kind: kGemmBf16 / kGemmFp8 -- L = d_1 + d_2 of the L2 distances of the
+// encoded embeddings; kGemmHamming -- E4M3 0/1 codes with their popcounts as
+// norms, dist = sum over both segmentations of |q| + |e| - 2 q.e (exact).
+enum GemmKind { kGemmBf16 = 0, kGemmFp8 = 1, kGemmHamming = 2 };
+cudaError_t launch_prefilter_gemm(const GemmArgs& a, int kind, int grid, cudaStream_t stream);
 
 // The c smallest distances per query (ties to the lower index), ascending:
 // dist [nq][n] -> cand [nq][c] entry indices.  c <= 1024, c <= n.

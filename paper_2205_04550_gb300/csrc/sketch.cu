@@ -8,6 +8,10 @@
 // unbiased estimate of their symmetric difference, and the sign code
 // [v_j > 0] of the sketch (a sign random projection) compared by Hamming
 // distance -- the popcount counterpart of the paper's hashing baseline.
+// For the Hamming prefilter the code is also written as FP8 E4M3 bytes
+// (1.0 for a set bit, 0 otherwise) with its popcount: for 0/1 vectors
+// Hamming(a, b) = |a| + |b| - 2 a.b, a dense contraction that runs exactly on
+// the tensor cores (products 0 or 1, sums of at most 4096 in binary32).
 //
 // Voxel x goes to bucket (h >> 32) mod D with sign (bit 31 of h ? -1 : +1),
 // h = SplitMix64 output for counter x (Steele, Lea & Flood 2014).  The
@@ -58,7 +62,8 @@ __global__ void __launch_bounds__(kSketchThreads)
 sketch_kernel(const uint32_t* __restrict__ planes, int64_t wp, int64_t words,
               uint16_t* __restrict__ out_bf16, uint8_t* __restrict__ out_f8,
               float* __restrict__ out_scale, float* __restrict__ out_nb, float* __restrict__ out_nf,
-              uint32_t* __restrict__ out_code)
+              uint32_t* __restrict__ out_code, uint8_t* __restrict__ out_code8,
+              float* __restrict__ out_cnorm)
 {
     __shared__ int sk[kSketchD];
     __shared__ float red[kSketchThreads / 32];
@@ -76,8 +81,9 @@ sketch_kernel(const uint32_t* __restrict__ planes, int64_t wp, int64_t words,
         }
     }
     __syncthreads();
-    float m = 0.0f, nb = 0.0f;
+    float m = 0.0f, nb = 0.0f, ones = 0.0f;
     uint16_t* ob = out_bf16 + row * kSketchD;
+    uint8_t* oc8 = out_code8 + row * kSketchD;
     for (int j = threadIdx.x; j < kSketchD; j += blockDim.x) {
         const float v = (float)sk[j];
         m = fmaxf(m, fabsf(v));
@@ -85,12 +91,16 @@ sketch_kernel(const uint32_t* __restrict__ planes, int64_t wp, int64_t words,
         ob[j] = __bfloat16_as_ushort(hb);
         const float hv = __bfloat162float(hb);
         nb = __fmaf_rn(hv, hv, nb);
-        // sign code: one ballot per 32 consecutive buckets
-        const uint32_t bits = __ballot_sync(0xffffffffu, sk[j] > 0);
+        // sign code: one ballot per 32 consecutive buckets, and as e4m3 0/1
+        const bool pos = sk[j] > 0;
+        const uint32_t bits = __ballot_sync(0xffffffffu, pos);
         if ((threadIdx.x & 31) == 0) out_code[row * (kSketchD / 32) + j / 32] = bits;
+        oc8[j] = pos ? (uint8_t)0x38 : (uint8_t)0;     // 0x38 = 1.0 in E4M3
+        ones += pos ? 1.0f : 0.0f;
     }
     const float mx = block_reduce(m, red, true);
     const float nbs = block_reduce(nb, red, false);
+    const float pop = block_reduce(ones, red, false);     // exact: an integer <= 4096
     const float s = (mx == 0.0f) ? 1.0f : __fdiv_rn(mx, 448.0f);
     float nq = 0.0f;
     uint8_t* oq = out_f8 + row * kSketchD;
@@ -107,53 +117,7 @@ sketch_kernel(const uint32_t* __restrict__ planes, int64_t wp, int64_t words,
         out_scale[row] = s;
         out_nb[row] = nbs;
         out_nf[row] = nqs * s * s;
-    }
-}
-
-// Hamming distances of sign codes: dist[q][e] = popc(code_q ^ code_e) over
-// both planes.  A CTA (8 warps) owns 128 consecutive entries; a warp holds
-// an entry's 2 x 128 code words in registers (8 per lane) and runs through
-// the queries of a 32-query chunk held in shared memory; results go through
-// a shared tile so each query's row is written 128 entries at a time.
-constexpr int kHamThreads = 256;
-constexpr int kHamEntries = 128;
-constexpr int kHamQueries = 32;
-constexpr int kCodeWords = 2 * kSketchD / 32;   // 256 words per entry (both planes)
-
-__global__ void __launch_bounds__(kHamThreads)
-hamming_kernel(const uint32_t* __restrict__ codes, int64_t n, const uint32_t* __restrict__ qcodes,
-               int nq, float* __restrict__ dist)
-{
-    __shared__ uint32_t qs[kHamQueries * kCodeWords];          // 32 KiB
-    __shared__ uint16_t tile[kHamQueries][kHamEntries + 2];   // distances <= 8192
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t e0 = (int64_t)blockIdx.x * kHamEntries;
-    for (int q0 = 0; q0 < nq; q0 += kHamQueries) {
-        const int qn = (nq - q0) < kHamQueries ? (nq - q0) : kHamQueries;
-        __syncthreads();
-        for (int i = threadIdx.x; i < qn * kCodeWords; i += kHamThreads)
-            qs[i] = qcodes[(int64_t)q0 * kCodeWords + i];
-        __syncthreads();
-        for (int le = warp; le < kHamEntries; le += kHamThreads / 32) {
-            const int64_t e = e0 + le;
-            uint32_t c[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) c[u] = e < n ? __ldg(codes + e * kCodeWords + lane + 32 * u) : 0u;
-            for (int q = 0; q < qn; ++q) {
-                const uint32_t* qc = qs + q * kCodeWords;
-                uint32_t h = 0;
-#pragma unroll
-                for (int u = 0; u < 8; ++u) h += __popc(c[u] ^ qc[lane + 32 * u]);
-                h = __reduce_add_sync(0xffffffffu, h);
-                if (lane == 0) tile[q][le] = (uint16_t)h;
-            }
-        }
-        __syncthreads();
-        for (int i = threadIdx.x; i < qn * kHamEntries; i += kHamThreads) {
-            const int q = i / kHamEntries, le = i % kHamEntries;
-            const int64_t e = e0 + le;
-            if (e < n) dist[(int64_t)(q0 + q) * n + e] = (float)tile[q][le];
-        }
+        out_cnorm[row] = pop;
     }
 }
 
@@ -163,27 +127,20 @@ int sketch_dims() { return kSketchD; }
 
 cudaError_t launch_sketch(const uint32_t* planes, int64_t count, int64_t wp, int64_t words,
                           uint16_t* out_bf16, uint8_t* out_f8, float* out_scale, float* out_nb,
-                          float* out_nf, uint32_t* out_code, cudaStream_t stream)
+                          float* out_nf, uint32_t* out_code, uint8_t* out_code8, float* out_cnorm,
+                          cudaStream_t stream)
 {
     for (int64_t e0 = 0; e0 < count; e0 += 65535) {
         const int64_t ce = (count - e0) < 65535 ? (count - e0) : 65535;
         sketch_kernel<<<dim3(2, (unsigned)ce), kSketchThreads, 0, stream>>>(
             planes + e0 * 2 * wp, wp, words, out_bf16 + e0 * 2 * kSketchD,
             out_f8 + e0 * 2 * kSketchD, out_scale + e0 * 2, out_nb + e0 * 2, out_nf + e0 * 2,
-            out_code + e0 * 2 * (kSketchD / 32));
+            out_code + e0 * 2 * (kSketchD / 32), out_code8 + e0 * 2 * kSketchD,
+            out_cnorm + e0 * 2);
         const cudaError_t err = cudaGetLastError();
         if (err != cudaSuccess) return err;
     }
     return cudaSuccess;
-}
-
-cudaError_t launch_hamming(const uint32_t* codes, int64_t n, const uint32_t* qcodes, int nq,
-                           float* dist, cudaStream_t stream)
-{
-    if (n <= 0 || nq <= 0) return cudaSuccess;
-    const int64_t blocks = (n + kHamEntries - 1) / kHamEntries;
-    hamming_kernel<<<(unsigned)blocks, kHamThreads, 0, stream>>>(codes, n, qcodes, nq, dist);
-    return cudaGetLastError();
 }
 
 }  // namespace dbq
