@@ -124,6 +124,7 @@ struct dbq_db {
     uint32_t* codes = nullptr;      // [n][2][dims/32] sign codes (DBQ_FLAG_SKETCH)
     uint8_t* codes8 = nullptr;      // [n][2][dims] the same codes as E4M3 0/1 bytes
     float* code_norm = nullptr;     // [n][2] their popcounts
+    uint16_t* sk_table = nullptr;   // [V] sketch bucket | sign << 15 of every voxel
     // batch workspace (allocated on first use)
     int bq = 0;                     // capacity in queries
     int bk = 0;                     // capacity in hits per query
@@ -188,6 +189,7 @@ struct dbq_db {
         cudaFree(codes);
         cudaFree(codes8);
         cudaFree(code_norm);
+        cudaFree(sk_table);
         cudaFree(bq_codes);
         cudaFree(bq_codes8);
         cudaFree(bq_code_norm);
@@ -515,7 +517,8 @@ int run_prefilter(dbq_db* db, int nq, int mode, int c, cudaStream_t s)
     mark(db, 1, s);
     cudaError_t err =
         db->sketch
-            ? dbq::launch_sketch(db->bplanes, nq, db->wp, db->words, db->bq_bf16, db->bq_f8,
+            ? dbq::launch_sketch(db->bplanes, nq, db->wp, db->words, db->sk_table, db->bq_bf16,
+                                 db->bq_f8,
                                  db->bq_scale, db->bq_nb, db->bq_nf, db->bq_codes, db->bq_codes8,
                                  db->bq_code_norm, s)
             : dbq::launch_embed(db->bplanes, nq, db->wp, db->nx, db->ny, db->nz, db->bq_bf16,
@@ -778,6 +781,12 @@ int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storag
             rc = dev_alloc(db, &db->codes, rows * (db->dims / 32) * 4, "sign codes");
         if (!rc && db->sketch) rc = dev_alloc(db, &db->codes8, rows * db->dims, "code bytes");
         if (!rc && db->sketch) rc = dev_alloc(db, &db->code_norm, rows * 4, "code popcounts");
+        if (!rc && db->sketch) rc = dev_alloc(db, &db->sk_table, (size_t)v * 2, "sketch table");
+        if (!rc && db->sketch) {
+            cudaError_t err = dbq::launch_sketch_table(v, db->sk_table, nullptr);
+            if (err == cudaSuccess) err = cudaDeviceSynchronize();
+            if (err != cudaSuccess) rc = cuda_fail(err, "sketch table");
+        }
     }
     db->grid = dbq::scan_packed_grid(dev);
     dbq::scan_packed_chunking(db->wp4, &db->chunk4, &db->nchunks);
@@ -905,7 +914,8 @@ int db_build_masks(dbq_db* db, void* stream)
                                             db->emb_nf, s);
         if (err != cudaSuccess) return cuda_fail(err, "embedding launch");
     } else if (db->flags & DBQ_FLAG_SKETCH) {
-        cudaError_t err = dbq::launch_sketch(db->planes, db->n, db->wp, db->words, db->emb_bf16,
+        cudaError_t err = dbq::launch_sketch(db->planes, db->n, db->wp, db->words, db->sk_table,
+                                             db->emb_bf16,
                                              db->emb_f8, db->emb_scale, db->emb_nb, db->emb_nf,
                                              db->codes, db->codes8, db->code_norm, s);
         if (err != cudaSuccess) return cuda_fail(err, "sketch launch");

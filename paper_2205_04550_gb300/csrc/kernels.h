@@ -110,8 +110,10 @@ cudaError_t launch_embed(const uint32_t* planes, int64_t count, int64_t wp, int 
 // 0/1 bytes [count][2][D] and its popcount per row [count][2] (binary32).
 // Any grid; `words` meaningful words of each wp-word plane.
 int sketch_dims();
+// table [V]: bucket | sign << 15 of every voxel index (built once per grid).
+cudaError_t launch_sketch_table(int64_t v, uint16_t* table, cudaStream_t stream);
 cudaError_t launch_sketch(const uint32_t* planes, int64_t count, int64_t wp, int64_t words,
-                          uint16_t* out_bf16, uint8_t* out_f8, float* out_scale, float* out_nb,
+                          const uint16_t* table, uint16_t* out_bf16, uint8_t* out_f8, float* out_scale, float* out_nb,
                           float* out_nf, uint32_t* out_code, uint8_t* out_code8, float* out_cnorm,
                           cudaStream_t stream);
 // Reaction-diffusion forward model (rd.cu).

@@ -14,7 +14,8 @@
 // the tensor cores (products 0 or 1, sums of at most 4096 in binary32).
 //
 // Voxel x goes to bucket (h >> 32) mod D with sign (bit 31 of h ? -1 : +1),
-// h = SplitMix64 output for counter x (Steele, Lea & Flood 2014).  The
+// h = SplitMix64 output for counter x (Steele, Lea & Flood 2014); the
+// bucket and sign of each voxel index come from a table built once.  The
 // sketch is encoded like the block-mean embedding: bfloat16 (nearest-even),
 // FP8 E4M3 of v / s with s = max|v| / 448 per row, squared norms of the
 // decoded rows; the sign code packs 32 buckets per word.
@@ -58,8 +59,21 @@ __device__ __forceinline__ float block_reduce(float v, float* red, bool is_max)
     return red[0];
 }
 
+// The bucket and sign of every voxel depend on its index only: one table of
+// V entries, bucket | sign << 15, built once per grid and read (L2-resident)
+// for every set voxel of every mask.
+__global__ void sketch_table_kernel(int64_t v, uint16_t* __restrict__ table)
+{
+    for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < v;
+         x += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t h = splitmix64_out((uint64_t)x);
+        table[x] = (uint16_t)(((h >> 32) & (kSketchD - 1)) | (((h >> 31) & 1u) << 15));
+    }
+}
+
 __global__ void __launch_bounds__(kSketchThreads)
 sketch_kernel(const uint32_t* __restrict__ planes, int64_t wp, int64_t words,
+              const uint16_t* __restrict__ table,
               uint16_t* __restrict__ out_bf16, uint8_t* __restrict__ out_f8,
               float* __restrict__ out_scale, float* __restrict__ out_nb, float* __restrict__ out_nf,
               uint32_t* __restrict__ out_code, uint8_t* __restrict__ out_code8,
@@ -67,17 +81,43 @@ sketch_kernel(const uint32_t* __restrict__ planes, int64_t wp, int64_t words,
 {
     __shared__ int sk[kSketchD];
     __shared__ float red[kSketchThreads / 32];
+    __shared__ unsigned long long next_chunk;
     const int64_t row = blockIdx.y * 2 + blockIdx.x;      // (entry, plane)
     const uint32_t* plane = planes + row * wp;
     for (int j = threadIdx.x; j < kSketchD; j += blockDim.x) sk[j] = 0;
+    if (threadIdx.x == 0) next_chunk = 0;
     __syncthreads();
-    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) {
-        uint32_t word = __ldg(plane + w);
-        while (word) {
-            const int b = __ffs(word) - 1;
-            word &= word - 1;
-            const uint64_t h = splitmix64_out((uint64_t)(w * 32 + b));
-            atomicAdd(&sk[(int)((h >> 32) & (kSketchD - 1))], ((h >> 31) & 1u) ? -1 : 1);
+    // Warps take chunks of 32 consecutive words (a lane per word) from a
+    // shared counter: the set voxels sit in the tumour's few columns, so a
+    // static split would leave most warps waiting at the barrier.
+    constexpr int kChunks = 4;                   // chunks per grab (loads in flight)
+    const int lane = threadIdx.x & 31;
+    const int64_t nchunks = (words + 31) / 32;
+    for (;;) {
+        int64_t c0 = 0;
+        if (lane == 0) c0 = atomicAdd(&next_chunk, (unsigned long long)kChunks);
+        c0 = __shfl_sync(0xffffffffu, c0, 0);
+        if (c0 >= nchunks) break;
+        uint32_t wd[kChunks];
+#pragma unroll
+        for (int u = 0; u < kChunks; ++u) {
+            const int64_t w = (c0 + u) * 32 + lane;
+            wd[u] = (c0 + u < nchunks && w < words) ? __ldg(plane + w) : 0u;
+        }
+        // the warp takes the non-zero words one at a time, lane l testing
+        // bit l: the table reads of one word are one coalesced 64-byte access
+#pragma unroll
+        for (int u = 0; u < kChunks; ++u) {
+            uint32_t nz = __ballot_sync(0xffffffffu, wd[u] != 0u);
+            while (nz) {
+                const int j = __ffs(nz) - 1;
+                nz &= nz - 1;
+                const uint32_t word = __shfl_sync(0xffffffffu, wd[u], j);
+                if ((word >> lane) & 1u) {
+                    const uint32_t t = __ldg(table + ((c0 + u) * 32 + j) * 32 + lane);
+                    atomicAdd(&sk[t & (kSketchD - 1)], (t >> 15) ? -1 : 1);
+                }
+            }
         }
     }
     __syncthreads();
@@ -125,15 +165,23 @@ sketch_kernel(const uint32_t* __restrict__ planes, int64_t wp, int64_t words,
 
 int sketch_dims() { return kSketchD; }
 
+cudaError_t launch_sketch_table(int64_t v, uint16_t* table, cudaStream_t stream)
+{
+    if (v <= 0) return cudaSuccess;
+    const int64_t want = (v + 255) / 256;
+    sketch_table_kernel<<<(unsigned)(want < 4096 ? want : 4096), 256, 0, stream>>>(v, table);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_sketch(const uint32_t* planes, int64_t count, int64_t wp, int64_t words,
-                          uint16_t* out_bf16, uint8_t* out_f8, float* out_scale, float* out_nb,
+                          const uint16_t* table, uint16_t* out_bf16, uint8_t* out_f8, float* out_scale, float* out_nb,
                           float* out_nf, uint32_t* out_code, uint8_t* out_code8, float* out_cnorm,
                           cudaStream_t stream)
 {
     for (int64_t e0 = 0; e0 < count; e0 += 65535) {
         const int64_t ce = (count - e0) < 65535 ? (count - e0) : 65535;
         sketch_kernel<<<dim3(2, (unsigned)ce), kSketchThreads, 0, stream>>>(
-            planes + e0 * 2 * wp, wp, words, out_bf16 + e0 * 2 * kSketchD,
+            planes + e0 * 2 * wp, wp, words, table, out_bf16 + e0 * 2 * kSketchD,
             out_f8 + e0 * 2 * kSketchD, out_scale + e0 * 2, out_nb + e0 * 2, out_nf + e0 * 2,
             out_code + e0 * 2 * (kSketchD / 32), out_code8 + e0 * 2 * kSketchD,
             out_cnorm + e0 * 2);
