@@ -11,21 +11,20 @@
 // summed over the two segmentations is exact (integer products and sums
 // below 2^24 in binary32), so no square root is taken.
 //
-//   * one CTA per SM, clusters of two CTAs on neighbouring SMs, persistent
-//     over pairs of 128-entry tiles (CTA rank r of the pair takes tile
-//     2p + r; both walk the same pairs so their K-slices stay in step);
-//   * warp 0 (one thread) issues TMA loads of 128-byte-swizzled K-slices of
-//     its entry tile (128 rows) into a 4-stage shared-memory ring guarded by
-//     full/empty mbarriers; the 256 query rows, which every tile needs, are
-//     loaded once per pair: each CTA loads 128 of them and multicasts them
-//     into the same stage of both CTAs, so L2 serves a third fewer bytes.  A
-//     stage is free again only when both CTAs' MMAs have read it (each MMA
-//     commit arrives on the stage's empty barrier in both CTAs);
-//   * warp 1 owns 512 TMEM columns and one thread issues tcgen05.mma
-//     (M = 128 entries, N = 256 queries, K = 16 bf16 or 32 fp8 per
-//     instruction): columns [0, 256) accumulate q_1 . e_1, [256, 512)
-//     q_2 . e_2; tcgen05.commit frees each stage and, per segmentation,
-//     tells the epilogue that its columns are complete;
+//   * one CTA per SM, clusters of two CTAs on neighbouring SMs that run one
+//     2-SM MMA together (tcgen05 cta_group::2, M = 256 entries: 128 in each
+//     CTA's TMEM), persistent over 256-entry tiles;
+//   * warp 0 of each CTA (one thread) issues TMA loads of 128-byte-swizzled
+//     K-slices of its 128 entry rows and of half of the 256 query rows into
+//     a 6-stage shared-memory ring; both CTAs' loads complete on the leader
+//     CTA's full barrier, so each SM fills only half of the query tile (the
+//     MMA reads the other half from the peer's shared memory);
+//   * warp 1 of each CTA allocates 512 TMEM columns as a pair; one thread of
+//     the leader issues tcgen05.mma.cta_group::2 (N = 256 queries, K = 16
+//     bf16 or 32 fp8 per instruction): columns [0, 256) accumulate
+//     q_1 . e_1, [256, 512) q_2 . e_2; its commits free each stage in both
+//     CTAs and, per segmentation, tell both epilogues that the columns are
+//     complete;
 //   * warps 2-17 read the accumulators with tcgen05.ld (a warp may only touch
 //     its 32-lane quarter, warp % 4; four warps share a quarter and take 64
 //     query columns each), form L in binary32 and store L[q][e] coalesced.
@@ -33,8 +32,8 @@
 //     so the epilogue of one tile runs under the MMAs of the next.  The square
 //     roots use the SFU's sqrt.approx.f32 (relative error about 2^-23): the
 //     correctly rounded square root with its special-case path doubled the
-//     launch time;
-//     the error is far inside the tolerance of the binary32 accumulation.
+//     launch time, and the error is far inside the tolerance of the binary32
+//     accumulation.
 // Every mbarrier wait is bounded (iteration count and %globaltimer); on a
 // timeout the CTA records an error code in `status`, stops issuing work,
 // waits (bounded) for the copies and MMAs it has in flight, frees its TMEM
@@ -46,18 +45,17 @@
 namespace dbq {
 namespace {
 
-constexpr int kBM = 128;          // entries per tile (TMEM lanes)
+constexpr int kBM = 128;          // entries per CTA (TMEM lanes); 256 per CTA pair
 constexpr int kBN = 256;          // queries per launch (MMA N)
-constexpr int kStages = 4;
+constexpr int kStages = 6;
 constexpr int kTileABytes = kBM * 128;   // 128 rows x 128 bytes (one swizzle atom wide)
 constexpr int kTileBBytes = kBN * 128;
-constexpr int kStageBytes = kTileABytes + kTileBBytes;
+constexpr int kStageBytes = kTileABytes + kTileBBytes / 2;   // per CTA: its A rows, half of B
 constexpr int kEpiWarps = 16;            // four per TMEM lane quarter, 64 columns each
 constexpr int kEpiCols = kBN / (kEpiWarps / 4);
 constexpr int kThreads = 64 + 32 * kEpiWarps;   // warp 0 TMA, warp 1 MMA, warps 2-17 epilogue
 constexpr unsigned long long kWaitNs = 2000000000ull;   // 2 s per wait
-constexpr int kCluster = 2;                               // CTAs sharing the query tiles
-constexpr int kHalfBBytes = kTileBBytes / kCluster;
+constexpr int kCluster = 2;                               // the CTA pair of one MMA
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
 {
@@ -80,11 +78,6 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t byt
 {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
@@ -114,26 +107,31 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                            int x, int y)
+// TMA load into this CTA's shared memory whose completion is signalled on an
+// mbarrier of either CTA of the pair (a shared::cluster address).
+__device__ __forceinline__ void tma_load_2d_pair(uint32_t dst, const CUtensorMap* map,
+                                                 uint32_t bar_cluster, int x, int y)
 {
     asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        "cp.async.bulk.tensor.2d.cta_group::2.shared::cluster.global.mbarrier::complete_tx::bytes"
         " [%0], [%1, {%3, %4}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y)
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar_cluster), "r"(x), "r"(y)
         : "memory");
 }
 
-// TMA load whose data and completion go to the same shared-memory offsets in
-// every CTA of `mask` (this cluster's CTAs).
-__device__ __forceinline__ void tma_load_2d_mc(uint32_t dst, const CUtensorMap* map, uint32_t bar,
-                                               int x, int y, uint16_t mask)
+// The shared::cluster address of this CTA's shared variable `saddr` in CTA
+// `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank)
 {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        ".multicast::cluster [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "h"(mask)
-        : "memory");
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t bar_cluster)
+{
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(bar_cluster)
+                 : "memory");
 }
 
 __device__ __forceinline__ uint32_t cluster_rank()
@@ -161,39 +159,35 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr)
     return d;
 }
 
+// One MMA of the CTA pair: D (M = 256 rows, 128 in each CTA's TMEM) +=
+// A (each CTA's 128 rows at `adesc` in its own shared memory) x B^T (N = 256
+// columns, 128 from each CTA's shared memory at `bdesc`).
 template <bool kFp8>
-__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                     uint32_t idesc, uint32_t accumulate)
+__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                          uint32_t idesc, uint32_t accumulate)
 {
     if (kFp8) {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            " tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
     } else {
         asm volatile(
             "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
+            " tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
             "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
             : "memory");
     }
 }
 
-// Arrives on the mbarrier at this offset in every CTA of `mask` once the
-// MMAs issued so far by this thread have completed.
-__device__ __forceinline__ void umma_commit_mc(uint32_t bar, uint16_t mask)
+// Arrives on the mbarrier at this offset in both CTAs of the pair once the
+// pair MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void umma_commit_pair(uint32_t bar)
 {
     asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
-        " [%0], %1;" ::"r"(bar), "h"(mask)
-        : "memory");
-}
-
-__device__ __forceinline__ void umma_commit(uint32_t bar)
-{
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64"
+        " [%0], %1;" ::"r"(bar), "h"((uint16_t)3)
         : "memory");
 }
 
@@ -223,8 +217,8 @@ __device__ __forceinline__ void tmem_wait_ld()
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// Instruction descriptor: fp32 accumulator, A/B K-major, M = 128, N = 256;
-// operand format bf16 (kind::f16) or E4M3 (kind::f8f6f4).
+// Instruction descriptor: fp32 accumulator, A/B K-major, M = 256 (the CTA
+// pair), N = 256; operand format bf16 (kind::f16) or E4M3 (kind::f8f6f4).
 template <bool kFp8>
 __host__ __device__ constexpr uint32_t instr_desc()
 {
@@ -232,7 +226,7 @@ __host__ __device__ constexpr uint32_t instr_desc()
            | ((kFp8 ? 0u : 1u) << 7)                   // A format: e4m3 / bf16
            | ((kFp8 ? 0u : 1u) << 10)                  // B format
            | ((uint32_t)(kBN >> 3) << 17)              // N / 8
-           | ((uint32_t)(kBM >> 4) << 24);             // M / 16
+           | ((uint32_t)((kCluster * kBM) >> 4) << 24);   // M / 16
 }
 
 template <bool kFp8, bool kHam>
@@ -255,28 +249,28 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     const int ktiles = a.dims / (kFp8 ? 128 : 64);                 // K-slices per segmentation
-    const int ntiles = (int)((a.n + kBM - 1) / kBM);
     const int rank = (int)cluster_rank();
+    const bool leader = rank == 0;
     const int pair0 = blockIdx.x / kCluster, npairs_grid = gridDim.x / kCluster;
-    const int npairs = (ntiles + kCluster - 1) / kCluster;
-    const uint16_t cluster_mask = (uint16_t)((1u << kCluster) - 1u);
+    const int npairs = (int)((a.n + kCluster * kBM - 1) / (kCluster * kBM));
 
     const uint32_t full0 = smem_u32(bars);
     const uint32_t empty0 = smem_u32(bars + kStages);
-    // seg_full[k]: the MMAs of segmentation k of the current tile are done;
-    // seg_free[k]: the epilogue has read TMEM columns [k*256, k*256+256)
+    // seg_full[k]: the MMAs of segmentation k of the current tile are done
+    // (both CTAs); seg_free[k] (the leader's): both CTAs' epilogues have read
+    // TMEM columns [k*256, k*256+256)
     const uint32_t seg_full0 = smem_u32(bars + 2 * kStages);
     const uint32_t seg_free0 = smem_u32(bars + 2 * kStages + 2);
     const uint32_t drain = smem_u32(bars + 2 * kStages + 4);
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
-            mbar_init(full0 + 8 * s, 1);
-            mbar_init(empty0 + 8 * s, kCluster);     // one MMA commit per CTA of the pair
+            mbar_init(full0 + 8 * s, 1);             // the leader's producer, plus bytes
+            mbar_init(empty0 + 8 * s, 1);            // the leader's MMA commit
         }
         for (int k = 0; k < 2; ++k) {
             mbar_init(seg_full0 + 8 * k, 1);
-            mbar_init(seg_free0 + 8 * k, 32 * kEpiWarps);
+            mbar_init(seg_free0 + 8 * k, kCluster * 32 * kEpiWarps);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -288,17 +282,21 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
         qscale[i] = (kFp8 && !kHam && q < a.nq) ? a.qscale[2 * q + k] : 1.0f;
     }
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+        // one warp of each CTA of the pair allocates together
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
                          smem_u32(tmem_slot))
                      : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
-    // the peer's barriers must be initialised before anything is multicast
+    // the peer's barriers must be initialised before either CTA signals them
     cluster_sync();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    // the leader's barriers as seen from this CTA
+    const uint32_t full0_lead = map_to_rank(full0, 0);
+    const uint32_t seg_free0_lead = map_to_rank(seg_free0, 0);
 
     uint32_t issued = 0;     // producer: stage loads issued
 
@@ -307,8 +305,9 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             uint32_t it = 0;
             bool ok = true;
             for (int pair = pair0; pair < npairs && ok; pair += npairs_grid) {
-                // a tile past the last entry reads zeros (out-of-range TMA rows)
-                const int tile = pair * kCluster + rank;
+                // this CTA's 128 entries of the pair's 256 (past the last
+                // entry the TMA reads zeros)
+                const int row0 = pair * (kCluster * kBM) + rank * kBM;
                 for (int seg = 0; seg < 2 && ok; ++seg) {
                     for (int kt = 0; kt < ktiles; ++kt, ++it) {
                         const int s = it % kStages;
@@ -316,13 +315,11 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                         if (!mbar_wait(empty0 + 8 * s, ph, abort_flag)) { ok = false; break; }
                         const uint32_t sa = smem_u32(ring + s * kStageBytes);
                         const uint32_t sb = sa + kTileABytes;
-                        // own entry tile + both halves of the query tile (one
-                        // from this CTA, one multicast by the peer)
-                        mbar_arrive_expect_tx(full0 + 8 * s, kStageBytes);
+                        // the leader's full barrier counts both CTAs' bytes
+                        if (leader) mbar_arrive_expect_tx(full0 + 8 * s, kCluster * kStageBytes);
                         const int x = seg * a.dims + kt * (kFp8 ? 128 : 64);
-                        tma_load_2d(sa, &tm_e, full0 + 8 * s, x, tile * kBM);
-                        tma_load_2d_mc(sb + rank * kHalfBBytes, &tm_q, full0 + 8 * s, x,
-                                       rank * (kBN / kCluster), cluster_mask);
+                        tma_load_2d_pair(sa, &tm_e, full0_lead + 8 * s, x, row0);
+                        tma_load_2d_pair(sb, &tm_q, full0_lead + 8 * s, x, rank * (kBN / 2));
                         ++issued;
                     }
                 }
@@ -333,13 +330,14 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             }
         }
     } else if (warp == 1) {
-        if (lane == 0) {
+        if (lane == 0 && leader) {
             constexpr uint32_t idesc = instr_desc<kFp8>();
             uint32_t it = 0, tiles_done = 0;
             bool ok = true;
             for (int pair = pair0; pair < npairs && ok; pair += npairs_grid, ++tiles_done) {
                 for (int seg = 0; seg < 2 && ok; ++seg) {
-                    // the previous tile's columns of this segmentation are read
+                    // both CTAs have read the previous tile's columns of this
+                    // segmentation
                     if (!mbar_wait(seg_free0 + 8 * seg, (tiles_done & 1) ^ 1, abort_flag)) {
                         ok = false;
                         break;
@@ -358,13 +356,14 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
 #pragma unroll
                         for (int kk = 0; kk < 4; ++kk) {
                             // K step of 32 bytes inside the 128-byte swizzle atom
-                            umma<kFp8>(d_tmem, sw128_desc(sa + 32 * kk), sw128_desc(sb + 32 * kk),
-                                       idesc, (kt > 0 || kk > 0) ? 1u : 0u);
+                            umma_pair<kFp8>(d_tmem, sw128_desc(sa + 32 * kk),
+                                            sw128_desc(sb + 32 * kk), idesc,
+                                            (kt > 0 || kk > 0) ? 1u : 0u);
                         }
                         // frees the stage in both CTAs when these MMAs finish
-                        umma_commit_mc(empty0 + 8 * s, cluster_mask);
+                        umma_commit_pair(empty0 + 8 * s);
                     }
-                    if (ok) umma_commit(seg_full0 + 8 * seg);
+                    if (ok) umma_commit_pair(seg_full0 + 8 * seg);
                 }
             }
             if (!ok) {
@@ -373,13 +372,14 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
             }
             // every MMA issued by this thread has completed once `drain` fires;
             // TMEM is released only after that (or after the time limit)
-            umma_commit(drain);
+            umma_commit_pair(drain);
             if (!mbar_wait(drain, 0, nullptr)) a.status[0] = 3;
         }
     } else {
-        // epilogue warps 2..17: TMEM lane quarter = warp % 4, column half by
-        // warp.  The first segmentation's distances are taken into registers
-        // as soon as its MMAs finish (the second's run meanwhile), which frees
+        // epilogue warps 2..17: TMEM lane quarter = warp % 4, 64 columns by
+        // warp.  Each CTA holds its own 128 rows of the pair's accumulator.
+        // The first segmentation's distances are taken into registers as
+        // soon as its MMAs finish (the second's run meanwhile), which frees
         // its columns for the next tile; the second's are combined and stored
         // while the next tile's first segmentation is being accumulated.
         const int quarter = warp & 3;
@@ -388,8 +388,7 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
         const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + c_begin;
         uint32_t tiles_done = 0;
         for (int pair = pair0; pair < npairs; pair += npairs_grid, ++tiles_done) {
-            const int tile = pair * kCluster + rank;
-            const int64_t e = (int64_t)tile * kBM + row;
+            const int64_t e = (int64_t)pair * (kCluster * kBM) + rank * kBM + row;
             const bool valid = e < a.n;
             float en0 = 0.f, en1 = 0.f, es0 = 1.f, es1 = 1.f;
             if (valid) {
@@ -426,7 +425,7 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                 }
             }
             tc_fence_before();
-            mbar_arrive(seg_free0);
+            mbar_arrive_cluster(seg_free0_lead);
             if (!mbar_wait(seg_full0 + 8, tiles_done & 1, abort_flag)) {
                 a.status[0] = 4;
                 *abort_flag = 1;
@@ -459,14 +458,14 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
                 }
             }
             tc_fence_before();
-            mbar_arrive(seg_free0 + 8);
+            mbar_arrive_cluster(seg_free0_lead + 8);
         }
     }
 
     __syncthreads();
-    if (warp == 0 && lane == 0 && *abort_flag) {
-        // let the loads already issued land before the CTA's shared memory is
-        // released: the last load into stage s completed phase (count_s - 1)
+    if (warp == 0 && lane == 0 && leader && *abort_flag) {
+        // let the loads already issued land before shared memory is released:
+        // the last fill of stage s completed phase (count_s - 1)
         for (int s = 0; s < kStages; ++s) {
             const uint32_t count_s = (issued + kStages - 1 - s) / kStages;
             if (count_s == 0) continue;
@@ -474,13 +473,14 @@ prefilter_gemm_kernel(const __grid_constant__ CUtensorMap tm_e,
         }
     }
     __syncthreads();
+    // the leader's MMAs (which read the peer's shared memory and write its
+    // TMEM) have completed before either CTA releases anything
+    cluster_sync();
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, 512;" ::"r"(tmem)
                      : "memory");
     }
-    // neither CTA leaves while the other may still multicast into its shared
-    // memory or arrive on its barriers
     cluster_sync();
 }
 
