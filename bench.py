@@ -449,6 +449,7 @@ def run_embed(args, wl, torch):
     words = (nx * ny * nz + 31) // 32
     rr_bytes = nq * c * (2 * words * 4 + 8)
     gemm_flops = 2.0 * nq * wl["n"] * 2 * dims
+    gemm_bytes = wl["n"] * 2 * dims * (1 if mode == DBQ_MODE_EMBED_FP8 else 2) + nq * wl["n"] * 4
     peak, peak_kind = _peaks()
     bf16_peak, bf16_kind = 1900.0, "fallback bf16 dense burst"
     gemm_peak = bf16_peak * (2.0 if mode == DBQ_MODE_EMBED_FP8 else 1.0)
@@ -479,7 +480,13 @@ def run_embed(args, wl, torch):
         "stages_ms": stages,
         "sparse_rerank": sparse_line,
         "gemm": ({"tflops": gemm_flops / (stages["distances"] / 1000.0) / 1e12, "peak": gemm_peak,
-                  "peak_kind": bf16_kind, "flops_per_launch": gemm_flops}
+                  "peak_kind": bf16_kind, "flops_per_launch": gemm_flops,
+                  "tensor_frac": gemm_flops / (stages["distances"] / 1000.0) / 1e12 / gemm_peak,
+                  # the entry embeddings stream from HBM once and the distances
+                  # are written once: at 256 queries the GEMM sits on the ridge
+                  "hbm_bytes_per_launch": gemm_bytes,
+                  "hbm_gbs": gemm_bytes / (stages["distances"] / 1000.0) / 1e9,
+                  "hbm_frac": gemm_bytes / (stages["distances"] / 1000.0) / 1e9 / peak}
                  if mode != DBQ_MODE_HASH else None),
         "hamming": ({"ms": stages["distances"], "code_bytes": wl["n"] * 2 * dims,
                      "pairs_per_s": nq * wl["n"] / (stages["distances"] / 1000.0),
