@@ -129,7 +129,12 @@ typedef struct dbq_hit {
  *                estimate of |A xor B|.  The sketch is encoded like the block
  *                means (bf16, FP8 with scale max|v|/448), and its sign code
  *                (bit j = [v_j > 0], 32 buckets per word) is kept for
- *                DBQ_MODE_HASH.  The two flags exclude each other.
+ *                DBQ_MODE_HASH, also as one E4M3 byte per bucket (1.0 or 0)
+ *                with its popcount, the operands of the exact tensor-core
+ *                Hamming distance.  Device memory per entry: 2 x 4096 x
+ *                (2 + 1 + 1) bytes + 1 KiB of bits + 24 bytes, plus a 2 x V
+ *                byte bucket table per database.  The two flags exclude each
+ *                other.
  * Returns DBQ_OK and *out, or DBQ_EINVAL / DBQ_ENOMEM / DBQ_ECUDA.
  */
 int db_create(dbq_db** out, int nx, int ny, int nz, int64_t capacity, int storage,
