@@ -57,7 +57,7 @@ enum dbq_status {
     DBQ_ENOMEM = -2,   /* device or host allocation failed                     */
     DBQ_ESTATE = -3,   /* call not valid in the handle's state (e.g. unbuilt)  */
     DBQ_ECUDA = -4,    /* a CUDA runtime call or a kernel launch failed         */
-    DBQ_ETIMEOUT = -5, /* reserved: a bounded device wait gave up               */
+    DBQ_ETIMEOUT = -5, /* a bounded device wait of the prefilter GEMM gave up  */
     DBQ_ERANGE = -6    /* k or an index outside [0, N]                          */
 };
 

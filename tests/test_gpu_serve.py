@@ -88,3 +88,36 @@ def test_admission_by_memory_budget(dbs):
             tiny.submit(v1[0], 0)
     finally:
         tiny.close()
+
+
+def test_hash_mode_in_the_mix_equals_alone():
+    """Serving over sketch databases with the Hamming prefilter: each
+    request's hits equal the same query run alone."""
+    import torch  # noqa: F401
+    from paper_2205_04550_gb300 import DBQ_MODE_HASH, build
+    build.build()
+    s1, s2 = (48, 40, 32), (32, 32, 32)
+    v1, _ = synth.database_np(s1, 300)
+    v2, _ = random_db(s2, 500, seed=5)
+    d1 = Database(s1, 300, DBQ_STORE_BITS, T1, T2, sketch=True)
+    d2 = Database(s2, 500, DBQ_STORE_BITS, T1, T2, sketch=True)
+    try:
+        d1.load(0, v1)
+        d1.build()
+        d2.load(0, v2)
+        d2.build()
+        reqs = _requests(v1, v2, 120, seed=13)
+        arrivals = serve.poisson_arrivals(3000.0, len(reqs), seed=9)
+        srv = serve.Server([d1, d2], mode="hash", k=10, n_candidates=64, max_batch=32, lanes=2)
+        try:
+            results = serve.run_open_loop(srv, reqs, arrivals)
+        finally:
+            srv.close()
+        databases = [d1, d2]
+        for i in range(0, len(reqs), 5):
+            p, db = reqs[i]
+            alone, _ = databases[db].query_batch([p], 10, DBQ_MODE_HASH, 64)
+            assert results[i].tobytes() == alone[0].tobytes(), i
+    finally:
+        d1.close()
+        d2.close()
