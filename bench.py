@@ -357,6 +357,43 @@ def run_reference(args, wl):
     return 0
 
 
+def _embed_distance_error(db, plist, mode, wl, stream, n_q=16, n_e=64):
+    """Prefilter distances L = d_1 + d_2 from the GPU against binary64
+    distances of the exact 8^3 block means (the embedding before any
+    encoding), on a sample of queries and entries: the error of the chosen
+    precision (encoding and binary32 accumulation together)."""
+    from paper_2205_04550_gb300 import _dbq
+    nx, ny, nz = wl["shape"]
+    n = wl["n"]
+    dist = np.zeros((n_q, n), np.float32)
+    _dbq.db_prefilter(db.handle, plist[:n_q], mode, 0, dist=dist, stream=stream)
+    ents = np.linspace(0, n - 1, n_e).astype(np.int64)
+
+    def block_means(mask):       # mask [nz, ny, nx] of 0/1
+        b = mask.reshape(nz // 8, 8, ny // 8, 8, nx // 8, 8).sum(axis=(1, 3, 5))
+        return b.reshape(-1).astype(np.float64) / 512.0
+
+    emb_e = []
+    for e in ents:
+        planes, _ = db.masks(int(e), 1)
+        bits = np.unpackbits(planes[0].view(np.uint8), axis=-1, bitorder="little")
+        bits = bits[:, :nx * ny * nz].reshape(2, nz, ny, nx)
+        emb_e.append([block_means(bits[k]) for k in range(2)])
+    t = (np.float32(wl["t1"]), np.float32(wl["t2"]))
+    err, rel = [], []
+    for q in range(n_q):
+        vol = plist[q].cpu().numpy()
+        eq = [block_means((vol >= t[k]).astype(np.uint8)) for k in range(2)]
+        for j, e in enumerate(ents):
+            ref = sum(float(np.sqrt(np.sum((eq[k] - emb_e[j][k]) ** 2))) for k in range(2))
+            d = abs(float(dist[q, e]) - ref)
+            err.append(d)
+            rel.append(d / ref if ref > 0 else 0.0)
+    return {"pairs": n_q * n_e, "max_abs": max(err), "mean_abs": float(np.mean(err)),
+            "max_rel": max(rel), "mean_rel": float(np.mean(rel)),
+            "reference": "binary64 L2 of the exact block means (before encoding)"}
+
+
 def run_embed(args, wl, torch):
     """Batched queries through the embedding prefilter + exact re-ranking,
     compared with the exact scan of the same queries on the same GPU."""
@@ -445,6 +482,7 @@ def run_embed(args, wl, torch):
                       for m in (1, 5, 15)}
     prefilter_only[f"best_in_{c}_candidates"] = float(np.mean(
         [best[q] in pf_cand[q] for q in range(nq)]))
+    dist_error = None if wl.get("sketch") else _embed_distance_error(db, plist, mode, wl, stream)
     value = world * args.steps * nq / elapsed
     words = (nx * ny * nz + 31) // 32
     rr_bytes = nq * c * (2 * words * 4 + 8)
@@ -475,6 +513,7 @@ def run_embed(args, wl, torch):
                    "embedding": "count sketch" if wl.get("sketch") else "8^3 block means"},
         "agreement_vs_exact_gpu_scan": agreement,
         "prefilter_ranking_vs_exact": prefilter_only,
+        "distance_error_vs_fp64": dist_error,
         "exact_scan_queries_per_s": nq / exact_s,
         "speedup_vs_exact_gpu_scan": (nq / exact_s and value / (nq / exact_s)),
         "stages_ms": stages,
