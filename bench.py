@@ -53,6 +53,10 @@ WORKLOADS = {
     "embed_10k_128": dict(shape=(128, 128, 128), n=10_000, k=10, t1=0.6, t2=0.25, embed=True,
                           queries=256, candidates=512, mode="bf16",
                           desc="10,000 x 128^3 bit-packed + bf16 embeddings (profiling size)"),
+    "embed_2k_128": dict(shape=(128, 128, 128), n=2000, k=10, t1=0.6, t2=0.25, embed=True,
+                         queries=256, candidates=512, mode="bf16",
+                         desc="2,000 x 128^3 bit-packed + bf16 embeddings (profiling size, "
+                              "1.1 GB on the device)"),
     "sketch_100k_128_hash": dict(shape=(128, 128, 128), n=100_000, k=15, t1=0.6, t2=0.25,
                                  sketch=True, queries=256, candidates=512, mode="hash",
                                  desc="100,000 x 128^3 bit-packed + count sketches (2x4096) and "
@@ -95,6 +99,13 @@ WORKLOADS = {
                          desc="Table-2 synthetic protocol on the surrogate: 1,000 held-out "
                               "patients, direct 128^3 query vs DS64 and DS32 (50,000 entries), "
                               "top-1/5/15 agreement"),
+    "plan_mix_small": dict(mix=[dict(shape=(64, 64, 64), n=8000), dict(shape=(128, 128, 128),
+                                                                     n=1000)],
+                           share=[0.7, 0.3], queries=128, k=10, t1=0.6, t2=0.25,
+                           desc="plan_mix with 8,000 x 64^3 and 1,000 x 128^3 (1.0 GB on the "
+                                "device, profiling size)"),
+    "ds_2k_128": dict(shape=(128, 128, 128), n=2000, k=15, t1=0.6, t2=0.25, patients=50,
+                      desc="ds_agreement on 2,000 x 128^3 and 50 patients (profiling size)"),
     "exact_packed_1k_64": dict(shape=(64, 64, 64), n=1024, k=10, t1=0.6, t2=0.25,
                                desc="1,024 x 64^3 bit-packed, t=(0.6,0.25), top-10"),
 }
@@ -869,11 +880,11 @@ def main(argv=None):
         return run_embed(args, wl, torch)
     if args.workload == "pde_db_128":
         return run_pde(args, wl, torch)
-    if args.workload == "plan_mix":
+    if args.workload in ("plan_mix", "plan_mix_small"):
         return run_plan_mix(args, wl, torch)
     if args.workload == "serve_mix":
         return run_serve(args, wl, torch)
-    if args.workload == "ds_agreement":
+    if args.workload in ("ds_agreement", "ds_2k_128"):
         return run_ds_agreement(args, wl, torch)
 
     db = build_database(torch, wl)

@@ -6,8 +6,9 @@
 // commutes with thresholding, so the downsampled masks are taken straight
 // from the full-resolution bit planes: voxel (x, y, z) of the coarse grid is
 // voxel (f x, f y, f z) of the fine grid (reading: stride sampling from the
-// origin).  One thread per coarse 32-bit word gathers its 32 bits; the
-// coarse mask sizes are re-counted with popcounts.
+// origin).  One thread per coarse 32-bit word gathers its 32 bits (when the
+// coarse rows are whole words, from one source row with no per-bit index
+// arithmetic); the coarse mask sizes are re-counted with popcounts.
 #include "kernels.h"
 
 namespace dbq {
@@ -25,7 +26,18 @@ __global__ void downsample_kernel(const uint32_t* __restrict__ src, int64_t src_
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < dst_wp;
          w += (int64_t)gridDim.x * blockDim.x) {
         uint32_t word = 0;
-        if (w < dst_words) {
+        if (w < dst_words && dnx % 32 == 0) {
+            // the word's 32 coarse voxels are one run along x: its source bits
+            // are j0, j0 + f, ..., one division per word
+            const int64_t i0 = w * 32;
+            const int64_t x0 = i0 % dnx, yz = i0 / dnx;
+            const int64_t y = yz % dny, z = yz / dny;
+            const int64_t j0 = f * x0 + (int64_t)nx * (f * y + (int64_t)ny * (f * z));
+            for (int b = 0; b < 32; ++b) {
+                const int64_t j = j0 + (int64_t)f * b;
+                word |= ((__ldg(s + (j >> 5)) >> (j & 31)) & 1u) << b;
+            }
+        } else if (w < dst_words) {
             for (int b = 0; b < 32; ++b) {
                 const int64_t i = w * 32 + b;             // coarse voxel
                 if (i >= dv) break;
