@@ -147,9 +147,78 @@ __device__ __forceinline__ bool topk_publish(TopK& t, int k, Cand* cand, unsigne
     return topk_publish_slot(t, k, cand, blockIdx.x, gridDim.x, ticket);
 }
 
+// Merge of m / k published lists, each sorted best first (every list comes
+// from a flushed or merged TopK), when they fit in half of the shared slots:
+// every candidate's final position is its position in its own list plus the
+// number of candidates of each other list that are better (a binary search
+// per list), and the first k positions are written to the upper half of the
+// slots, then moved down to [0, k).  The order is strict (entry indices are
+// unique), so positions never collide; sentinels are never better than a
+// real candidate and are not placed.
+__device__ __forceinline__ bool topk_merge_sorted(TopK& t, int k, const Cand* cand, int64_t m)
+{
+    constexpr int kHalf = kTopkCap / 2;
+    if (m % k != 0 || m > kHalf || k > kHalf) return false;
+    const int lists = (int)(m / k);
+    for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) {
+        if (i < (int)m) {
+            const Cand* src = cand + i;
+            t.key[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->key));
+            t.idx[i] = __ldcg(reinterpret_cast<const long long*>(&src->index));
+            t.pay0[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay0));
+            t.pay1[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay1));
+        } else if (i >= kHalf) {
+            topk_clear_slot(t, i);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (int)m; i += blockDim.x) {
+        const uint64_t ck = t.key[i];
+        const int64_t ci = t.idx[i];
+        if (ci == kSentinelIndex) continue;
+        const int own = i / k;
+        int r = i - own * k;
+        for (int l = 0; l < lists && r < k; ++l) {
+            if (l == own) continue;
+            // the candidates of list l better than this one form a prefix
+            int lo = 0, hi = k;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const int j = l * k + mid;
+                if (better(t.key[j], t.idx[j], ck, ci)) lo = mid + 1;
+                else hi = mid;
+            }
+            r += lo;
+        }
+        if (r < k) {
+            t.key[kHalf + r] = ck;
+            t.idx[kHalf + r] = ci;
+            t.pay0[kHalf + r] = t.pay0[i];
+            t.pay1[kHalf + r] = t.pay1[i];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHalf; i += blockDim.x) {
+        if (i < k) {
+            t.key[i] = t.key[kHalf + i];
+            t.idx[i] = t.idx[kHalf + i];
+            t.pay0[i] = t.pay0[kHalf + i];
+            t.pay1[i] = t.pay1[kHalf + i];
+        } else {
+            topk_clear_slot(t, i);
+        }
+    }
+    __syncthreads();
+    for (int i = kHalf + threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
+    if (threadIdx.x == 0) t.misc[0] = 0;
+    __syncthreads();
+    return true;
+}
+
 // In the last CTA: merge the m published candidates into slots [0, k).
 __device__ __forceinline__ void topk_merge_published(TopK& t, int k, const Cand* cand, int64_t m)
 {
+    if (topk_merge_sorted(t, k, cand, m)) return;
     for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
     if (threadIdx.x == 0) t.misc[0] = 0;
     __syncthreads();
@@ -175,7 +244,7 @@ __device__ __forceinline__ void topk_merge_published(TopK& t, int k, const Cand*
     }
 }
 
-constexpr int kMergeGroup = 8;   // CTAs per first-level merge group
+constexpr int kMergeGroup = 16;  // CTAs per first-level merge group
 
 // Two-level publication for a grid of CTAs: every CTA publishes its list to
 // cand[blockIdx.x * k]; the last CTA to finish in each group of kMergeGroup
