@@ -116,12 +116,12 @@ DEFAULT_WORKLOAD = "exact_packed_50k_128"
 TRAFFIC = {
     "scan_packed_kernel": dict(files=("scan_packed.cu", "scan_core.cuh", "topk.cuh",
                                       "common.cuh"),
-                               sha="6c56322f5d16fbf3", entries=2000,
-                               read_bytes=1049182208, write_bytes=3328256,
+                               sha="28b320973988c1aa", entries=2000,
+                               read_bytes=1049206272, write_bytes=3647488,
                                capture="profiles/scan_packed_2k_128_ncu_full.md"),
     "scan_f16_kernel": dict(files=("scan_f16.cu", "topk.cuh", "common.cuh"),
-                            sha="96842491439226c1", entries=4000,
-                            read_bytes=2097512192, write_bytes=3325440,
+                            sha="bea418ed01a7b08d", entries=4000,
+                            read_bytes=2097377536, write_bytes=3295744,
                             capture="profiles/scan_f16_4k_64_ncu_full.md"),
 }
 METRIC = "DB entries/s per query (HBM GB/s vs peak); batched queries/s at top-1 match"
