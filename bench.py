@@ -174,6 +174,21 @@ def _peaks():
     return FALLBACK_HBM_GBS, "fallback"
 
 
+def _bf16_peak():
+    """Dense bf16 tensor peak (TFLOP/s) for a kernel timed alone: the measured
+    burst figure when the peaks file has it, else the 1.9 PFLOP/s fallback."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as fh:
+                d = json.load(fh)
+            if "bf16_tflops" in d:
+                return float(d["bf16_tflops"]), "measured bf16 dense burst"
+        except Exception:
+            pass
+    return 1900.0, "fallback bf16 dense burst"
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -466,10 +481,28 @@ def run_embed(args, wl, torch):
     torch.cuda.synchronize()
     db.set_sparse(False)
     sp_elapsed = p0.elapsed_time(p1) / 1000.0
+    sp_stages = {a: v / args.steps for a, v in sp_stage.items()}
+    # algorithmic bytes of the sparse re-rank: per candidate the 16-byte
+    # granules of the entry where the patient's masks are non-zero (both
+    # planes, 128 voxels of the flattened grid per granule) + 8 B of sizes
+    granules = 0
+    for q in range(nq):
+        flat = pats[q].reshape(-1)
+        pad = (-flat.numel()) % 128
+        for t in (wl["t1"], wl["t2"]):
+            m = flat >= t
+            if pad:
+                m = torch.cat([m, m.new_zeros(pad)])
+            granules += int(m.view(-1, 128).any(dim=1).sum().item())
+    sp_bytes = c * (16 * granules + 8 * nq)
+    sp_gbs = sp_bytes / (sp_stages["rerank"] / 1000.0) / 1e9
     sparse_line = {"queries_per_s": world * args.steps * nq / sp_elapsed,
                    "ms_per_step": 1000.0 * sp_elapsed / args.steps,
-                   "stages_ms": {a: v / args.steps for a, v in sp_stage.items()},
-                   "identical_hits": bool(sp_hits.tobytes() == hits.tobytes())}
+                   "stages_ms": sp_stages,
+                   "identical_hits": bool(sp_hits.tobytes() == hits.tobytes()),
+                   "rerank": {"gbs": sp_gbs, "bytes_per_launch": sp_bytes,
+                              "mean_support_bytes_per_candidate": 16.0 * granules / nq,
+                              "frac": None}}
     # the exact scan of the same queries, for agreement and speed-up
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -500,7 +533,8 @@ def run_embed(args, wl, torch):
     gemm_flops = 2.0 * nq * wl["n"] * 2 * dims
     gemm_bytes = wl["n"] * 2 * dims * (1 if mode == DBQ_MODE_EMBED_FP8 else 2) + nq * wl["n"] * 4
     peak, peak_kind = _peaks()
-    bf16_peak, bf16_kind = 1900.0, "fallback bf16 dense burst"
+    sparse_line["rerank"]["frac"] = sp_gbs / peak
+    bf16_peak, bf16_kind = _bf16_peak()
     gemm_peak = bf16_peak * (2.0 if mode == DBQ_MODE_EMBED_FP8 else 1.0)
     dominant = "rerank" if stages["rerank"] >= stages["distances"] or mode == DBQ_MODE_HASH else "gemm"
     if dominant == "rerank":

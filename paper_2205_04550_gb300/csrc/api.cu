@@ -375,7 +375,7 @@ int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaSt
 namespace {
 
 constexpr int kBatchQ = 256;      // queries per prefilter group (tensor-core N)
-constexpr int kRerankSlices = 8;
+constexpr int kRerankSlices = 4;
 
 size_t patient_bytes(const dbq_db* db, int kind)
 {
@@ -402,7 +402,8 @@ int ensure_batch(dbq_db* db, int k)
         if (!rc) rc = grow(db, &db->bplanes, q * 2 * db->wp * 4, "batch patient planes");
         if (!rc) rc = grow(db, &db->bpcount, q * 2 * 4, "batch patient sizes");
         if (!rc) rc = grow(db, &db->bhits, q * kMaxK * sizeof(dbq::Hit), "batch hits");
-        if (!rc) rc = grow(db, &db->btickets, q * sizeof(unsigned int), "batch tickets");
+        // one ticket per query, then the sparse re-rank's item counter
+        if (!rc) rc = grow(db, &db->btickets, (q + 1) * sizeof(unsigned int), "batch tickets");
         if (!rc) rc = grow(db, &db->bstatus, 16, "status");
         if (!rc) rc = grow(db, &db->bsup, q * 2 * db->wp4 * 4, "batch support lists");
         if (!rc) rc = grow(db, &db->bsuplen, q * 2 * 4, "batch support lengths");
@@ -434,7 +435,7 @@ int ensure_batch(dbq_db* db, int k)
             }
         }
         if (!rc) {
-            cudaError_t err = cudaMemset(db->btickets, 0, q * sizeof(unsigned int));
+            cudaError_t err = cudaMemset(db->btickets, 0, (q + 1) * sizeof(unsigned int));
             if (err == cudaSuccess) err = cudaMemset(db->bstatus, 0, 16);
             if (err == cudaSuccess) err = cudaDeviceSynchronize();
             if (err != cudaSuccess) rc = cuda_fail(err, "batch workspace initialisation");
@@ -1268,6 +1269,7 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
                 r.hits = db->bhits;
                 r.sup_lists = db->sparse ? db->bsup : nullptr;
                 r.sup_lens = db->sparse ? db->bsuplen : nullptr;
+                r.sched = db->sparse ? db->btickets + kBatchQ : nullptr;
                 cudaError_t err = dbq::launch_rerank(r, s);
                 if (err != cudaSuccess) return cuda_fail(err, "re-rank launch");
                 mark(db, 5, s);

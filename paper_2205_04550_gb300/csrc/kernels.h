@@ -189,6 +189,8 @@ struct RerankArgs {
     Hit* hits;                  // [nq][k]
     const uint32_t* sup_lists;  // [nq][2][wp4] support lists, or null (dense)
     const uint32_t* sup_lens;   // [nq][2]
+    unsigned int* sched;        // sparse only: item counter, zero between launches (nq <= 512),
+                                // or null for the round-robin order
 };
 cudaError_t launch_rerank(const RerankArgs& a, cudaStream_t stream);
 

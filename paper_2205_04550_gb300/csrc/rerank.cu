@@ -5,12 +5,17 @@
 // added, largest wins), so the returned hits carry exact counts and binary64
 // scores; only which entries are looked at comes from the prefilter.
 //
-// Work items are (query, slice of its candidates); the grid walks them
-// round-robin.  Each item gathers its candidates' planes with the shared
-// count loop of scan_core.cuh (patient words in registers), keeps a running
-// top-k, publishes it to the query's scratch row, and the last item of a
-// query (per-query atomic ticket, no spinning) merges the slices into the
-// query's k hits.
+// Work items are (query, slice of its candidates).  Each item gathers its
+// candidates' planes with the shared count loop of scan_core.cuh (patient
+// words in registers), keeps a running top-k, publishes it to the query's
+// scratch row, and the last item of a query (per-query atomic ticket, no
+// spinning) merges the slices into the query's k hits.
+//
+// Dense items all cost the same and the grid walks them round-robin.  Sparse
+// items cost in proportion to their query's support, which varies thirty-fold
+// between patients; there the CTAs take items from a global counter, largest
+// support first (each CTA ranks the queries by support length in shared
+// memory, the same order in every CTA), so the small items fill the tail.
 #include "kernels.h"
 #include "scan_core.cuh"
 #include "topk.cuh"
@@ -19,6 +24,26 @@ namespace dbq {
 namespace {
 
 constexpr int kGroupMax = 1024;
+constexpr int kOrderMax = 512;     // queries ranked by support for the sparse order
+
+// Largest support first, ties by query index: rank of query q among all.
+__device__ __forceinline__ void rank_by_support(const uint32_t* sup_lens, int nq, int* cost,
+                                                int* order)
+{
+    for (int q = threadIdx.x; q < nq; q += blockDim.x)
+        cost[q] = (int)(sup_lens[2 * q] + sup_lens[2 * q + 1]);
+    __syncthreads();
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+        const int c = cost[q];
+        int r = 0;
+        for (int j = 0; j < nq; ++j) {
+            const int cj = cost[j];
+            r += (cj > c || (cj == c && j < q)) ? 1 : 0;
+        }
+        order[r] = q;
+    }
+    __syncthreads();
+}
 
 template <int U, int EPI, bool kSparse>
 __global__ void __launch_bounds__(kScanThreads, 1)
@@ -29,13 +54,26 @@ rerank_kernel(const RerankArgs a)
     unsigned char* after_topk = topk_carve(tk, smem_raw);
     uint32_t* icnt = reinterpret_cast<uint32_t*>(after_topk);                  // [kGroupMax][2]
     int* next = reinterpret_cast<int*>(after_topk + (size_t)kGroupMax * 2 * sizeof(uint32_t));
-    unsigned char* cache_raw = after_topk + (size_t)kGroupMax * 2 * sizeof(uint32_t) + 16;
+    int* order = next + 4;                                                     // [kOrderMax]
+    int* cost = order + kOrderMax;                                              // [kOrderMax]
+    unsigned char* cache_raw = reinterpret_cast<unsigned char*>(cost + kOrderMax);
+    __shared__ int s_item;
     const int tid = threadIdx.x;
     const int per = (a.c + a.slices - 1) / a.slices;
     const int items = a.nq * a.slices;
     const uint2* ecount2 = reinterpret_cast<const uint2*>(a.ecount);
-    for (int item = blockIdx.x; item < items; item += gridDim.x) {
-        const int q = item / a.slices;
+    // every CTA makes exactly one failing grab, so items + grid grabs return
+    // the counter to zero for the next launch
+    const bool dynamic = kSparse && a.sched != nullptr;
+    if (dynamic) rank_by_support(a.sup_lens, a.nq, cost, order);
+    for (int iter = 0;; ++iter) {
+        if (dynamic) {
+            if (tid == 0) s_item = (int)atomicInc(a.sched, (unsigned)(items + gridDim.x - 1));
+            __syncthreads();
+        }
+        const int item = dynamic ? s_item : (int)blockIdx.x + iter * (int)gridDim.x;
+        if (item >= items) break;
+        const int q = dynamic ? order[item / a.slices] : item / a.slices;
         const int sl = item % a.slices;
         const int first = sl * per;
         const int gn = (a.c - first) < per ? (a.c - first) : per;
@@ -99,7 +137,9 @@ cudaError_t launch_rerank(const RerankArgs& a, cudaStream_t stream)
     if (a.nq < 1 || a.c < 1 || a.k < 1 || a.k > a.c || a.slices < 1 ||
         (a.c + a.slices - 1) / a.slices > kGroupMax)
         return cudaErrorInvalidValue;
+    if (a.sched && (!a.sup_lists || a.nq > kOrderMax)) return cudaErrorInvalidValue;
     const size_t smem = topk_smem_bytes() + (size_t)kGroupMax * 2 * sizeof(uint32_t) + 16 +
+                        (size_t)2 * kOrderMax * sizeof(int) +
                         (a.sup_lists ? kSupportCacheBytes : 0);
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);

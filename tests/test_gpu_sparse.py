@@ -103,3 +103,54 @@ def test_sparse_toggle_and_surrogate(torch):
         for q in range(3):
             assert_hits_equal(exact_b[q], oracle.query(vols, pats[q], T1, T2, 10), 10)
         assert sparse_b[2][0]["index"] == 77
+
+
+def test_sparse_rerank_scheduling_many_queries(torch):
+    """Sparse re-ranking takes its items largest support first from a device
+    counter that must return to zero after every launch: many queries with
+    supports from empty to the whole grid, launched repeatedly with different
+    batch sizes, give the dense re-rank's hits bit for bit and the oracle's
+    hits among the candidates."""
+    shape = (64, 64, 32)
+    n, c, k = 600, 96, 7
+    vols, _ = synth.database_np(shape, n)
+    pats = [_sparse_patient(shape, s, frac=f)
+            for s, f in enumerate([0.002, 0.01, 0.05, 0.1, 0.3, 0.6] * 20)]
+    pats[5] = np.zeros(shape[::-1], np.float32)
+    pats[6] = np.ones(shape[::-1], np.float32)
+    pats += list(synth.patients_np(shape, list(range(1, 31)))[0])
+    vols[123] = pats[40]
+    with Database(shape, n, DBQ_STORE_BITS, T1, T2, embed=True) as db:
+        db.load(0, vols)
+        db.build()
+        dense, _ = db.query_batch(pats, k, DBQ_MODE_EMBED_BF16, c)
+        _, cand = db.prefilter(pats, DBQ_MODE_EMBED_BF16, c)
+        db.set_sparse(True)
+        for sub in (pats, pats[:3], pats[100:], pats):
+            sparse, _ = db.query_batch(sub, k, DBQ_MODE_EMBED_BF16, c)
+            off = 100 if len(sub) == len(pats) - 100 else 0
+            assert sparse.tobytes() == dense[off:off + len(sub)].tobytes()
+    for q in (0, 5, 6, 40, 149):
+        sorted_c = np.sort(cand[q])
+        ref = oracle.query(vols[sorted_c], pats[q], T1, T2, k)
+        ref["index"] = sorted_c[ref["index"]]
+        assert_hits_equal(dense[q], ref, k)
+    assert dense[40][0]["index"] == 123
+
+
+def test_sparse_rerank_support_beyond_cache(torch):
+    """A full patient on a 128 x 64 x 64 grid has 8,192 support positions,
+    more than the shared-memory cache holds: that item falls back to the
+    CTA-wide count loop while the others run one warp per entry."""
+    shape = (128, 64, 64)
+    n, c, k = 200, 40, 5
+    vols, _ = synth.database_np(shape, n)
+    pats = [np.ones(shape[::-1], np.float32)] + [_sparse_patient(shape, s) for s in range(9)]
+    with Database(shape, n, DBQ_STORE_BITS, T1, T2, embed=True) as db:
+        db.load(0, vols)
+        db.build()
+        dense, _ = db.query_batch(pats, k, DBQ_MODE_EMBED_BF16, c)
+        db.set_sparse(True)
+        for _ in range(2):
+            sparse, _ = db.query_batch(pats, k, DBQ_MODE_EMBED_BF16, c)
+            assert sparse.tobytes() == dense.tobytes()
