@@ -485,15 +485,7 @@ def run_embed(args, wl, torch):
     # algorithmic bytes of the sparse re-rank: per candidate the 16-byte
     # granules of the entry where the patient's masks are non-zero (both
     # planes, 128 voxels of the flattened grid per granule) + 8 B of sizes
-    granules = 0
-    for q in range(nq):
-        flat = pats[q].reshape(-1)
-        pad = (-flat.numel()) % 128
-        for t in (wl["t1"], wl["t2"]):
-            m = flat >= t
-            if pad:
-                m = torch.cat([m, m.new_zeros(pad)])
-            granules += int(m.view(-1, 128).any(dim=1).sum().item())
+    granules = sum(_support_granules(torch, pats[q], wl["t1"], wl["t2"]) for q in range(nq))
     sp_bytes = c * (16 * granules + 8 * nq)
     sp_gbs = sp_bytes / (sp_stages["rerank"] / 1000.0) / 1e9
     sparse_line = {"queries_per_s": world * args.steps * nq / sp_elapsed,
@@ -688,6 +680,20 @@ def run_pde(args, wl, torch):
     return 0
 
 
+def _support_granules(torch, vol, t1, t2):
+    """16-byte granules (128 voxels of the flattened grid) where the
+    patient's two masks are non-zero: what the sparse loops read per entry."""
+    flat = vol.reshape(-1)
+    pad = (-flat.numel()) % 128
+    total = 0
+    for t in (t1, t2):
+        m = flat >= t
+        if pad:
+            m = torch.cat([m, m.new_zeros(pad)])
+        total += int(m.view(-1, 128).any(dim=1).sum().item())
+    return total
+
+
 def _mix_databases(torch, wl, embed=False):
     dbs = []
     for part in wl["mix"]:
@@ -757,9 +763,19 @@ def run_plan_mix(args, wl, torch):
             e1.record(stream)
             torch.cuda.synchronize()
             el = e0.elapsed_time(e1) / 1000.0
+            # algorithmic bytes per launch: every query reads its database's
+            # planes (dense) or their patient-support granules (sparse) once
+            nbytes = 0
+            for q in range(nq):
+                part = wl["mix"][which[q]]
+                nx, ny, nz = part["shape"]
+                per = (16 * _support_granules(torch, pats[q], wl["t1"], wl["t2"]) if sparse
+                       else 2 * ((nx * ny * nz + 31) // 32) * 4)
+                nbytes += part["n"] * (per + 8)
             results["sparse" if sparse else "dense"] = {
                 "queries_per_s": world * args.steps * nq / el,
                 "ms_per_launch": 1000.0 * el / args.steps,
+                "bytes_per_launch": nbytes, "gbs": nbytes / (el / args.steps) / 1e9,
                 "items_per_sm": tuned["items_per_sm"], "tuning_ms": tuned.get("ms"),
                 "tuning_cached": tuned.get("cached")}
     dense = results["dense"]

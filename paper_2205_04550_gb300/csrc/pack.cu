@@ -15,7 +15,7 @@ namespace dbq {
 namespace {
 
 constexpr int kPackThreads = 256;
-constexpr int kPackUnroll = 4;   // words per warp per iteration (loads in flight)
+constexpr int kPackUnroll = 8;   // loads per lane per iteration (in flight at once)
 
 template <bool kHalf>
 __device__ __forceinline__ float load_value(const void* base, int64_t i)
@@ -51,7 +51,7 @@ __device__ __forceinline__ void pack_volume(const void* __restrict__ src, int64_
 #pragma unroll
             for (int u = 0; u < kPackUnroll; ++u) {
                 const int64_t vox = (g0 + u) * (WPL * 32) + (int64_t)lane * VPL;
-                raw[u] = (g0 + u < groups && vox < v) ? __ldg(s4 + vox / VPL) : make_uint4(0, 0, 0, 0);
+                raw[u] = (g0 + u < groups && vox < v) ? __ldcs(s4 + vox / VPL) : make_uint4(0, 0, 0, 0);
             }
 #pragma unroll
             for (int u = 0; u < kPackUnroll; ++u) {
@@ -200,15 +200,17 @@ __global__ void rows_to_f16_kernel(const void* __restrict__ src, int64_t v, int6
     }
 }
 
-// Blocks per volume: enough warps for the words of one volume (4 words per
-// warp-iteration at least), 64 per volume for many volumes, and enough to
-// fill the GPU (about 8 blocks per SM) when there are few.
+// Blocks per volume: no more warps than the words of one volume need
+// (kPackUnroll loads of 4 words per warp-iteration), at least 16 per volume
+// when there are many volumes (each warp then loops over several
+// iterations), and enough to fill the GPU (about 8 blocks per SM) when
+// there are few.
 int64_t pack_blocks(int64_t wp, int64_t count)
 {
     const int64_t warps_needed = (wp + kPackUnroll * 4 - 1) / (kPackUnroll * 4);
     const int64_t most = (warps_needed * 32 + kPackThreads - 1) / kPackThreads;
     int64_t bx = (1216 + count - 1) / count;
-    if (bx < 64) bx = 64;
+    if (bx < 16) bx = 16;
     if (bx > most) bx = most;
     return bx < 1 ? 1 : bx;
 }

@@ -110,7 +110,7 @@ __device__ __forceinline__ void zero(float (&r)[VEC])
 // tile) read a clamped voxel and store nothing.  Offsets are 32-bit
 // (V < 2^31).
 template <int VEC>
-__global__ void __launch_bounds__(256, VEC == 4 ? 3 : 4)
+__global__ void __launch_bounds__(256, 4)   // 64 registers: 32 warps per SM
 rd_step_kernel(RdStepArgs g, int launch)
 {
     constexpr int TX = tile_x(VEC);
