@@ -649,7 +649,8 @@ def run_pde(args, wl, torch):
             "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
             "algorithmic_bytes_per_launch": updates * 8.0 / max(launches, 1),
             "note": "8 B per voxel update (read u, write u); the face coefficients "
-                    "(12 B/voxel, shared by the batch) are L2-resident re-reads",
+                    "(16 B/voxel: +x, +y, +z and -y faces, shared by the batch) are "
+                    "L2-resident re-reads",
             "kernel_ms_per_launch": step_ms / max(launches, 1)}
     value = world * sims * args.steps / elapsed
     line = {
