@@ -1541,7 +1541,7 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
     }
     bool any_sparse = false;
     for (int q = 0; q < nq; ++q) any_sparse |= p->dbs[db_of_query[q]]->sparse;
-    cudaError_t err = dbq::launch_scan_tasks(p->tasks_dev, p->items_dev, nitems, p->counter,
+    cudaError_t err = dbq::launch_scan_tasks(p->tasks_dev, nq, p->items_dev, nitems, p->counter,
                                              p->sms, any_sparse, s);
     if (err != cudaSuccess) return cuda_fail(err, "task scan launch");
     return DBQ_OK;

@@ -211,9 +211,10 @@ struct QueryTask {
     Hit* hits;                  // [k]
 };
 size_t scan_tasks_smem(bool sparse);
-// items[i] = (task, slice); next_item is a device counter (cleared here);
-// any_sparse: some task has support lists.
-cudaError_t launch_scan_tasks(const QueryTask* tasks, const int2* items, int nitems,
+// items[i] = (task, slice), every slice of the ntasks tasks once; next_item
+// is a device counter (cleared here); any_sparse: some task has support
+// lists, and the items are then re-ordered in place, costliest first.
+cudaError_t launch_scan_tasks(const QueryTask* tasks, int ntasks, int2* items, int nitems,
                               unsigned int* next_item, int grid, bool any_sparse,
                               cudaStream_t stream);
 

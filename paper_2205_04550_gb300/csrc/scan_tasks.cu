@@ -9,6 +9,13 @@
 // (dense, or restricted to the patient's support lists), keeps a running
 // top-k, publishes it to the query's scratch row; the last item of a query
 // (per-query atomic ticket, no spinning) merges the slices into its k hits.
+//
+// The host splits queries into slices in proportion to their databases'
+// dense bytes.  A sparse query reads only its patient's support, which the
+// host does not know when it enqueues the launch (the support lists are
+// built on the device just before), and supports differ thirty-fold; for
+// launches with sparse queries a one-CTA kernel therefore re-orders the
+// items on the device, longest first, before the scan starts.
 #include "kernels.h"
 #include "scan_core.cuh"
 #include "topk.cuh"
@@ -115,6 +122,45 @@ scan_tasks_kernel(const QueryTask* __restrict__ tasks, const int2* __restrict__ 
     }
 }
 
+// Power-of-two class of an item's cost: its entries times the 16-byte
+// words it reads per entry (both planes' support, or both whole planes).
+__device__ __forceinline__ int cost_class(const QueryTask& t)
+{
+    const uint64_t per_entry = t.sup_list ? (uint64_t)t.sup_len[0] + t.sup_len[1]
+                                          : 2ull * (uint64_t)t.wp4;
+    const uint64_t entries = (uint64_t)((t.n + t.slices - 1) / t.slices);
+    return 63 - __clzll((long long)(per_entry * entries + 1));
+}
+
+// Rewrites the item list with the items of the costliest classes first (an
+// approximate longest-processing-time order; within a class the order is
+// that of the atomic cursor, which the results do not depend on: hits are
+// ordered by score and index).  One CTA.
+__global__ void order_items_kernel(const QueryTask* __restrict__ tasks, int ntasks,
+                                   int2* __restrict__ items)
+{
+    __shared__ unsigned int hist[64];
+    __shared__ unsigned int cursor[64];
+    if (threadIdx.x < 64) hist[threadIdx.x] = 0u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntasks; t += blockDim.x)
+        atomicAdd(&hist[cost_class(tasks[t])], (unsigned int)tasks[t].slices);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned int run = 0;
+        for (int b = 63; b >= 0; --b) {
+            cursor[b] = run;
+            run += hist[b];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ntasks; t += blockDim.x) {
+        const int sl = tasks[t].slices;
+        const unsigned int pos = atomicAdd(&cursor[cost_class(tasks[t])], (unsigned int)sl);
+        for (int j = 0; j < sl; ++j) items[pos + j] = make_int2(t, j);
+    }
+}
+
 }  // namespace
 
 size_t scan_tasks_smem(bool sparse)
@@ -123,11 +169,16 @@ size_t scan_tasks_smem(bool sparse)
            (sparse ? kSupportCacheBytes : 0);
 }
 
-cudaError_t launch_scan_tasks(const QueryTask* tasks, const int2* items, int nitems,
+cudaError_t launch_scan_tasks(const QueryTask* tasks, int ntasks, int2* items, int nitems,
                               unsigned int* next_item, int grid, bool any_sparse,
                               cudaStream_t stream)
 {
     if (nitems <= 0) return cudaSuccess;
+    if (any_sparse) {
+        order_items_kernel<<<1, 1024, 0, stream>>>(tasks, ntasks, items);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     const size_t smem = scan_tasks_smem(any_sparse);
     auto kern = any_sparse ? scan_tasks_kernel<true> : scan_tasks_kernel<false>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,

@@ -71,8 +71,11 @@ def test_plan_two_resolutions(torch, two_dbs, sparse, items_per_sm):
     d1.set_sparse(False)
 
 
-def test_plan_captured_in_cuda_graph_and_replayed(torch, two_dbs):
+@pytest.mark.parametrize("sparse", [False, True])
+def test_plan_captured_in_cuda_graph_and_replayed(torch, two_dbs, sparse):
     (d1, v1), (d2, v2) = two_dbs
+    d1.set_sparse(sparse)
+    d2.set_sparse(sparse)
     rng = np.random.default_rng(7)
     nq, k = 6, 10
     which = [0, 1, 0, 1, 1, 0]
@@ -100,6 +103,49 @@ def test_plan_captured_in_cuda_graph_and_replayed(torch, two_dbs):
             for q, (p, w) in enumerate(zip(pats, which)):
                 vols = v1 if w == 0 else v2
                 assert_hits_equal(got[q], oracle.query(vols, p, T1, T2, k), k)
+    d1.set_sparse(False)
+    d2.set_sparse(False)
+
+
+def _box_patient(rng, shape, frac):
+    """A patient whose masks fill a random box holding about frac of the grid."""
+    nx, ny, nz = shape
+    p = np.zeros((nz, ny, nx), np.float32)
+    d = [max(1, int(n * frac ** (1 / 3))) for n in (nz, ny, nx)]
+    o = [int(rng.integers(0, n - dd + 1)) for n, dd in zip((nz, ny, nx), d)]
+    p[o[0]:o[0] + d[0], o[1]:o[1] + d[1], o[2]:o[2] + d[2]] = rng.random(d, dtype=np.float32)
+    return p
+
+
+def test_plan_sparse_items_ordered_by_support(torch, two_dbs):
+    """Sparse queries whose supports range from empty to the whole grid, with
+    dense queries in the same launch: the items are re-ordered on the device
+    by cost before the scan; every hit list stays the oracle's."""
+    (d1, v1), (d2, v2) = two_dbs
+    d1.set_sparse(True)
+    rng = np.random.default_rng(11)
+    fracs = [0.0, 1.0, 0.001, 0.01, 0.05, 0.2, 0.5, 0.8] * 3
+    pats = [_box_patient(rng, v1.shape[1:][::-1], f) for f in fracs]
+    pats[0] = np.zeros(v1.shape[1:], np.float32)
+    pats[1] = np.ones(v1.shape[1:], np.float32)
+    pats += _patients(rng, v2, 9)
+    which = [0] * len(fracs) + [1] * 9
+    perm = rng.permutation(len(pats))
+    pats = [pats[i] for i in perm]
+    which = [which[i] for i in perm]
+    k = 12
+    with Plan([d1, d2], len(pats), k) as plan:
+        for ips in (2, 16):
+            plan.set_items_per_sm(ips)
+            dev = [torch.from_numpy(p).cuda() for p in pats]
+            hits = torch.zeros((len(pats), k * 40), dtype=torch.uint8, device="cuda")
+            plan.query(which, dev, hits)
+            torch.cuda.synchronize()
+            got = hits.cpu().numpy().view(_dbq.HIT_DTYPE)
+            for q, (p, w) in enumerate(zip(pats, which)):
+                vols = v1 if w == 0 else v2
+                assert_hits_equal(got[q], oracle.query(vols, p, T1, T2, k), k)
+    d1.set_sparse(False)
 
 
 def test_plan_errors(torch, two_dbs):
