@@ -1524,8 +1524,13 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
             t.scratch = p->scratch + (size_t)(slot + i) * p->max_slices * p->k;
             t.ticket = p->tickets + slot + i;
             t.hits = reinterpret_cast<dbq::Hit*>(hits_dev) + (size_t)q * p->k;
-            for (int j = 0; j < sl; ++j) p->items_host[nitems++] = make_int2(slot + i, j);
         }
+        // slice-major: the same entry slice of every query of this database
+        // in consecutive items, so CTAs that run them at the same time read
+        // those entries from HBM once and share them through L2
+        const int gsl = p->tasks_host[slot].slices;      // equal within a database
+        for (int j = 0; j < gsl; ++j)
+            for (int i = 0; i < cnt; ++i) p->items_host[nitems++] = make_int2(slot + i, j);
         word_off += (size_t)cnt * 2 * db->wp;
         sup_off += (size_t)cnt * 2 * db->wp4;
         slot += cnt;

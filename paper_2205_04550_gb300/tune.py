@@ -16,7 +16,7 @@ import threading
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(_HERE, "_build", "autotune.json")
-CANDIDATES = (1, 2, 4, 8, 16, 32)
+CANDIDATES = (1, 2, 4, 8, 16, 32, 64)
 _lock = threading.Lock()
 
 
