@@ -789,7 +789,10 @@ def run_plan_mix(args, wl, torch):
                        "queries_per_db": [which.count(0), which.count(1)],
                        "l2": "inputs larger than L2 (32.8 GB of packed databases); no flush"},
             "dense": dense, "sparse": results["sparse"],
-            "gpu_launches": 3 * args.steps}
+            # per dense launch: a patient-packing kernel per database, and for
+            # each database with >= 16 queries the tensor-core contraction and
+            # its selection kernel (every database here has more)
+            "gpu_launches": 3 * len(wl["mix"]) * args.steps}
     for d in dbs:
         d.close()
     if rank == 0:

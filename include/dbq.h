@@ -57,7 +57,7 @@ enum dbq_status {
     DBQ_ENOMEM = -2,   /* device or host allocation failed                     */
     DBQ_ESTATE = -3,   /* call not valid in the handle's state (e.g. unbuilt)  */
     DBQ_ECUDA = -4,    /* a CUDA runtime call or a kernel launch failed         */
-    DBQ_ETIMEOUT = -5, /* a bounded device wait of the prefilter GEMM gave up  */
+    DBQ_ETIMEOUT = -5, /* a bounded device wait of a tensor-core kernel gave up  */
     DBQ_ERANGE = -6    /* k or an index outside [0, N]                          */
 };
 
@@ -271,6 +271,14 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
  *                 built, and outlive the plan.  1 <= k <= 1024.
  * db_plan_set     DBQ_PLAN_ITEMS_PER_SM: work items (query slices) per SM
  *                 of one launch (default 4; chosen by the autotuner).
+ *                 DBQ_PLAN_TC_MIN_QUERIES: a database queried by at least
+ *                 this many dense (not DBQ_OPT_SPARSE) queries in one call,
+ *                 with V <= 2^24 voxels, is scanned for all of them at once
+ *                 as a contraction on the tensor cores (the intersections
+ *                 of Section 2.3 as 0/1 dot products over the voxels, exact
+ *                 in binary32; up to 128 queries per pass), then scored and
+ *                 ranked per query -- the same hits as the CUDA-core loop.
+ *                 Default 16; 0 keeps every query on the CUDA-core loop.
  * db_plan_query   patients_dev[nq] device pointers (kind DBQ_F32 / DBQ_F16
  *                 volumes or DBQ_BITS planes of the query's database),
  *                 t1/t2 per query or NULL (NaN = build thresholds; others
@@ -279,14 +287,19 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
  *                 plan's host-side tables are rewritten by each call: a call
  *                 outside stream capture waits until the previous call's
  *                 tables have been copied to the device.
+ * db_plan_status  synchronises `stream` and reports whether a bounded wait
+ *                 of the tensor-core path has timed out since the last call
+ *                 (DBQ_ETIMEOUT, and the affected hits are not valid) or
+ *                 not (DBQ_OK); clears the condition.  Not capturable.
  * db_plan_destroy frees the plan (NULL accepted).
  */
 typedef struct dbq_plan dbq_plan;
-enum dbq_plan_param { DBQ_PLAN_ITEMS_PER_SM = 1 };
+enum dbq_plan_param { DBQ_PLAN_ITEMS_PER_SM = 1, DBQ_PLAN_TC_MIN_QUERIES = 2 };
 int db_plan_create(dbq_plan** out, dbq_db* const* dbs, int ndb, int max_queries, int k);
 int db_plan_set(dbq_plan* plan, int param, int64_t value);
 int db_plan_query(dbq_plan* plan, const int* db_of_query, int nq, const void* const* patients_dev,
                   int kind, const float* t1, const float* t2, dbq_hit* hits_dev, void* stream);
+int db_plan_status(dbq_plan* plan, void* stream);
 int db_plan_destroy(dbq_plan* plan);
 
 /*

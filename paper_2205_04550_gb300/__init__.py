@@ -17,16 +17,17 @@ from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_FLAG_SKETCH,
                    db_get_masks, db_info, db_last_error, db_load_volumes, db_prefilter,
                    db_prepare_patient, db_query, db_query_async, db_query_batch,
                    db_query_prepared, db_scan_counts, db_scan_packed_noalloc, db_set_option,
-                   db_stage_times, DBQ_OPT_SPARSE, DBQ_PLAN_ITEMS_PER_SM, db_plan_create,
-                   db_plan_set, db_plan_query, db_plan_destroy, db_create_downsampled)
+                   db_stage_times, DBQ_OPT_SPARSE, DBQ_PLAN_ITEMS_PER_SM, DBQ_PLAN_TC_MIN_QUERIES,
+                   db_plan_create, db_plan_set, db_plan_query, db_plan_status, db_plan_destroy,
+                   db_create_downsampled)
 
 __all__ = ["Database", "ForwardModel", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_F16", "DBQ_BITS",
            "DBQ_STORE_BITS", "DBQ_STORE_F16", "DBQ_FLAG_EMBED", "DBQ_FLAG_SKETCH",
            "DBQ_MODE_EXACT", "DBQ_MODE_EMBED_BF16", "DBQ_MODE_EMBED_FP8", "DBQ_MODE_HASH",
            "SKETCH_DIMS", "db_get_codes", "db_query_batch", "db_prefilter",
            "db_get_embeddings", "db_scan_packed_noalloc", "db_set_option", "db_stage_times",
-           "DBQ_OPT_SPARSE", "DBQ_PLAN_ITEMS_PER_SM", "Plan", "db_plan_create",
-           "db_plan_set", "db_plan_query", "db_plan_destroy", "db_create_downsampled", "db_create", "db_load_volumes",
+           "DBQ_OPT_SPARSE", "DBQ_PLAN_ITEMS_PER_SM", "DBQ_PLAN_TC_MIN_QUERIES", "Plan",
+           "db_plan_create", "db_plan_set", "db_plan_query", "db_plan_status", "db_plan_destroy", "db_create_downsampled", "db_create", "db_load_volumes",
            "db_build_masks", "db_query", "db_query_async", "db_prepare_patient",
            "db_query_prepared", "db_scan_counts", "db_get_masks",
            "db_info", "db_destroy", "db_last_error"]
@@ -198,6 +199,14 @@ class Plan:
 
     def set_items_per_sm(self, value: int):
         db_plan_set(self.handle, DBQ_PLAN_ITEMS_PER_SM, int(value))
+
+    def set_tc_min_queries(self, value: int):
+        """Dense queries per database from which that database is scanned for
+        all of them at once on the tensor cores (0 = never)."""
+        db_plan_set(self.handle, DBQ_PLAN_TC_MIN_QUERIES, int(value))
+
+    def status(self, stream=None):
+        db_plan_status(self.handle, stream)
 
     def query(self, db_of_query, patients_dev, hits_dev, kind=None, stream=None, keep=None):
         db_plan_query(self.handle, db_of_query, patients_dev, hits_dev, kind, stream=stream,

@@ -38,6 +38,7 @@ SKETCH_DIMS = 4096
 DBQ_OPT_SPARSE = 1
 
 DBQ_PLAN_ITEMS_PER_SM = 1
+DBQ_PLAN_TC_MIN_QUERIES = 2
 
 DBQ_MODE_EXACT = 0
 DBQ_MODE_EMBED_BF16 = 1
@@ -102,6 +103,7 @@ _SIGS = [
                                       ctypes.c_int]),
     ("db_plan_set", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
     ("db_plan_query", ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]),
+    ("db_plan_status", ctypes.c_int, [_P, _P]),
     ("db_plan_destroy", ctypes.c_int, [_P]),
     ("db_create_downsampled", ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.c_int]),
     ("db_scan_packed_noalloc", ctypes.c_int, [_P, _P, ctypes.c_int64, ctypes.c_int64, _P, _P,
@@ -340,6 +342,12 @@ def db_create_downsampled(src: int, factor: int) -> int:
     h = _P()
     _check(load().db_create_downsampled(ctypes.byref(h), src, factor))
     return h.value
+
+
+def db_plan_status(plan: int, stream=None):
+    """Raises DbqError (DBQ_ETIMEOUT) if a tensor-core wait of the plan has
+    timed out since the last check; synchronises the stream."""
+    _check(load().db_plan_status(plan, _stream(stream)))
 
 
 def db_plan_destroy(plan: int):

@@ -612,8 +612,15 @@ struct dbq_plan {
     const void** ptrs_host = nullptr;       // pinned
     cudaEvent_t copied = nullptr;
     bool copy_pending = false;
+    // tensor-core path for databases queried by many dense queries at once
+    int tc_min = 16;                  // queries per database that switch it on (0 = never)
+    int tc_rows = 0;                  // queries per tensor-core launch (0 = unavailable)
+    uint2* tc_counts = nullptr;       // [tc_rows][largest n] intersections
+    int* tc_status = nullptr;         // nonzero after a timed-out wait
     ~dbq_plan()
     {
+        cudaFree(tc_counts);
+        cudaFree(tc_status);
         cudaFree(planes);
         cudaFree(pcount);
         cudaFree(sup);
@@ -1407,7 +1414,23 @@ int db_plan_create(dbq_plan** out, dbq_db* const* dbs, int ndb, int max_queries,
         delete p;
         return fail(DBQ_ENOMEM, "plan allocation failed");
     }
+    // counts of the tensor-core path: at most 1 GiB, for 16 to 128 queries
+    // per launch; databases beyond 2^24 voxels stay on the CUDA-core path
+    int64_t tc_n = 0;
+    for (const dbq_db* db : p->dbs)
+        if (db->v <= (int64_t)1 << 24) tc_n = std::max<int64_t>(tc_n, db->n);
+    if (tc_n > 0) {
+        int rows = std::min(max_queries, dbq::tc_scan_max_queries());
+        while (rows > 16 && (size_t)rows * tc_n * sizeof(uint2) > ((size_t)1 << 30)) rows /= 2;
+        if ((size_t)rows * tc_n * sizeof(uint2) <= ((size_t)1 << 30) &&
+            dalloc(&p->tc_counts, (size_t)rows * tc_n * sizeof(uint2)) &&
+            dalloc(&p->tc_status, 16))
+            p->tc_rows = rows;
+        else
+            cudaGetLastError();
+    }
     cudaError_t err = cudaMemset(p->tickets, 0, q * 4);
+    if (err == cudaSuccess && p->tc_status) err = cudaMemset(p->tc_status, 0, 16);
     if (err == cudaSuccess) err = cudaEventCreateWithFlags(&p->copied, cudaEventDisableTiming);
     if (err == cudaSuccess) err = cudaDeviceSynchronize();
     if (err != cudaSuccess) {
@@ -1424,6 +1447,12 @@ int db_plan_set(dbq_plan* plan, int param, int64_t value)
     if (param == DBQ_PLAN_ITEMS_PER_SM) {
         if (value < 1 || value > 64) return fail(DBQ_EINVAL, "items per SM must be in [1, 64]");
         plan->items_per_sm = (int)value;
+        return DBQ_OK;
+    }
+    if (param == DBQ_PLAN_TC_MIN_QUERIES) {
+        if (value < 0 || value > 65535)
+            return fail(DBQ_EINVAL, "tensor-core query threshold must be in [0, 65535]");
+        plan->tc_min = (int)value;
         return DBQ_OK;
     }
     return fail(DBQ_EINVAL, "unknown plan parameter %d", param);
@@ -1461,12 +1490,27 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
     for (int q = 0; q < nq; ++q) order[q] = q;
     std::stable_sort(order.begin(), order.end(),
                      [&](int a, int b) { return db_of_query[a] < db_of_query[b]; });
+    // databases whose dense queries go to the tensor-core contraction
+    std::vector<int> per_db((size_t)ndb, 0);
+    for (int q = 0; q < nq; ++q) ++per_db[db_of_query[q]];
+    std::vector<char> use_tc((size_t)ndb, 0);
+    for (int d = 0; d < ndb; ++d) {
+        const dbq_db* db = p->dbs[d];
+        use_tc[d] = p->tc_rows > 0 && p->tc_min > 0 && per_db[d] >= p->tc_min && !db->sparse &&
+                    db->v <= ((int64_t)1 << 24);
+    }
     // work-item budget: items_per_sm * SMs, shared in proportion to bytes
     double total = 0;
     for (int q = 0; q < nq; ++q) {
         const dbq_db* db = p->dbs[db_of_query[q]];
-        total += (double)db->n * db->wp4;
+        if (!use_tc[db_of_query[q]]) total += (double)db->n * db->wp4;
     }
+    struct TcGroup {
+        const dbq_db* db;
+        int slot, cnt;
+        const uint32_t* qplanes;
+    };
+    std::vector<TcGroup> tc_groups;
     const double budget = (double)p->items_per_sm * p->sms;
     int nitems = 0;
     size_t word_off = 0, sup_off = 0;
@@ -1513,7 +1557,9 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
             t.chunk4 = db->chunk4;
             t.nchunks = db->nchunks;
             t.k = p->k;
-            int sl = (int)std::lround(budget * ((double)db->n * db->wp4) / total);
+            int sl = 1;
+            if (!use_tc[d] && total > 0)
+                sl = (int)std::lround(budget * ((double)db->n * db->wp4) / total);
             sl = std::max(1, std::min(sl, p->max_slices));
             if ((int64_t)sl > db->n) sl = (int)db->n;
             t.slices = sl;
@@ -1525,12 +1571,19 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
             t.ticket = p->tickets + slot + i;
             t.hits = reinterpret_cast<dbq::Hit*>(hits_dev) + (size_t)q * p->k;
         }
-        // slice-major: the same entry slice of every query of this database
-        // in consecutive items, so CTAs that run them at the same time read
-        // those entries from HBM once and share them through L2
-        const int gsl = p->tasks_host[slot].slices;      // equal within a database
-        for (int j = 0; j < gsl; ++j)
-            for (int i = 0; i < cnt; ++i) p->items_host[nitems++] = make_int2(slot + i, j);
+        if (use_tc[d]) {
+            // no work items: the group runs as a contraction after the scan
+            for (int i = 0; i < cnt; ++i) p->tasks_host[slot + i].slices = 0;
+            tc_groups.push_back({db, slot, cnt, gplanes});
+        } else {
+            // slice-major: the same entry slice of every query of this
+            // database in consecutive items, so CTAs that run them at the
+            // same time read those entries from HBM once and share them
+            // through L2
+            const int gsl = p->tasks_host[slot].slices;      // equal within a database
+            for (int j = 0; j < gsl; ++j)
+                for (int i = 0; i < cnt; ++i) p->items_host[nitems++] = make_int2(slot + i, j);
+        }
         word_off += (size_t)cnt * 2 * db->wp;
         sup_off += (size_t)cnt * 2 * db->wp4;
         slot += cnt;
@@ -1549,6 +1602,41 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
     cudaError_t err = dbq::launch_scan_tasks(p->tasks_dev, nq, p->items_dev, nitems, p->counter,
                                              p->sms, any_sparse, s);
     if (err != cudaSuccess) return cuda_fail(err, "task scan launch");
+    for (const TcGroup& tg : tc_groups) {
+        for (int c0 = 0; c0 < tg.cnt; c0 += p->tc_rows) {
+            const int nqc = std::min(p->tc_rows, tg.cnt - c0);
+            dbq::TcScanArgs ta;
+            ta.planes = tg.db->planes;
+            ta.n = tg.db->n;
+            ta.wp = tg.db->wp;
+            ta.qplanes = tg.qplanes + (size_t)c0 * 2 * tg.db->wp;
+            ta.nq = nqc;
+            ta.counts = p->tc_counts;
+            ta.status = p->tc_status;
+            err = dbq::launch_tc_scan(ta, p->sms, s);
+            if (err != cudaSuccess) return cuda_fail(err, "tensor-core scan launch");
+            err = dbq::launch_tc_select(p->tasks_dev, tg.slot + c0, nqc, p->tc_counts, tg.db->n, s);
+            if (err != cudaSuccess) return cuda_fail(err, "tensor-core selection launch");
+        }
+    }
+    return DBQ_OK;
+}
+
+int db_plan_status(dbq_plan* p, void* stream)
+{
+    if (!p) return fail(DBQ_EINVAL, "plan is NULL");
+    DeviceGuard guard(p->device);
+    if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", p->device);
+    if (!p->tc_status) return DBQ_OK;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int st = 0;
+    DBQ_CUDA(cudaMemcpyAsync(&st, p->tc_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    DBQ_CUDA(cudaStreamSynchronize(s));
+    if (st != 0) {
+        DBQ_CUDA(cudaMemsetAsync(p->tc_status, 0, sizeof(int), s));
+        DBQ_CUDA(cudaStreamSynchronize(s));
+        return fail(DBQ_ETIMEOUT, "a tensor-core wait timed out (code %d)", st);
+    }
     return DBQ_OK;
 }
 

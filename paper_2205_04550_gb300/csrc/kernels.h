@@ -211,6 +211,24 @@ struct QueryTask {
     Hit* hits;                  // [k]
 };
 size_t scan_tasks_smem(bool sparse);
+
+// ---- many exact queries against one database on the tensor cores
+struct TcScanArgs {
+    const uint32_t* planes;     // database [n][2][wp] bit planes (16-byte aligned)
+    int64_t n;
+    int64_t wp;                 // words per plane, a multiple of 4
+    const uint32_t* qplanes;    // patients [nq][2][wp] bit planes (16-byte aligned)
+    int nq;                     // 1 .. tc_scan_max_queries()
+    uint2* counts;              // out: [nq][n] (I_1, I_2)
+    int* status;                // device word: nonzero after a timed-out wait
+};
+int tc_scan_max_queries();
+// Exact only while V <= 2^24 (the binary32 accumulators count voxels).
+cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream);
+// Scores and top-k of patients tasks[task0 .. task0 + nq) from counts [nq][n]
+// (mask sizes, k and the hit output taken from each task).
+cudaError_t launch_tc_select(const QueryTask* tasks, int task0, int nq, const uint2* counts,
+                             int64_t n, cudaStream_t stream);
 // items[i] = (task, slice), every slice of the ntasks tasks once; next_item
 // is a device counter (cleared here); any_sparse: some task has support
 // lists, and the items are then re-ordered in place, costliest first.

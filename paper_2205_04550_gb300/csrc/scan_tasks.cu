@@ -144,7 +144,8 @@ __global__ void order_items_kernel(const QueryTask* __restrict__ tasks, int ntas
     if (threadIdx.x < 64) hist[threadIdx.x] = 0u;
     __syncthreads();
     for (int t = threadIdx.x; t < ntasks; t += blockDim.x)
-        atomicAdd(&hist[cost_class(tasks[t])], (unsigned int)tasks[t].slices);
+        if (tasks[t].slices > 0)
+            atomicAdd(&hist[cost_class(tasks[t])], (unsigned int)tasks[t].slices);
     __syncthreads();
     if (threadIdx.x == 0) {
         unsigned int run = 0;
@@ -156,6 +157,7 @@ __global__ void order_items_kernel(const QueryTask* __restrict__ tasks, int ntas
     __syncthreads();
     for (int t = threadIdx.x; t < ntasks; t += blockDim.x) {
         const int sl = tasks[t].slices;
+        if (sl <= 0) continue;              // a task without items (tensor-core path)
         const unsigned int pos = atomicAdd(&cursor[cost_class(tasks[t])], (unsigned int)sl);
         for (int j = 0; j < sl; ++j) items[pos + j] = make_int2(t, j);
     }

@@ -168,3 +168,102 @@ def test_plan_errors(torch, two_dbs):
             plan.query([2], [p], hits)                      # no such database
         with pytest.raises(DbqError):
             _dbq.db_plan_query(plan.handle, [0], [p], hits, t1=[0.5], t2=[0.25])
+        with pytest.raises(DbqError):
+            plan.set_tc_min_queries(-1)
+        plan.status()                                       # nothing timed out
+
+
+def _run_plan(torch, dbs, which, pats, k, tc_min, items_per_sm=4):
+    with Plan(dbs, len(pats), k) as plan:
+        plan.set_items_per_sm(items_per_sm)
+        plan.set_tc_min_queries(tc_min)
+        dev = [torch.from_numpy(p).cuda() for p in pats]
+        hits = torch.zeros((len(pats), k * 40), dtype=torch.uint8, device="cuda")
+        plan.query(which, dev, hits)
+        plan.status()
+        torch.cuda.synchronize()
+        return hits.cpu().numpy().view(_dbq.HIT_DTYPE).copy()
+
+
+def test_plan_tensor_core_path_matches_oracle_and_cuda_cores(torch, two_dbs):
+    """Every dense query on the tensor-core contraction (threshold 1): hits
+    equal to the oracle's and bit-identical to the CUDA-core loop's."""
+    (d1, v1), (d2, v2) = two_dbs
+    rng = np.random.default_rng(21)
+    pats = _patients(rng, v1, 7) + _patients(rng, v2, 19)
+    pats[0] = np.zeros_like(pats[0])                 # empty masks: Dice 1 only for empty entries
+    pats[8] = np.ones_like(pats[8])
+    which = [0] * 7 + [1] * 19
+    perm = rng.permutation(len(pats))
+    pats = [pats[i] for i in perm]
+    which = [which[i] for i in perm]
+    k = 20
+    tc = _run_plan(torch, [d1, d2], which, pats, k, tc_min=1)
+    cc = _run_plan(torch, [d1, d2], which, pats, k, tc_min=0)
+    assert tc.tobytes() == cc.tobytes()
+    for q, (p, w) in enumerate(zip(pats, which)):
+        vols = v1 if w == 0 else v2
+        assert_hits_equal(tc[q], oracle.query(vols, p, T1, T2, k), k)
+
+
+@pytest.mark.parametrize("shape,n", [((30, 17, 11), 300), ((128, 16, 8), 129)])
+def test_plan_tensor_core_ragged_sizes(torch, shape, n):
+    """Grids whose voxel count is not a multiple of the 256-voxel K-slice,
+    entry counts one past a 128-entry tile, more than 128 queries (two
+    passes of the contraction over the database), and a sparse database
+    next to the dense one in the same call."""
+    vols, _ = random_db(shape, n, seed=n)
+    rng = np.random.default_rng(n)
+    pats = _patients(rng, vols, 131)
+    v3, _ = random_db((16, 16, 16), 200, seed=5)
+    with Database(shape, n, DBQ_STORE_BITS, T1, T2) as db, \
+            Database((16, 16, 16), 200, DBQ_STORE_BITS, T1, T2) as ds:
+        db.load(0, vols)
+        db.build()
+        ds.load(0, v3)
+        ds.build()
+        ds.set_sparse(True)
+        sp = _patients(rng, v3, 20)
+        allp = pats + sp
+        which = [0] * len(pats) + [1] * len(sp)
+        k = 9
+        tc = _run_plan(torch, [db, ds], which, allp, k, tc_min=16)
+        cc = _run_plan(torch, [db, ds], which, allp, k, tc_min=0)
+    assert tc.tobytes() == cc.tobytes()
+    for q in list(range(0, 131, 13)) + [130]:
+        assert_hits_equal(tc[q], oracle.query(vols, pats[q], T1, T2, k), k)
+    for q in (0, 19):
+        assert_hits_equal(tc[131 + q], oracle.query(v3, sp[q], T1, T2, k), k)
+
+
+def test_plan_tensor_core_graph_replay(torch, two_dbs):
+    (d1, v1), (d2, v2) = two_dbs
+    rng = np.random.default_rng(3)
+    nq, k = 24, 6
+    which = [1] * 20 + [0] * 4
+    shapes = [v1.shape[1:] if w == 0 else v2.shape[1:] for w in which]
+    slots = [torch.zeros(sh, dtype=torch.float32, device="cuda") for sh in shapes]
+    hits = torch.zeros((nq, k * 40), dtype=torch.uint8, device="cuda")
+    with Plan([d1, d2], nq, k) as plan:
+        plan.set_tc_min_queries(16)                 # database 1 on the tensor cores
+        keep = []
+        plan.query(which, slots, hits, keep=keep)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            with torch.cuda.graph(g, stream=s):
+                plan.query(which, slots, hits, keep=keep)
+        torch.cuda.synchronize()
+        for rep in range(2):
+            pats = [(_patients(rng, v1, 1) if w == 0 else _patients(rng, v2, 1))[0] for w in which]
+            for sl, p in zip(slots, pats):
+                sl.copy_(torch.from_numpy(p))
+            g.replay()
+            torch.cuda.synchronize()
+            plan.status()
+            got = hits.cpu().numpy().view(_dbq.HIT_DTYPE)
+            for q, (p, w) in enumerate(zip(pats, which)):
+                vols = v1 if w == 0 else v2
+                assert_hits_equal(got[q], oracle.query(vols, p, T1, T2, k), k)
