@@ -212,7 +212,13 @@ tc_scan_kernel(const TcScanArgs a, int npad, int nstages)
             int s = 0;
             uint32_t phase = 0;      // of the stage ring (flips when s wraps)
             bool ok = true;
-            const uint32_t stage0 = smem_u32(stages);
+            // descriptors differ only in the start-address field (address / 16,
+            // below 2^14 for any shared-memory address), so they are the first
+            // stage's descriptor plus constant offsets
+            const uint64_t desc0 = sw128_desc(smem_u32(stages));
+            const uint64_t b_off = (uint64_t)(kTcABytes >> 4);
+            const uint64_t b_col = (uint64_t)(npad * 128 >> 4);
+            uint64_t sdesc = desc0;
             for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
                 const int buf = (int)(tl & 1);
                 if (!mbar_wait(acc_free0 + 8 * buf, (uint32_t)(((tl >> 1) & 1) ^ 1), abort_flag)) {
@@ -228,21 +234,22 @@ tc_scan_kernel(const TcScanArgs a, int npad, int nstages)
                             break;
                         }
                         tc_fence_after();
-                        const uint32_t sa = stage0 + (uint32_t)(s * sbytes);
-                        const uint32_t sb = sa + kTcABytes;
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
 #pragma unroll
                             for (int kk = 0; kk < 4; ++kk) {
-                                umma_f8(d_tmem, sw128_desc(sa + h * kTcColBytes + 32 * kk),
-                                        sw128_desc(sb + (uint32_t)(h * npad * 128) + 32 * kk),
-                                        idesc, (kc > 0 || h > 0 || kk > 0) ? 1u : 0u);
+                                // K step of 32 bytes: +2 in the address field
+                                umma_f8(d_tmem, sdesc + (uint64_t)(h * (kTcColBytes >> 4) + 2 * kk),
+                                        sdesc + b_off + h * b_col + (uint64_t)(2 * kk), idesc,
+                                        (kc > 0 || h > 0 || kk > 0) ? 1u : 0u);
                             }
                         }
                         umma_commit(empty0 + 8 * s);
+                        sdesc += sbytes >> 4;
                         if (++s == nstages) {
                             s = 0;
                             phase ^= 1u;
+                            sdesc = desc0;
                         }
                     }
                 }
