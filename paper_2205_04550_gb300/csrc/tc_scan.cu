@@ -3,36 +3,41 @@
 //
 // For Q patients and N entries the intersections I_k(q, e) = |P_k(q) n E_k(e)|
 // are dot products of 0/1 vectors over the V voxels: one dense contraction
-// [N x V] . [V x Q] per segmentation.  The masks are stored as bits, which
-// the tensor cores cannot read, so converter warps expand each K-slice of
-// 256 voxels of 128 entries and of the Q patients into E4M3 bytes (2.0 for a
-// set bit, 0 otherwise) in the 128-byte-swizzled K-major layout of a tcgen05
-// shared-memory operand, and one thread issues tcgen05.mma (kind::f8f6f4,
-// M = 128 entries, N = Q rounded up to 16, K = 32 per instruction) with
-// binary32 accumulators in tensor memory.  Every product is 0 or 4 and every
-// partial sum 4 times an integer no larger than V <= 2^24, so the
-// accumulators hold 4 x the exact counts (2.0 is 0x40: one bit per byte,
-// which saves a multiply per output word over 1.0 = 0x38).
+// [Q x V] . [V x N] per segmentation.  The masks are stored as bits, which
+// the tensor cores cannot read, so converter warps expand each K-slice of 128
+// voxels of the patients' rows and of 256 entry rows into E4M3 bytes (2.0 for
+// a set bit, 0 otherwise) in the 128-byte-swizzled K-major layout of tcgen05
+// shared-memory operands, and one thread issues tcgen05.mma (kind::f8f6f4,
+// M = 128 patient rows -- the rows past Q are zero --, N = 256 entries,
+// K = 32 per instruction) with binary32 accumulators in tensor memory.  An
+// MMA instruction costs about the same for any N, so the entries, not the
+// few patients, take the N side.  Every product is 0 or 4 and every partial
+// sum 4 times an integer no larger than V <= 2^24, so the accumulators hold
+// 4 x the exact counts (2.0 is 0x40: one bit per byte, which saves a
+// multiply per output word over 1.0 = 0x38).
 //
-//   * one CTA per SM, persistent over 128-entry tiles (round-robin);
-//   * warps 6-21 (converters): thread t copies with cp.async the 16 bytes
-//     (128 voxels) of half a row of every K-slice -- an entry row for t <
-//     256, a patient row for 256 <= t < 256 + 2N -- four slices ahead,
-//     expands them into the stage's operand tiles and makes the stores
-//     visible to the tensor core (fence.proxy.async); one lane per warp then
-//     arrives on the stage's full barrier (a warp's stores are ordered before
-//     it by __syncwarp) and one lane per warp waits for a stage to be free;
-//   * the operand stages (as many as shared memory holds: 3 to 5) and the
-//     cp.async ring fill one CTA's shared memory;
-//   * warp 0 (one thread): per K-slice eight MMAs (two 128-byte swizzle
-//     columns x four K steps) into the tile's accumulator columns -- [0, N)
-//     for the first segmentation, [128, 128 + N) for the second -- of one of
-//     two TMEM buffers, so the epilogue of a tile overlaps the next tile's
-//     MMAs; its commits free the stage and, at the end of a tile, hand the
-//     buffer to the epilogue;
-//   * warps 2-5 (epilogue, one TMEM lane quarter each): tcgen05.ld the
-//     counts and store counts[q][e] = (I_1, I_2), coalesced over e;
+//   * work units are (256-entry tile, segmentation), round-robin over one
+//     persistent CTA per SM; each unit writes its own component of the
+//     counts, so no unit waits for another;
+//   * warps 6-17 (converters): thread t < 256 copies with cp.async the 16
+//     bytes (128 voxels) of entry row t of every K-slice, thread 256 + r
+//     those of patient row r < Q, four slices ahead, expands them into a
+//     4-stage ring of operand tiles and makes the stores visible to the
+//     tensor core (fence.proxy.async); one lane per warp then arrives on the
+//     stage's full barrier (the warp's stores ordered before it by
+//     __syncwarp), and one lane per warp waits for a stage to be free.  The
+//     patient rows past Q are cleared once at the start;
+//   * warp 0 (one thread): per K-slice four MMAs into the unit's 256
+//     accumulator columns in one of two TMEM buffers, so the epilogue of a
+//     unit overlaps the next unit's MMAs; its commits free the stage and, at
+//     the end of a unit, hand the buffer to the epilogue;
+//   * warps 2-5 (epilogue, one TMEM lane quarter each, lane = patient row):
+//     tcgen05.ld the counts of 16 entries at a time and store them into
+//     counts[q][e];
 //   * warp 1 allocates and frees the 512 TMEM columns.
+// The expanded operands pass through shared memory twice (converter stores,
+// tensor-core reads): about 24 bytes of shared-memory traffic per byte of
+// bits, which bounds this design near 8 bytes of bits per cycle per SM.
 // The mask sizes, binary64 scores and each patient's top-k follow in
 // tc_select_kernel.  Every mbarrier wait is bounded; on a timeout the CTA
 // records an error code in `status`, stops, drains its MMAs and copies and
@@ -44,35 +49,23 @@
 namespace dbq {
 namespace {
 
-constexpr int kTcM = 128;                    // entries per tile (TMEM lanes)
-constexpr int kTcMaxN = 128;                 // patients per launch
-constexpr int kTcMaxStages = 6;              // operand stages (as many as fit)
+constexpr int kTcQ = 128;                    // query rows of the MMA (M), zero-padded
+constexpr int kTcE = 256;                    // entries per tile (MMA N)
+constexpr int kTcMaxN = 128;                 // queries per launch
+constexpr int kTcStages = 4;
 constexpr int kTcAhead = 4;                  // K-slices in flight per converter thread
-constexpr int kTcConv = 512;                 // converter threads (warps 6-21)
+constexpr int kTcConv = kTcE + kTcQ;         // converter threads: 256 entry rows + 128 query rows
 constexpr int kTcConvWarps = kTcConv / 32;
-constexpr int kTcConv0 = 192;                // first converter thread
+constexpr int kTcConv0 = 192;
 constexpr int kTcThreads = kTcConv0 + kTcConv;
-constexpr int kTcSliceWords = 8;             // 256 voxels per K-slice and row
-constexpr int kTcColBytes = kTcM * 128;      // one 128-byte swizzle column of the A tile
-constexpr int kTcABytes = 2 * kTcColBytes;
-constexpr size_t kTcSmemMax = 232448;        // dynamic shared memory of one CTA
-
-__host__ __device__ constexpr size_t stage_bytes(int npad)
-{
-    return (size_t)kTcABytes + (size_t)npad * 256;
-}
+constexpr int kTcSliceWords = 4;             // 128 voxels per K-slice and row
+constexpr int kTcABytes = kTcQ * 128;        // query operand of a stage
+constexpr int kTcBBytes = kTcE * 128;        // entry operand of a stage
+constexpr int kTcStageBytes = kTcABytes + kTcBBytes;
 
 __host__ __device__ constexpr size_t ring_bytes() { return (size_t)kTcAhead * kTcConv * 16; }
 
-constexpr size_t kTcFixedBytes = 1024 + ring_bytes() + (2 * kTcMaxStages + 5) * 8 + 16;
-
-int stages_for(int npad)
-{
-    const int s = (int)((kTcSmemMax - kTcFixedBytes) / stage_bytes(npad));
-    return s < kTcMaxStages ? s : kTcMaxStages;
-}
-
-size_t smem_bytes(int npad) { return kTcFixedBytes + stages_for(npad) * stage_bytes(npad); }
+size_t smem_bytes() { return 1024 + (size_t)kTcStages * kTcStageBytes + ring_bytes() + (2 * kTcStages + 5) * 8 + 16; }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid)
 {
@@ -153,41 +146,47 @@ __device__ __forceinline__ uint32_t row_offset(int row)
     return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
-tc_scan_kernel(const TcScanArgs a, int npad, int nstages)
+__global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    const size_t sbytes = stage_bytes(npad);
-    unsigned char* stages = base;                                   // nstages x sbytes
-    unsigned char* ring = stages + nstages * sbytes;                // [kTcAhead][kTcConv] x 16 B
+    unsigned char* stages = base;                                  // kTcStages x (A | B)
+    unsigned char* ring = stages + (size_t)kTcStages * kTcStageBytes;   // [ahead][kTcConv] x 16 B
     uint64_t* bars = reinterpret_cast<uint64_t*>(ring + ring_bytes());
-    // bars: full[kTcMaxStages], empty[kTcMaxStages], acc_full[2], acc_free[2], drain
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcMaxStages + 5);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 5);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t ntiles = (a.n + kTcM - 1) / kTcM;
-    const int64_t my_tiles = ntiles > blockIdx.x ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t nk = (a.wp + kTcSliceWords - 1) / kTcSliceWords;   // K-slices per plane
-    const int64_t total = my_tiles * 2 * nk;                         // stages of this CTA
+    const int64_t ntiles = (a.n + kTcE - 1) / kTcE;
+    const int64_t nunits = ntiles * 2;                             // (tile, plane)
+    const int64_t my_units = nunits > blockIdx.x ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t nk = (a.wp + kTcSliceWords - 1) / kTcSliceWords;
+    const int64_t total = my_units * nk;
 
     const uint32_t full0 = smem_u32(bars);
-    const uint32_t empty0 = smem_u32(bars + kTcMaxStages);
-    const uint32_t acc_full0 = smem_u32(bars + 2 * kTcMaxStages);
-    const uint32_t acc_free0 = smem_u32(bars + 2 * kTcMaxStages + 2);
-    const uint32_t drain = smem_u32(bars + 2 * kTcMaxStages + 4);
+    const uint32_t empty0 = smem_u32(bars + kTcStages);
+    const uint32_t acc_full0 = smem_u32(bars + 2 * kTcStages);
+    const uint32_t acc_free0 = smem_u32(bars + 2 * kTcStages + 2);
+    const uint32_t drain = smem_u32(bars + 2 * kTcStages + 4);
 
+    // the query rows past nq stay zero in every stage: cleared once here
+    for (int i = threadIdx.x; i < kTcStages * (kTcABytes / 16); i += blockDim.x) {
+        const int st = i / (kTcABytes / 16), off = i % (kTcABytes / 16);
+        const int row = ((off * 16) / 1024) * 8 + ((off * 16) % 1024) / 128;   // row of this 16 B
+        if (row >= a.nq)
+            *reinterpret_cast<uint4*>(stages + (size_t)st * kTcStageBytes + off * 16) = make_uint4(0, 0, 0, 0);
+    }
+    fence_proxy_async();
     if (threadIdx.x == 0) {
-        for (int s = 0; s < nstages; ++s) {
-            mbar_init(full0 + 8 * s, kTcConvWarps);  // one lane of every converter warp
-            mbar_init(empty0 + 8 * s, 1);            // the MMA commit
+        for (int s = 0; s < kTcStages; ++s) {
+            mbar_init(full0 + 8 * s, kTcConvWarps);
+            mbar_init(empty0 + 8 * s, 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full0 + 8 * b, 1);
-            mbar_init(acc_free0 + 8 * b, 128);       // every epilogue thread
+            mbar_init(acc_free0 + 8 * b, 128);
         }
         mbar_init(drain, 1);
         *abort_flag = 0;
@@ -206,51 +205,39 @@ tc_scan_kernel(const TcScanArgs a, int npad, int nstages)
 
     if (warp == 0) {
         if (lane == 0) {
-            // D f32 (bit 4), A and B E4M3 (0), both K-major, N / 8, M / 16
+            // D f32, A and B E4M3, K-major, N = 256 entries, M = 128 query rows
             const uint32_t idesc =
-                (1u << 4) | ((uint32_t)(npad >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+                (1u << 4) | ((uint32_t)(kTcE >> 3) << 17) | ((uint32_t)(kTcQ >> 4) << 24);
             int s = 0;
-            uint32_t phase = 0;      // of the stage ring (flips when s wraps)
+            uint32_t phase = 0;
             bool ok = true;
-            // descriptors differ only in the start-address field (address / 16,
-            // below 2^14 for any shared-memory address), so they are the first
-            // stage's descriptor plus constant offsets
             const uint64_t desc0 = sw128_desc(smem_u32(stages));
             const uint64_t b_off = (uint64_t)(kTcABytes >> 4);
-            const uint64_t b_col = (uint64_t)(npad * 128 >> 4);
             uint64_t sdesc = desc0;
-            for (int64_t tl = 0; tl < my_tiles && ok; ++tl) {
-                const int buf = (int)(tl & 1);
-                if (!mbar_wait(acc_free0 + 8 * buf, (uint32_t)(((tl >> 1) & 1) ^ 1), abort_flag)) {
+            for (int64_t u = 0; u < my_units && ok; ++u) {
+                const int buf = (int)(u & 1);
+                if (!mbar_wait(acc_free0 + 8 * buf, (uint32_t)(((u >> 1) & 1) ^ 1), abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                for (int plane = 0; plane < 2 && ok; ++plane) {
-                    const uint32_t d_tmem = tmem + (uint32_t)(buf * 256 + plane * 128);
-                    for (int64_t kc = 0; kc < nk; ++kc) {
-                        if (!mbar_wait(full0 + 8 * s, phase, abort_flag)) {
-                            ok = false;
-                            break;
-                        }
-                        tc_fence_after();
+                const uint32_t d_tmem = tmem + (uint32_t)(buf * kTcE);
+                for (int64_t kc = 0; kc < nk; ++kc) {
+                    if (!mbar_wait(full0 + 8 * s, phase, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
 #pragma unroll
-                        for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                            for (int kk = 0; kk < 4; ++kk) {
-                                // K step of 32 bytes: +2 in the address field
-                                umma_f8(d_tmem, sdesc + (uint64_t)(h * (kTcColBytes >> 4) + 2 * kk),
-                                        sdesc + b_off + h * b_col + (uint64_t)(2 * kk), idesc,
-                                        (kc > 0 || h > 0 || kk > 0) ? 1u : 0u);
-                            }
-                        }
-                        umma_commit(empty0 + 8 * s);
-                        sdesc += sbytes >> 4;
-                        if (++s == nstages) {
-                            s = 0;
-                            phase ^= 1u;
-                            sdesc = desc0;
-                        }
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_f8(d_tmem, sdesc + (uint64_t)(2 * kk), sdesc + b_off + (uint64_t)(2 * kk),
+                                idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    umma_commit(empty0 + 8 * s);
+                    sdesc += kTcStageBytes >> 4;
+                    if (++s == kTcStages) {
+                        s = 0;
+                        phase ^= 1u;
+                        sdesc = desc0;
                     }
                 }
                 if (ok) umma_commit(acc_full0 + 8 * buf);
@@ -263,31 +250,33 @@ tc_scan_kernel(const TcScanArgs a, int npad, int nstages)
             if (!mbar_wait(drain, 0, nullptr)) a.status[0] = 3;
         }
     } else if (warp >= 2 && warp < 6) {
+        // lane = query row; columns = the unit's 256 entries
         const int quarter = warp & 3;
-        const int row = quarter * 32 + lane;
-        for (int64_t tl = 0; tl < my_tiles; ++tl) {
-            const int buf = (int)(tl & 1);
-            if (!mbar_wait(acc_full0 + 8 * buf, (uint32_t)((tl >> 1) & 1), abort_flag)) {
+        const int q = quarter * 32 + lane;
+        uint32_t* cnt = reinterpret_cast<uint32_t*>(a.counts);
+        for (int64_t u = 0; u < my_units; ++u) {
+            const int buf = (int)(u & 1);
+            if (!mbar_wait(acc_full0 + 8 * buf, (uint32_t)((u >> 1) & 1), abort_flag)) {
                 a.status[0] = 4;
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            const int64_t e = (blockIdx.x + tl * gridDim.x) * kTcM + row;
-            const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256);
-            for (int c0 = 0; c0 < npad; c0 += 16) {
-                uint32_t r1[16], r2[16];
-                tmem_ld16(lane_base + c0, r1);
-                tmem_ld16(lane_base + 128 + c0, r2);
+            const int64_t unit = blockIdx.x + u * gridDim.x;
+            const int64_t e0 = (unit >> 1) * kTcE;
+            const int plane = (int)(unit & 1);
+            const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kTcE);
+            for (int c0 = 0; c0 < kTcE; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(lane_base + c0, r);
                 tmem_wait_ld();
-                if (e < a.n) {
+                if (q < a.nq) {
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
-                        const int q = c0 + j;
-                        if (q < a.nq)
-                            a.counts[(int64_t)q * a.n + e] =   // 4 x the counts, exact
-                                make_uint2((uint32_t)(__uint_as_float(r1[j]) * 0.25f),
-                                           (uint32_t)(__uint_as_float(r2[j]) * 0.25f));
+                        const int64_t e = e0 + c0 + j;
+                        if (e < a.n)   // 4 x the count, exact
+                            cnt[((int64_t)q * a.n + e) * 2 + plane] =
+                                (uint32_t)(__uint_as_float(r[j]) * 0.25f);
                     }
                 }
             }
@@ -295,62 +284,54 @@ tc_scan_kernel(const TcScanArgs a, int npad, int nstages)
             mbar_arrive(acc_free0 + 8 * buf);
         }
     } else if (warp >= kTcConv0 / 32) {
-        // thread ct expands half a row of every K-slice: of entry row ct / 2
-        // for ct < 256, of patient row (ct - 256) / 2 for the next 2 npad
-        // threads; the remaining threads only take part in the barriers
+        // converters: thread ct < 256 expands entry row ct of the tile, thread
+        // 256 + r query row r (r < nq)
         const int ct = threadIdx.x - kTcConv0;
-        const bool is_a = ct < 2 * kTcM;
-        const int task = is_a ? ct : ct - 2 * kTcM;
-        const int row = task >> 1, half = task & 1;
-        const bool active = is_a || task < 2 * npad;
-        const uint32_t col = is_a ? (uint32_t)(half * kTcColBytes)
-                                  : (uint32_t)(kTcABytes + half * npad * 128);
-        const uint32_t ring0 = smem_u32(ring) + (uint32_t)(ct * 16);   // + slot * kTcConv * 16
-        // position of the next K-slice to copy (tile, plane, slice), kept
-        // incrementally: no divisions on the per-slice path
-        int64_t i_tl = 0, i_kc = 0;
-        int i_plane = 0, i_slot = 0;
-        const uint32_t* src_row = nullptr;   // this thread's row of the current (tile, plane)
+        const bool is_b = ct < kTcE;
+        const int row = is_b ? ct : ct - kTcE;
+        const bool active = is_b || row < a.nq;
+        int64_t i_u = 0, i_kc = 0;
+        int i_slot = 0;
+        const uint32_t* src_row = nullptr;
         bool row_ok = false;
         auto row_start = [&]() {
-            if (is_a) {
-                const int64_t e = (blockIdx.x + i_tl * gridDim.x) * kTcM + row;
+            const int64_t unit = blockIdx.x + i_u * gridDim.x;
+            const int plane = (int)(unit & 1);
+            if (is_b) {
+                const int64_t e = (unit >> 1) * kTcE + row;
                 row_ok = e < a.n;
-                src_row = a.planes + (e * 2 + i_plane) * a.wp + half * 4;
+                src_row = a.planes + (e * 2 + plane) * a.wp;
             } else {
-                row_ok = row < a.nq;
-                src_row = a.qplanes + ((int64_t)row * 2 + i_plane) * a.wp + half * 4;
+                row_ok = true;
+                src_row = a.qplanes + ((int64_t)row * 2 + plane) * a.wp;
             }
         };
         if (active) row_start();
+        const uint32_t ring0 = smem_u32(ring) + (uint32_t)(ct * 16);
         auto issue = [&]() {
-            if (active && i_tl < my_tiles) {
+            if (active && i_u < my_units) {
                 const int64_t w = i_kc * kTcSliceWords;
-                const bool v = row_ok && w + half * 4 < a.wp;
+                const bool v = row_ok && w < a.wp;
                 cp_async16(ring0 + (uint32_t)(i_slot * kTcConv * 16), v ? src_row + w : a.planes, v);
                 if (++i_kc == nk) {
                     i_kc = 0;
-                    if (++i_plane == 2) {
-                        i_plane = 0;
-                        ++i_tl;
-                    }
-                    if (i_tl < my_tiles) row_start();
+                    ++i_u;
+                    if (i_u < my_units) row_start();
                 }
             }
-            cp_async_commit();      // one group per slice, empty when idle
+            cp_async_commit();
             if (++i_slot == kTcAhead) i_slot = 0;
         };
         for (int d = 0; d < kTcAhead; ++d) issue();
         int c_slot = 0, s = 0;
         uint32_t phase = 0;
+        const uint32_t dst = (is_b ? (uint32_t)kTcABytes : 0u) + row_offset(row);
+        const uint32_t stage0 = smem_u32(stages);
         for (int64_t it = 0; it < total; ++it) {
-            cp_async_wait<kTcAhead - 1>();          // this thread's copy of slice `it`
+            cp_async_wait<kTcAhead - 1>();
             uint4 bits = make_uint4(0, 0, 0, 0);
-            if (active)
-                bits = *reinterpret_cast<const uint4*>(ring + ct * 16 + c_slot * kTcConv * 16);
+            if (active) bits = *reinterpret_cast<const uint4*>(ring + ct * 16 + c_slot * kTcConv * 16);
             if (++c_slot == kTcAhead) c_slot = 0;
-            // one lane waits for the stage to be free; __syncwarp orders the
-            // other lanes' stores after that
             int ok = 1;
             if (lane == 0) ok = mbar_wait(empty0 + 8 * s, phase ^ 1u, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok, 0);
@@ -362,13 +343,11 @@ tc_scan_kernel(const TcScanArgs a, int npad, int nstages)
                 }
                 break;
             }
-            if (active)
-                expand_row(smem_u32(stages) + (uint32_t)(s * sbytes) + col + row_offset(row), row,
-                           bits);
+            if (active) expand_row(stage0 + (uint32_t)(s * kTcStageBytes) + dst, row, bits);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(full0 + 8 * s);
-            if (++s == nstages) {
+            if (++s == kTcStages) {
                 s = 0;
                 phase ^= 1u;
             }
@@ -437,16 +416,14 @@ cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream)
     if (a.nq < 1 || a.nq > kTcMaxN || a.n < 1 || a.wp < 4 || a.wp % 4 != 0 ||
         (reinterpret_cast<uintptr_t>(a.planes) & 15) || (reinterpret_cast<uintptr_t>(a.qplanes) & 15))
         return cudaErrorInvalidValue;
-    const int npad = a.nq <= 16 ? 16 : (a.nq + 15) / 16 * 16;
-    const int nstages = stages_for(npad);
-    const size_t smem = smem_bytes(npad);
+    const size_t smem = smem_bytes();
     cudaError_t err = cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                            (int)smem);
     if (err != cudaSuccess) return err;
-    const int64_t ntiles = (a.n + kTcM - 1) / kTcM;
-    if (grid > ntiles) grid = (int)ntiles;
+    const int64_t nunits = (a.n + kTcE - 1) / kTcE * 2;
+    if (grid > nunits) grid = (int)nunits;
     if (grid < 1) grid = 1;
-    tc_scan_kernel<<<grid, kTcThreads, smem, stream>>>(a, npad, nstages);
+    tc_scan_kernel<<<grid, kTcThreads, smem, stream>>>(a);
     return cudaGetLastError();
 }
 
