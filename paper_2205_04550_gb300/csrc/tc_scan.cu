@@ -52,11 +52,11 @@ namespace {
 constexpr int kTcQ = 128;                    // query rows of the MMA (M), zero-padded
 constexpr int kTcE = 256;                    // entries per tile (MMA N)
 constexpr int kTcMaxN = 128;                 // queries per launch
-constexpr int kTcStages = 4;
+constexpr int kTcStages = 4;                 // operand stages, 48 KiB each
 constexpr int kTcAhead = 4;                  // K-slices in flight per converter thread
 constexpr int kTcConv = kTcE + kTcQ;         // converter threads: 256 entry rows + 128 query rows
 constexpr int kTcConvWarps = kTcConv / 32;
-constexpr int kTcConv0 = 192;
+constexpr int kTcConv0 = 192;                // first converter thread (warps 0-5: MMA, TMEM, epilogue)
 constexpr int kTcThreads = kTcConv0 + kTcConv;
 constexpr int kTcSliceWords = 4;             // 128 voxels per K-slice and row
 constexpr int kTcABytes = kTcQ * 128;        // query operand of a stage
@@ -65,7 +65,13 @@ constexpr int kTcStageBytes = kTcABytes + kTcBBytes;
 
 __host__ __device__ constexpr size_t ring_bytes() { return (size_t)kTcAhead * kTcConv * 16; }
 
-size_t smem_bytes() { return 1024 + (size_t)kTcStages * kTcStageBytes + ring_bytes() + (2 * kTcStages + 5) * 8 + 16; }
+// 1 KiB of alignment slack, the stages, the cp.async ring, the mbarriers
+// (full and empty per stage, two accumulator pairs, the drain), TMEM slot and
+// abort flag.
+size_t smem_bytes()
+{
+    return 1024 + (size_t)kTcStages * kTcStageBytes + ring_bytes() + (2 * kTcStages + 5) * 8 + 16;
+}
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid)
 {
@@ -176,7 +182,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
         const int st = i / (kTcABytes / 16), off = i % (kTcABytes / 16);
         const int row = ((off * 16) / 1024) * 8 + ((off * 16) % 1024) / 128;   // row of this 16 B
         if (row >= a.nq)
-            *reinterpret_cast<uint4*>(stages + (size_t)st * kTcStageBytes + off * 16) = make_uint4(0, 0, 0, 0);
+            *reinterpret_cast<uint4*>(stages + (size_t)st * kTcStageBytes + off * 16) =
+                make_uint4(0, 0, 0, 0);
     }
     fence_proxy_async();
     if (threadIdx.x == 0) {
