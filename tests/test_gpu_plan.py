@@ -267,3 +267,19 @@ def test_plan_tensor_core_graph_replay(torch, two_dbs):
             for q, (p, w) in enumerate(zip(pats, which)):
                 vols = v1 if w == 0 else v2
                 assert_hits_equal(got[q], oracle.query(vols, p, T1, T2, k), k)
+
+
+@pytest.mark.parametrize("k", [300, 500])
+def test_plan_tensor_core_large_k(torch, two_dbs, k):
+    """The selection after the contraction with k close to its shared-memory
+    capacity (flushes after every round of offers): the oracle's full
+    ranking down to position k, bit-identical to the CUDA-core loop."""
+    (d1, v1), _ = two_dbs
+    rng = np.random.default_rng(k)
+    pats = _patients(rng, v1, 17)
+    which = [0] * len(pats)
+    tc = _run_plan(torch, [d1], which, pats, k, tc_min=16)
+    cc = _run_plan(torch, [d1], which, pats, k, tc_min=0)
+    assert tc.tobytes() == cc.tobytes()
+    for q in (0, 8, 16):
+        assert_hits_equal(tc[q], oracle.query(v1, pats[q], T1, T2, k), k)
