@@ -685,16 +685,24 @@ def run_pde(args, wl, torch):
 
 
 def _support_granules(torch, vol, t1, t2):
-    """16-byte granules (128 voxels of the flattened grid) where the
-    patient's two masks are non-zero: what the sparse loops read per entry."""
+    """16-byte words the sparse loops read per entry: the support lists hold
+    every word of each 64-byte granule (512 voxels of the flattened grid)
+    where the patient's mask is non-zero, both planes (a final partial
+    granule has fewer words)."""
     flat = vol.reshape(-1)
-    pad = (-flat.numel()) % 128
+    v = flat.numel()
+    wp4 = ((v + 31) // 32 + 3) // 4                 # 16-byte words per plane
+    pad = (-v) % 512
     total = 0
     for t in (t1, t2):
         m = flat >= t
         if pad:
             m = torch.cat([m, m.new_zeros(pad)])
-        total += int(m.view(-1, 128).any(dim=1).sum().item())
+        nz = m.view(-1, 512).any(dim=1)
+        words = 4 * int(nz.sum().item())
+        if wp4 % 4 and bool(nz[-1].item()):
+            words -= 4 - wp4 % 4
+        total += words
     return total
 
 
