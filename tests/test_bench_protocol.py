@@ -29,3 +29,31 @@ def test_traffic_reported_only_for_the_captured_grid():
     assert bench._traffic("no_such_kernel", 10, (128, 128, 128)) is None
     if full is not None:      # None once the kernel's sources change
         assert abs(full - (t["read_bytes"] / t["entries"] * 50_000 + t["write_bytes"])) < 1.0
+
+
+def test_support_words_match_the_support_lists_definition():
+    """The sparse loops read every 16-byte word of each 64-byte granule of a
+    plane where the patient's mask is non-zero (fewer words in a final
+    partial granule): the bench's byte count, against a direct count."""
+    import numpy as np
+    import torch
+    rng = np.random.default_rng(0)
+    for shape in ((128, 128, 128), (30, 17, 11), (64, 64, 64), (9, 10, 11)):
+        nx, ny, nz = shape
+        vol = np.zeros((nz, ny, nx), np.float32)
+        z0 = int(rng.integers(0, nz // 2 + 1))
+        dz = min(max(1, nz // 4), nz - z0)
+        vol[z0:z0 + dz, : max(1, ny // 3), :] = rng.random((dz, max(1, ny // 3), nx),
+                                                            dtype=np.float32)
+        got = bench._support_granules(torch, torch.from_numpy(vol), 0.6, 0.25)
+        v = nx * ny * nz
+        wp4 = ((v + 31) // 32 + 3) // 4
+        want = 0
+        for t in (np.float32(0.6), np.float32(0.25)):
+            m = np.zeros(wp4 * 128, bool)
+            m[:v] = vol.reshape(-1) >= t
+            word_nz = m.reshape(wp4, 128).any(axis=1)
+            for g in range((wp4 + 3) // 4):
+                if word_nz[4 * g:4 * g + 4].any():
+                    want += min(4, wp4 - 4 * g)
+        assert got == want, (shape, got, want)
