@@ -154,3 +154,30 @@ def test_sparse_rerank_support_beyond_cache(torch):
         for _ in range(2):
             sparse, _ = db.query_batch(pats, k, DBQ_MODE_EMBED_BF16, c)
             assert sparse.tobytes() == dense.tobytes()
+
+
+@pytest.mark.parametrize("shape", [(128, 64, 32), (30, 17, 11)])
+def test_support_lengths_follow_the_granule_definition(torch, shape):
+    """The support lists hold every 16-byte word of each 64-byte granule of
+    a plane where the patient's mask is non-zero (fewer words in a final
+    partial granule): db_last_support against that count on the CPU."""
+    nx, ny, nz = shape
+    vols, _ = random_db(shape, 8, seed=1)
+    with Database(shape, 8, DBQ_STORE_BITS, T1, T2) as db:
+        db.load(0, vols)
+        db.build()
+        db.set_sparse(True)
+        for seed in range(4):
+            patient = _sparse_patient(shape, seed, frac=0.05 * (seed + 1))
+            db.query(patient, 3)
+            l1, l2 = _dbq.db_last_support(db.handle)
+            v = nx * ny * nz
+            wp4 = ((v + 31) // 32 + 3) // 4
+            want = []
+            for t in (T1, T2):
+                m = np.zeros(wp4 * 128, bool)
+                m[:v] = patient.reshape(-1) >= t
+                word_nz = m.reshape(wp4, 128).any(axis=1)
+                want.append(sum(min(4, wp4 - 4 * g) for g in range((wp4 + 3) // 4)
+                                if word_nz[4 * g:4 * g + 4].any()))
+            assert (l1, l2) == tuple(want), (seed, l1, l2, want)
