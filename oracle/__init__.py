@@ -13,7 +13,8 @@ Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 library and never imports it.
 
 Pinned functions (the pins live in ``tests/test_oracle_*.py``):
-counts, Dice, score, ranking, thresholding (f32 and f16), the binary16
+counts (from volumes and from byte masks), Dice, score, ranking,
+thresholding (f32 and f16), the binary16
 decoder, bit-plane unpacking, block means, L2 distance, nearest-neighbour
 downsampling, count sketches and sign codes, and the reaction-diffusion
 forward model of Section 2.1.
@@ -197,7 +198,9 @@ def counts(db: np.ndarray, pmask: np.ndarray, t1: float, t2: float,
 
 
 def counts_masks(dbmask: np.ndarray, pmask: np.ndarray, nthreads: int = 0):
-    """Counts for database entries given as masks [N][2][V] uint8."""
+    """Counts for database entries given as masks [N][2][V] uint8 (0/1):
+    (counts [N,4] = I1, I2, E1, E2;  pcount [2]).  Any other byte value
+    raises ValueError."""
     lib = _load()
     n = int(dbmask.shape[0])
     v = int(dbmask.shape[-1])
@@ -205,7 +208,8 @@ def counts_masks(dbmask: np.ndarray, pmask: np.ndarray, nthreads: int = 0):
     pm = _c(pmask.reshape(2, v), np.uint8)
     out = np.zeros((n, 4), dtype=np.uint32)
     pc = np.zeros(2, dtype=np.uint32)
-    lib.oracle_counts_masks(_p(a), n, v, _p(pm), int(nthreads), _p(out), _p(pc))
+    if lib.oracle_counts_masks(_p(a), n, v, _p(pm), int(nthreads), _p(out), _p(pc)) != 0:
+        raise ValueError("mask bytes must be 0 or 1")
     return out, pc
 
 

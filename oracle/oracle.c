@@ -227,10 +227,16 @@ int oracle_counts_f16(const uint16_t* db, int64_t n, int64_t v, const uint8_t* p
 }
 
 /* Counts against database entries given directly as byte masks [n][2][v]
-   (used for the downsampled loop and for masks built by other means). */
+   (used for the downsampled loop and for masks built by other means).  A
+   mask byte is a set membership, 0 or 1; any other byte value is rejected
+   (returns -1, nothing written) because summing it would miscount. */
 int oracle_counts_masks(const uint8_t* dbmask, int64_t n, int64_t v, const uint8_t* pmask,
                         int nthreads, uint32_t* out /* [n][4] */, uint32_t* pcount)
 {
+    for (int64_t x = 0; x < 2 * v; ++x)
+        if (pmask[x] > 1) return -1;
+    for (int64_t x = 0; x < n * 2 * v; ++x)
+        if (dbmask[x] > 1) return -1;
     patient_sizes(pmask, v, pcount);
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);

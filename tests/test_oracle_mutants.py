@@ -43,6 +43,9 @@ MUTANTS = {
     "rd_y_stride_is_ny": ("const int64_t sy = nx, sz = (int64_t)nx * ny;",
                           "const int64_t sy = ny, sz = (int64_t)nx * ny;"),
     "rd_steps_ignore_m_max": ("double rate = 6.0 * dw * m_max + rho;", "double rate = 6.0 * dw + rho;"),
+    "counts_masks_flair_vs_t1gd_patient": ("            i2 += m[v + x] & pmask[v + x];",
+                                           "            i2 += m[v + x] & pmask[x];"),
+    "counts_masks_drops_plane_offset": ("            e2 += m[v + x];", "            e2 += m[x];"),
     "patient_flair_at_t1": ("        mask[v + x] = (uint8_t)in_mask_f32(vol[x], t2);",
                             "        mask[v + x] = (uint8_t)in_mask_f32(vol[x], t1);"),
 }

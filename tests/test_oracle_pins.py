@@ -286,3 +286,79 @@ def test_downsample_nearest_neighbour_layout():
             out = oracle.downsample_nn(m, nx, ny, nz, f)
             o = nx // f
             assert out.sum() == 1 and out[x + o * (y + o * z)] == 1
+
+
+# ------------------------------------------------------------------ counts from masks
+def test_counts_masks_golden_2x2x2_hand_worked():
+    """The hand-worked golden query, with every segmentation written out as
+    the set of voxels the golden file lists, not derived by any oracle
+    call: patient T1Gd {0,1,4}, FLAIR {0,1,2,4,5,7}; the entries' sets
+    follow from their values by reading them against 0.6 and 0.25."""
+    g = _load_golden()
+    v = 8
+    sets = [  # (T1Gd voxels, FLAIR voxels) of each golden entry, by hand
+        ({0, 1, 4}, {0, 1, 2, 4, 5, 7}),       # identical to the patient
+        (set(), set()),                         # all zero
+        ({0}, {0}),                             # 0.6 at voxel 0 only
+        ({2, 3, 6}, {2, 3, 6, 7}),              # 0.1 0.1 0.9 0.9 0.1 0.1 0.9 0.3
+        (set(range(8)), set(range(8))),         # all one
+        ({0}, {0}),                             # same as entry 2
+        (set(), {0, 1}),                        # values just below / at the thresholds
+    ]
+    db = np.zeros((len(sets), 2, v), np.uint8)
+    for e, (a, b) in enumerate(sets):
+        db[e, 0, sorted(a)] = 1
+        db[e, 1, sorted(b)] = 1
+    pm = np.zeros((2, v), np.uint8)
+    pm[0, [0, 1, 4]] = 1
+    pm[1, [0, 1, 2, 4, 5, 7]] = 1
+    cnt, pc = oracle.counts_masks(db, pm)
+    assert list(pc) == [g["P1"], g["P2"]]
+    for e, ent in enumerate(g["database"]):
+        assert list(cnt[e]) == [ent["I1"], ent["I2"], ent["E1"], ent["E2"]], e
+
+
+def test_counts_masks_sets_on_irregular_grid():
+    """Counts of random byte masks against Python set sizes, per plane, on a
+    grid whose voxel count is not a multiple of anything the GPU uses."""
+    v = 7 * 5 * 3
+    db = (rng.random((9, 2, v)) < 0.4).astype(np.uint8)
+    pm = (rng.random((2, v)) < 0.5).astype(np.uint8)
+    cnt, pc = oracle.counts_masks(db, pm)
+    psets = [set(np.flatnonzero(pm[k]).tolist()) for k in range(2)]
+    assert list(pc) == [len(psets[0]), len(psets[1])]
+    for e in range(9):
+        esets = [set(np.flatnonzero(db[e, k]).tolist()) for k in range(2)]
+        assert list(cnt[e]) == [len(psets[0] & esets[0]), len(psets[1] & esets[1]),
+                                len(esets[0]), len(esets[1])], e
+
+
+def test_counts_masks_equals_counts_of_thresholded_volumes():
+    """counts_masks(threshold(vols), threshold(patient)) == counts(vols, patient):
+    carries the pins of the volume counts over to the mask counts, with the
+    two planes thresholded at different values so that a swapped plane or
+    a dropped plane offset shows."""
+    vols = _random_volumes(15, shape=(6, 9, 11))
+    patient = _random_volumes(1, shape=(6, 9, 11))[0]
+    vols[4] = patient
+    t1, t2 = 0.6, 0.25
+    pm = oracle.threshold(patient, t1, t2)
+    want, wpc = oracle.counts(vols, pm, t1, t2)
+    dbm = np.stack([oracle.threshold(x, t1, t2) for x in vols])
+    got, gpc = oracle.counts_masks(dbm, pm)
+    np.testing.assert_array_equal(got, want)
+    np.testing.assert_array_equal(gpc, wpc)
+    assert np.any(want[:, 0] != want[:, 1]) and np.any(want[:, 2] != want[:, 3])
+
+
+def test_counts_masks_rejects_non_binary_bytes():
+    db = np.zeros((2, 2, 16), np.uint8)
+    pm = np.zeros((2, 16), np.uint8)
+    oracle.counts_masks(db, pm)
+    db[1, 1, 5] = 2
+    with pytest.raises(ValueError):
+        oracle.counts_masks(db, pm)
+    db[1, 1, 5] = 1
+    pm[0, 3] = 255
+    with pytest.raises(ValueError):
+        oracle.counts_masks(db, pm)
