@@ -26,7 +26,9 @@
  *
  * Conventions:
  *   * Every call returns a dbq_status; on failure db_last_error() returns a
- *     thread-local message and no output has been written.
+ *     thread-local message and no output has been written -- except that a
+ *     failure of the device itself (DBQ_ECUDA, DBQ_ETIMEOUT) can leave
+ *     partial results in device-memory outputs that kernels write directly.
  *   * "host or device" pointers are classified with cudaPointerGetAttributes;
  *     host memory may be pageable or pinned.
  *   * `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
@@ -391,8 +393,11 @@ int db_create_downsampled(dbq_db** out, dbq_db* src, int factor);
  * Only enqueues work on `stream`; allocates nothing.  Its scratch is one
  * fixed array of 512.25 KiB in device memory that every GPU loading the
  * library keeps until exit, shared by all calls: calls that overlap on the
- * GPU race.  The first call on a device caches the array's address; make it
- * before any stream capture.  Devices with more than 256 SMs are rejected.
+ * GPU race.  Each call made outside stream capture looks up the array's
+ * device address and caches it per device (so a device reset between calls
+ * is harmless); a call made during capture uses the cached address, so make
+ * the first call on a device before any capture (DBQ_ESTATE otherwise).
+ * Devices with more than 256 SMs are rejected.
  */
 int db_scan_packed_noalloc(const uint32_t* planes, const uint32_t* sizes, int64_t n,
                            int64_t stride_words, const uint32_t* patient_planes,

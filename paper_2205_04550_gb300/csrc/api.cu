@@ -1003,16 +1003,17 @@ int db_query(dbq_db* db, const void* patient, int kind, float t1, float t2, int 
     DBQ_CUDA(cudaMemcpyAsync(db->hits_host, db->hits_dev, (size_t)k * sizeof(dbq::Hit),
                              cudaMemcpyDeviceToHost, s));
     DBQ_CUDA(cudaStreamSynchronize(s));
-    std::memcpy(hits, db->hits_host, (size_t)k * sizeof(dbq_hit));
-    if (params && db->n_params) {
-        for (int j = 0; j < k; ++j) {
-            const int64_t e = hits[j].index;
-            if (e < 0 || e >= db->n) return fail(DBQ_ECUDA, "kernel returned index %lld",
-                                                 (long long)e);
-            std::memcpy(params + (size_t)j * db->n_params, &db->params[(size_t)e * db->n_params],
+    // every check before the first byte of output is written
+    const dbq_hit* got = reinterpret_cast<const dbq_hit*>(db->hits_host);
+    for (int j = 0; j < k; ++j)
+        if (got[j].index < 0 || got[j].index >= db->n)
+            return fail(DBQ_ECUDA, "kernel returned index %lld", (long long)got[j].index);
+    std::memcpy(hits, got, (size_t)k * sizeof(dbq_hit));
+    if (params && db->n_params)
+        for (int j = 0; j < k; ++j)
+            std::memcpy(params + (size_t)j * db->n_params,
+                        &db->params[(size_t)got[j].index * db->n_params],
                         sizeof(double) * db->n_params);
-        }
-    }
     return DBQ_OK;
 }
 
@@ -1207,6 +1208,10 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
     if (kind != DBQ_F32 && kind != DBQ_F16 && kind != DBQ_BITS)
         return fail(DBQ_EINVAL, "unknown patient kind %d", kind);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // results are staged here and copied out only once every group has
+    // succeeded, so that a failing call writes no output
+    std::vector<dbq_hit> staged((size_t)nq * (size_t)(k > 0 ? k : 0));
+    std::vector<const dbq_db*> owner((size_t)nq, nullptr);
     // group queries by database, keeping their order inside a group
     std::vector<int> order((size_t)nq);
     for (int q = 0; q < nq; ++q) order[q] = q;
@@ -1291,21 +1296,24 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
             DBQ_CUDA(cudaStreamSynchronize(s));
             for (int q = 0; q < gn; ++q) {
                 const int qi = order[g0 + q];
-                std::memcpy(hits + (size_t)qi * k, db->bhits_host + (size_t)q * k,
-                            (size_t)k * sizeof(dbq_hit));
-                if (params && db->n_params) {
-                    for (int h = 0; h < k; ++h) {
-                        const int64_t e = hits[(size_t)qi * k + h].index;
-                        if (e < 0 || e >= db->n)
-                            return fail(DBQ_ECUDA, "kernel returned index %lld", (long long)e);
-                        std::memcpy(params + ((size_t)qi * k + h) * db->n_params,
-                                    &db->params[(size_t)e * db->n_params],
-                                    sizeof(double) * db->n_params);
-                    }
-                }
+                const dbq_hit* got = reinterpret_cast<const dbq_hit*>(db->bhits_host) + (size_t)q * k;
+                for (int h = 0; h < k; ++h)
+                    if (got[h].index < 0 || got[h].index >= db->n)
+                        return fail(DBQ_ECUDA, "kernel returned index %lld",
+                                    (long long)got[h].index);
+                std::memcpy(&staged[(size_t)qi * k], got, (size_t)k * sizeof(dbq_hit));
+                owner[(size_t)qi] = db;
             }
         }
         i = j;
+    }
+    if (nq > 0) std::memcpy(hits, staged.data(), staged.size() * sizeof(dbq_hit));
+    for (int qi = 0; qi < nq && params; ++qi) {
+        const dbq_db* db = owner[(size_t)qi];
+        for (int h = 0; h < k && db->n_params; ++h)
+            std::memcpy(params + ((size_t)qi * k + h) * db->n_params,
+                        &db->params[(size_t)staged[(size_t)qi * k + h].index * db->n_params],
+                        sizeof(double) * db->n_params);
     }
     return DBQ_OK;
 }

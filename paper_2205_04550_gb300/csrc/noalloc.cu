@@ -21,9 +21,13 @@
 //     and can return wrong hits.  The ticket is cleared on the caller's
 //     stream before each launch; the candidate lists are fully rewritten by
 //     every launch and need no clearing;
-//   * the first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress) and caches it; make that first call before any
-//     stream capture begins.
+//   * every call made outside stream capture looks up the array's device
+//     address (cudaGetSymbolAddress) for the current device and caches it;
+//     a call made while its stream is being captured uses that cached
+//     address, so the first call on a device must come before any capture.
+//     Looking the address up again on every uncaptured call keeps it valid
+//     after the primary context has been torn down and created again (a
+//     cudaDeviceReset reloads the module at a new address).
 #include <mutex>
 
 #include "dbq.h"
@@ -68,11 +72,19 @@ extern "C" int db_scan_packed_noalloc(const uint32_t* planes, const uint32_t* si
     if (grid > kMaxNoallocCtas)
         return noalloc_fail(DBQ_ERANGE, "device has more SMs than the scratch array serves");
 
-    // One-time set-up per device: the device address of the scratch array.
+    // The device address of the scratch array: looked up (and cached per
+    // device) by every call outside stream capture, taken from the cache
+    // during capture.
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus capture = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &capture) != cudaSuccess) {
+        cudaGetLastError();
+        return noalloc_fail(DBQ_ECUDA, "cannot query the stream's capture status");
+    }
     void* scratch = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_setup_mu);
-        if (!g_scratch_addr[dev]) {
+        if (capture == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
             const cudaError_t err = cudaGetSymbolAddress(&p, g_noalloc_scratch);
             if (err != cudaSuccess || !p) {
@@ -80,12 +92,14 @@ extern "C" int db_scan_packed_noalloc(const uint32_t* planes, const uint32_t* si
                 return noalloc_fail(DBQ_ECUDA, "cudaGetSymbolAddress of the scratch array failed");
             }
             g_scratch_addr[dev] = p;
+        } else if (!g_scratch_addr[dev]) {
+            return noalloc_fail(DBQ_ESTATE,
+                                "the first call on a device must come before any stream capture");
         }
         scratch = g_scratch_addr[dev];
     }
     unsigned char* base = static_cast<unsigned char*>(scratch);
     unsigned int* ticket = reinterpret_cast<unsigned int*>(base + kScratchBytes);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     if (cudaMemsetAsync(ticket, 0, sizeof(unsigned int), s) != cudaSuccess) {
         cudaGetLastError();
         return noalloc_fail(DBQ_ECUDA, "clearing the ticket failed");

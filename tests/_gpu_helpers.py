@@ -52,3 +52,65 @@ def assert_hits_equal(hits, ref, k):
 
 def oracle_query(db, patient, t1, t2, k, patient_mask=None):
     return oracle.query(db, patient, t1, t2, k, patient_mask=patient_mask)
+
+
+def stream_oracle_counts(shape, n, queries, dtype="float32", chunk=256, seed=synth.DB_SEED):
+    """The oracle's per-entry counts over a whole surrogate database that is
+    too large to hold on the host: the same seeded volumes the database was
+    built from are generated on the GPU chunk by chunk, copied into pinned
+    host memory, and counted by ``oracle.counts`` on all host cores by one
+    worker thread while the next chunk is generated and copied (ctypes
+    releases the GIL during the oracle's C call).
+
+    queries: list of (patient mask [2][V] uint8, t1, t2).
+    Returns one [n, 4] uint32 array (I1, I2, E1, E2) per query.
+    """
+    import queue
+    import threading
+
+    import torch
+
+    nx, ny, nz = shape
+    tdt = torch.float16 if dtype == "float16" else torch.float32
+    gen = synth.DeviceGenerator(shape, seed, np.arange(n))
+    dev = torch.empty((chunk, nz, ny, nx), dtype=tdt, device="cuda")
+    host = [torch.empty((chunk, nz, ny, nx), dtype=tdt, pin_memory=True) for _ in range(2)]
+    free = [threading.Semaphore(1) for _ in range(2)]     # host buffer not in use by the oracle
+    work = queue.Queue()
+    out = [np.zeros((n, 4), dtype=np.uint32) for _ in queries]
+    errors = []
+
+    def worker():
+        while True:
+            item = work.get()
+            if item is None:
+                return
+            buf, c0, cn = item
+            try:
+                vols = host[buf][:cn].numpy()
+                if dtype == "float16":
+                    vols = vols.view(np.uint16)
+                for qi, (pm, t1, t2) in enumerate(queries):
+                    cnt, _ = oracle.counts(vols, pm, t1, t2)
+                    out[qi][c0:c0 + cn] = cnt
+            except Exception as exc:  # pragma: no cover - surfaced below
+                errors.append(exc)
+            free[buf].release()
+
+    th = threading.Thread(target=worker)
+    th.start()
+    try:
+        for i, c0 in enumerate(range(0, n, chunk)):
+            buf = i & 1
+            cn = min(chunk, n - c0)
+            gen.fill(c0, cn, dev)
+            free[buf].acquire()
+            host[buf][:cn].copy_(dev[:cn])
+            torch.cuda.synchronize()
+            work.put((buf, c0, cn))
+    finally:
+        work.put(None)
+        th.join()
+    if errors:
+        raise errors[0]
+    return out

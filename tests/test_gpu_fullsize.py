@@ -4,17 +4,17 @@ benchmark times.
 * 1,024 entries at 64^3 (float32 surrogate volumes, t = 0.6 / 0.25, top-10):
   the oracle runs over the whole database; every count, the scores and the
   top-10 must match exactly.
-* 50,000 entries at 128^3 bit-packed (top-64): the oracle recomputes the
-  counts of a seeded sample of entries and of every returned hit from the
-  same volumes, and ranks the GPU's per-entry counts with its own scoring --
-  the GPU top-64 must equal that ranking exactly.
+* 50,000 entries at 128^3 bit-packed (top-64): the oracle counts every
+  entry from the same volumes (streamed from the GPU generator through host
+  memory in chunks); every count, the patient's sizes, the top-64 order and
+  the hits' score bits must equal the oracle's own ranking of its own scores.
 """
 import numpy as np
 import pytest
 
 import oracle
 from paper_2205_04550_gb300 import DBQ_STORE_BITS, Database, synth
-from tests._gpu_helpers import assert_hits_equal
+from tests._gpu_helpers import assert_hits_equal, stream_oracle_counts
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +61,7 @@ def test_exact_query_1024_entries_64cube_full_oracle(torch):
         np.testing.assert_array_equal(pcount, ref["pcount"])
 
 
-def test_exact_query_50000_entries_128cube_sampled(torch):
+def test_exact_query_50000_entries_128cube_every_entry(torch):
     shape = (128, 128, 128)
     n, k = 50_000, 64
     db = _build_db_on_device(torch, shape, n, chunk=8)
@@ -71,23 +71,16 @@ def test_exact_query_50000_entries_128cube_sampled(torch):
         hits, params = db.query(patient, k)
         counts, pcount = db.scan_counts(patient)
         pmask = oracle.threshold(patient, T1, T2)
+        # the oracle over every entry, from the volumes themselves
+        (ref_counts,) = stream_oracle_counts(shape, n, [(pmask, T1, T2)], chunk=256)
+        np.testing.assert_array_equal(counts, ref_counts)
         np.testing.assert_array_equal(pcount, pmask.sum(axis=1))
-        # the ranking of the GPU's counts by the oracle's scoring and order
-        sc = oracle.scores(counts, pcount)
+        sc = oracle.scores(ref_counts, pmask.sum(axis=1).astype(np.uint32))
         idx, val = oracle.rank(sc, k)
-        np.testing.assert_array_equal(hits["index"], idx)
-        np.testing.assert_array_equal(hits["score"].view(np.uint64), val.view(np.uint64))
-        # the counts themselves, recomputed by the oracle from the volumes
-        rng = np.random.default_rng(20220510)
-        sample = np.unique(np.concatenate([rng.choice(n, 48, replace=False), idx,
-                                           [0, n - 1]]))
-        vols_dev, _ = synth.generate_device(shape, synth.DB_SEED, sample)
-        vols = vols_dev.cpu().numpy()
-        ref_counts, ref_p = oracle.counts(vols, pmask, T1, T2)
-        np.testing.assert_array_equal(counts[sample], ref_counts)
-        np.testing.assert_array_equal(pcount, ref_p)
-        hit_counts = np.stack([hits[f] for f in ("i1", "i2", "e1", "e2")], axis=1)
-        np.testing.assert_array_equal(hit_counts, counts[idx])
+        ref = {"index": idx, "score": val,
+               "counts": np.concatenate([ref_counts[idx],
+                                         np.tile(pmask.sum(axis=1), (k, 1))], axis=1)}
+        assert_hits_equal(hits, ref, k)
         theta = synth.entry_params(shape, synth.DB_SEED, idx)
         np.testing.assert_array_equal(params, theta)
         # the sparse scan (patient support only) gives the identical result

@@ -283,3 +283,39 @@ def test_plan_tensor_core_large_k(torch, two_dbs, k):
     assert tc.tobytes() == cc.tobytes()
     for q in (0, 8, 16):
         assert_hits_equal(tc[q], oracle.query(v1, pats[q], T1, T2, k), k)
+
+
+@pytest.mark.parametrize("shape,n", [((128, 128, 128), 64), ((256, 256, 256), 8)])
+def test_plan_tensor_core_counts_near_the_binary32_limit(torch, shape, n):
+    """The contraction's counts where they are largest: full and nearly full
+    masks at 128^3 (counts up to 2^21) and 256^3 (up to 2^24, the largest
+    grid the tensor-core path takes).  The binary32 accumulators must still
+    hold the exact integers: hits bit-identical to the CUDA-core loop's and
+    equal to the oracle's."""
+    nx, ny, nz = shape
+    rng = np.random.default_rng(n)
+    vols = np.empty((n, nz, ny, nx), np.float32)
+    for e in range(n):
+        if e % 4 == 0:
+            vols[e] = 1.0                                    # E_1 = E_2 = V
+        else:
+            vols[e] = rng.random((nz, ny, nx), dtype=np.float32)
+            vols[e][rng.random((nz, ny, nx)) < 0.02 * e / n] = 0.0
+    pats = [np.ones((nz, ny, nx), np.float32), vols[1].copy(), vols[n - 1].copy()]
+    for _ in range(3):
+        p = rng.random((nz, ny, nx), dtype=np.float32)
+        p[rng.random(p.shape) < 0.01] = 0.0
+        pats.append(p)
+    which = [0] * len(pats)
+    k = min(n, 8)
+    with Database(shape, n, DBQ_STORE_BITS, T1, T2) as db:
+        db.load(0, vols)
+        db.build()
+        tc = _run_plan(torch, [db], which, pats, k, tc_min=1)
+        cc = _run_plan(torch, [db], which, pats, k, tc_min=0)
+    assert tc.tobytes() == cc.tobytes()
+    for q, p in enumerate(pats):
+        ref = oracle.query(vols, p, T1, T2, k)
+        assert_hits_equal(tc[q], ref, k)
+    # the full patient against a full entry: I = E = P = V exactly
+    assert int(tc[0]["i2"][0]) == nx * ny * nz and tc[0]["score"][0] == 1.0

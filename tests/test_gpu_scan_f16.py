@@ -8,7 +8,7 @@ import pytest
 
 import oracle
 from paper_2205_04550_gb300 import DBQ_STORE_F16, Database, DbqError, _dbq, synth
-from tests._gpu_helpers import assert_hits_equal, pack_bits_np, random_db
+from tests._gpu_helpers import assert_hits_equal, pack_bits_np, random_db, stream_oracle_counts
 
 pytestmark = pytest.mark.gpu
 
@@ -123,9 +123,10 @@ def test_f16_errors(torch):
         assert e.value.status == _dbq.DBQ_ESTATE
 
 
-def test_f16_query_100000_entries_64cube_sampled(torch):
+def test_f16_query_100000_entries_64cube_every_entry(torch):
     """Full size: 100,000 binary16 entries at 64^3 (52 GB), per-query
-    thresholds t1 ~ U(0.5, 0.8), t2 ~ U(0.15, 0.35), top-16."""
+    thresholds t1 ~ U(0.5, 0.8), t2 ~ U(0.15, 0.35), top-16; the oracle
+    counts every entry of both queries from the same binary16 values."""
     shape = (64, 64, 64)
     n, k, chunk = 100_000, 16, 64
     nx, ny, nz = shape
@@ -141,19 +142,23 @@ def test_f16_query_100000_entries_64cube_sampled(torch):
         db.build()
         pat, _ = synth.patients_np(shape, [2], dtype=np.float16)
         p16 = pat[0].view(np.uint16)
+        queries, gpu = [], []
         for q in range(2):
             t1, t2 = _thresholds(100 + q)
-            hits, _ = db.query(p16, k, t1, t2)
+            hits, params = db.query(p16, k, t1, t2)
             counts, pcount = db.scan_counts(p16, t1, t2)
             pmask = oracle.threshold(pat[0], t1, t2)
             np.testing.assert_array_equal(pcount, pmask.sum(axis=1))
-            idx, val = oracle.rank(oracle.scores(counts, pcount), k)
-            np.testing.assert_array_equal(hits["index"], idx)
-            np.testing.assert_array_equal(hits["score"].view(np.uint64), val.view(np.uint64))
-            rng = np.random.default_rng(q)
-            sample = np.unique(np.concatenate([rng.choice(n, 40, replace=False), idx, [n - 1]]))
-            vols_dev, _ = synth.generate_device(shape, synth.DB_SEED, sample, dtype="float16")
-            ref_counts, _ = oracle.counts(vols_dev.cpu().numpy(), pmask, t1, t2)
-            np.testing.assert_array_equal(counts[sample], ref_counts)
+            queries.append((pmask, t1, t2))
+            gpu.append((hits, params, counts))
+        refs = stream_oracle_counts(shape, n, queries, dtype="float16", chunk=2048)
+        for (pmask, _, _), (hits, params, counts), ref_counts in zip(queries, gpu, refs):
+            np.testing.assert_array_equal(counts, ref_counts)
+            pc = pmask.sum(axis=1).astype(np.uint32)
+            idx, val = oracle.rank(oracle.scores(ref_counts, pc), k)
+            ref = {"index": idx, "score": val,
+                   "counts": np.concatenate([ref_counts[idx], np.tile(pc, (k, 1))], axis=1)}
+            assert_hits_equal(hits, ref, k)
+            np.testing.assert_array_equal(params, gen.theta[idx])
     finally:
         db.close()

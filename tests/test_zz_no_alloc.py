@@ -3,11 +3,13 @@ query, for callers that cannot allocate device memory (a pool that owns the
 whole GPU, a request path that must not synchronise on an allocation, a
 plug-in host that forbids device allocations).
 
-It is checked through the C ABI against the handle API's db_query on the
-same database and patients -- bit-exact, the tolerance every parity test here
-uses -- on two calls in a row with different patients, so a stale scratch
-array from the first call would show in the second.  This file is collected
-last on purpose.
+It is checked through the C ABI against the handle API's db_query and
+against the CPU oracle on the same database and patients -- bit-exact, the
+tolerance every parity test here uses -- on two calls in a row with different
+patients, so a stale scratch array from the first call would show in the
+second.  The cases cover the documented limit k = 64, fewer entries than
+SMs (CTAs with no entries publish lists of sentinels into the shared array)
+and k = n.  This file is collected last on purpose.
 """
 import ctypes
 
@@ -16,7 +18,7 @@ import pytest
 
 import oracle
 from paper_2205_04550_gb300 import DBQ_STORE_BITS, Database, _dbq
-from tests._gpu_helpers import pack_bits_np, random_db
+from tests._gpu_helpers import assert_hits_equal, pack_bits_np, random_db
 
 pytestmark = pytest.mark.gpu
 
@@ -35,11 +37,12 @@ def _hits(t):
     return _dbq.hits_from_device(t)
 
 
-def test_noalloc_matches_db_query_two_calls(torch):
+@pytest.mark.parametrize("n,k", [(777, 13), (777, 64), (50, 7), (64, 64)])
+def test_noalloc_matches_db_query_two_calls(torch, n, k):
     shape = (32, 32, 32)                      # 1024 words per plane, a multiple of 4
-    n, k = 777, 13
-    vols, patient_a = random_db(shape, n, seed=41, plant=(500,))
-    _, patient_b = random_db(shape, 1, seed=42)
+    plant = n * 2 // 3
+    vols, patient_a = random_db(shape, n, seed=41 + n, plant=(plant,))
+    _, patient_b = random_db(shape, 1, seed=42 + n)
     lib = _dbq.load()
     with Database(shape, n, DBQ_STORE_BITS, T1, T2) as db:
         db.load(0, vols)
@@ -63,9 +66,10 @@ def test_noalloc_matches_db_query_two_calls(torch):
             want, _ = db.query(patient, k)
             got = _hits(out)
             assert got.tobytes() == want.tobytes()
+            assert_hits_equal(got, oracle.query(vols, patient, T1, T2, k), k)
             best.append(int(got["index"][0]))
         # the planted copy of patient a is the best match of the first call only
-        assert best[0] == 500 and best[1] != 500
+        assert best[0] == plant and best[1] != plant
 
 
 def test_noalloc_rejects_sizes_beyond_its_limits(torch):
