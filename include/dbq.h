@@ -296,7 +296,16 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
  * db_plan_destroy frees the plan (NULL accepted).
  */
 typedef struct dbq_plan dbq_plan;
-enum dbq_plan_param { DBQ_PLAN_ITEMS_PER_SM = 1, DBQ_PLAN_TC_MIN_QUERIES = 2 };
+enum dbq_plan_param {
+    DBQ_PLAN_ITEMS_PER_SM = 1,
+    DBQ_PLAN_TC_MIN_QUERIES = 2,
+    DBQ_PLAN_TEST_STALL_NS = 3   /* test hook, default 0: with value > 0, each
+                                    tensor-core launch first waits up to that
+                                    many ns on a barrier that nothing arrives
+                                    at, gives up, and takes its timeout path
+                                    (no hits are valid; db_plan_status then
+                                    returns DBQ_ETIMEOUT).  At most 2e9. */
+};
 int db_plan_create(dbq_plan** out, dbq_db* const* dbs, int ndb, int max_queries, int k);
 int db_plan_set(dbq_plan* plan, int param, int64_t value);
 int db_plan_query(dbq_plan* plan, const int* db_of_query, int nq, const void* const* patients_dev,

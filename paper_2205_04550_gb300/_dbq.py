@@ -39,6 +39,7 @@ DBQ_OPT_SPARSE = 1
 
 DBQ_PLAN_ITEMS_PER_SM = 1
 DBQ_PLAN_TC_MIN_QUERIES = 2
+DBQ_PLAN_TEST_STALL_NS = 3
 
 DBQ_MODE_EXACT = 0
 DBQ_MODE_EMBED_BF16 = 1

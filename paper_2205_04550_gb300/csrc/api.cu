@@ -615,7 +615,8 @@ struct dbq_plan {
     // tensor-core path for databases queried by many dense queries at once
     int tc_min = 16;                  // queries per database that switch it on (0 = never)
     int tc_rows = 0;                  // queries per tensor-core launch (0 = unavailable)
-    uint2* tc_counts = nullptr;       // [tc_rows][largest n] intersections
+    uint32_t* tc_counts = nullptr;    // [2][tc_rows][stride of the largest n] intersections
+    unsigned long long tc_stall_ns = 0;   // DBQ_PLAN_TEST_STALL_NS
     int* tc_status = nullptr;         // nonzero after a timed-out wait
     ~dbq_plan()
     {
@@ -1428,10 +1429,11 @@ int db_plan_create(dbq_plan** out, dbq_db* const* dbs, int ndb, int max_queries,
     for (const dbq_db* db : p->dbs)
         if (db->v <= (int64_t)1 << 24) tc_n = std::max<int64_t>(tc_n, db->n);
     if (tc_n > 0) {
+        const size_t row_bytes = (size_t)dbq::tc_counts_stride(tc_n) * 2 * sizeof(uint32_t);
         int rows = std::min(max_queries, dbq::tc_scan_max_queries());
-        while (rows > 16 && (size_t)rows * tc_n * sizeof(uint2) > ((size_t)1 << 30)) rows /= 2;
-        if ((size_t)rows * tc_n * sizeof(uint2) <= ((size_t)1 << 30) &&
-            dalloc(&p->tc_counts, (size_t)rows * tc_n * sizeof(uint2)) &&
+        while (rows > 16 && (size_t)rows * row_bytes > ((size_t)1 << 30)) rows /= 2;
+        if ((size_t)rows * row_bytes <= ((size_t)1 << 30) &&
+            dalloc(&p->tc_counts, (size_t)rows * row_bytes) &&
             dalloc(&p->tc_status, 16))
             p->tc_rows = rows;
         else
@@ -1461,6 +1463,12 @@ int db_plan_set(dbq_plan* plan, int param, int64_t value)
         if (value < 0 || value > 65535)
             return fail(DBQ_EINVAL, "tensor-core query threshold must be in [0, 65535]");
         plan->tc_min = (int)value;
+        return DBQ_OK;
+    }
+    if (param == DBQ_PLAN_TEST_STALL_NS) {
+        if (value < 0 || value > 2000000000LL)
+            return fail(DBQ_EINVAL, "stall must be in [0, 2e9] ns");
+        plan->tc_stall_ns = (unsigned long long)value;
         return DBQ_OK;
     }
     return fail(DBQ_EINVAL, "unknown plan parameter %d", param);
@@ -1620,10 +1628,13 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
             ta.qplanes = tg.qplanes + (size_t)c0 * 2 * tg.db->wp;
             ta.nq = nqc;
             ta.counts = p->tc_counts;
+            ta.stride = dbq::tc_counts_stride(tg.db->n);
             ta.status = p->tc_status;
+            ta.stall_ns = p->tc_stall_ns;
             err = dbq::launch_tc_scan(ta, p->sms, s);
             if (err != cudaSuccess) return cuda_fail(err, "tensor-core scan launch");
-            err = dbq::launch_tc_select(p->tasks_dev, tg.slot + c0, nqc, p->tc_counts, tg.db->n, s);
+            err = dbq::launch_tc_select(p->tasks_dev, tg.slot + c0, nqc, p->tc_counts, tg.db->n,
+                                        ta.stride, s);
             if (err != cudaSuccess) return cuda_fail(err, "tensor-core selection launch");
         }
     }

@@ -219,16 +219,20 @@ struct TcScanArgs {
     int64_t wp;                 // words per plane, a multiple of 4
     const uint32_t* qplanes;    // patients [nq][2][wp] bit planes (16-byte aligned)
     int nq;                     // 1 .. tc_scan_max_queries()
-    uint2* counts;              // out: [nq][n] (I_1, I_2)
+    uint32_t* counts;           // out: [2][nq][stride] I_k of (patient, entry), 16-byte aligned
+    int64_t stride;             // tc_counts_stride(n)
     int* status;                // device word: nonzero after a timed-out wait
+    unsigned long long stall_ns;  // test only: 0, or first wait this long on a barrier
+                                  // nothing arrives at (the timeout path; status 5)
 };
 int tc_scan_max_queries();
+int64_t tc_counts_stride(int64_t n);
 // Exact only while V <= 2^24 (the binary32 accumulators count voxels).
 cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream);
-// Scores and top-k of patients tasks[task0 .. task0 + nq) from counts [nq][n]
-// (mask sizes, k and the hit output taken from each task).
-cudaError_t launch_tc_select(const QueryTask* tasks, int task0, int nq, const uint2* counts,
-                             int64_t n, cudaStream_t stream);
+// Scores and top-k of patients tasks[task0 .. task0 + nq) from counts
+// [2][nq][stride] (mask sizes, k and the hit output taken from each task).
+cudaError_t launch_tc_select(const QueryTask* tasks, int task0, int nq, const uint32_t* counts,
+                             int64_t n, int64_t stride, cudaStream_t stream);
 // items[i] = (task, slice), every slice of the ntasks tasks once; next_item
 // is a device counter (cleared here); any_sparse: some task has support
 // lists, and the items are then re-ordered in place, costliest first.

@@ -4,44 +4,51 @@
 // For Q patients and N entries the intersections I_k(q, e) = |P_k(q) n E_k(e)|
 // are dot products of 0/1 vectors over the V voxels: one dense contraction
 // [Q x V] . [V x N] per segmentation.  The masks are stored as bits, which
-// the tensor cores cannot read, so converter warps expand each K-slice of 128
-// voxels of the patients' rows and of 256 entry rows into E4M3 bytes (2.0 for
-// a set bit, 0 otherwise) in the 128-byte-swizzled K-major layout of tcgen05
-// shared-memory operands, and one thread issues tcgen05.mma (kind::f8f6f4,
-// M = 128 patient rows -- the rows past Q are zero --, N = 256 entries,
-// K = 32 per instruction) with binary32 accumulators in tensor memory.  An
+// the tensor cores cannot read, so converter warps expand each K-slice of 256
+// voxels of the patients' rows and of 240 entry rows into 4-bit E2M1 values
+// (1.0 for a set bit, 0 otherwise; two voxels per byte) in the
+// 128-byte-swizzled K-major layout of tcgen05 shared-memory operands, and one
+// thread issues block-scaled tcgen05.mma (kind::mxf4, every UE8M0 scale 1.0;
+// M = 128 patient rows -- the rows past Q are zero --, N = 240 entries,
+// K = 64 per instruction) with binary32 accumulators in tensor memory.  An
 // MMA instruction costs about the same for any N, so the entries, not the
-// few patients, take the N side.  Every product is 0 or 4 and every partial
-// sum 4 times an integer no larger than V <= 2^24, so the accumulators hold
-// 4 x the exact counts (2.0 is 0x40: one bit per byte, which saves a
-// multiply per output word over 1.0 = 0x38).
+// few patients, take the N side.  Every product is 0 or 1 and every partial
+// sum an integer no larger than V <= 2^24, so the accumulators hold the
+// exact counts.
 //
-//   * work units are (256-entry tile, segmentation), round-robin over one
+// Voxel order inside a K-slice: a dot product does not depend on the order
+// of its terms as long as both operands use the same one, so the expansion
+// takes whatever order is cheapest: 16-byte chunk c of a row holds the 32
+// voxels of bit word c, its 32-bit word j holds bits j, j + 4, ..., j + 28 of
+// that word, one per nibble ((u >> j) & 0x11111111, shifted to the 1.0 code
+// 0x2).  That is two integer instructions per 8 voxels.
+//
+//   * work units are (240-entry tile, segmentation), round-robin over one
 //     persistent CTA per SM; each unit writes its own component of the
 //     counts, so no unit waits for another;
-//   * warps 6-17 (converters): thread t < 256 copies with cp.async the 16
-//     bytes (128 voxels) of entry row t of every K-slice, thread 256 + r
-//     those of patient row r < Q, four slices ahead, expands them into a
-//     4-stage ring of operand tiles and makes the stores visible to the
-//     tensor core (fence.proxy.async); one lane per warp then arrives on the
-//     stage's full barrier (the warp's stores ordered before it by
-//     __syncwarp), and one lane per warp waits for a stage to be free.  The
-//     patient rows past Q are cleared once at the start;
-//   * warp 0 (one thread): per K-slice four MMAs into the unit's 256
-//     accumulator columns in one of two TMEM buffers, so the epilogue of a
-//     unit overlaps the next unit's MMAs; its commits free the stage and, at
-//     the end of a unit, hand the buffer to the epilogue;
+//   * warps 6-17 (converters): thread t < 240 expands entry row t of the
+//     tile, thread 240 + r patient row r < Q; each keeps the 32 bytes of bits
+//     of the next three K-slices in registers (loads issued three slices
+//     ahead), expands one slice into a 4-stage ring of operand tiles and makes
+//     the stores visible to the tensor core (fence.proxy.async); one lane per
+//     warp then arrives on the stage's full barrier, and one lane per warp
+//     waits for a stage to be free.  The patient rows past Q are cleared once;
+//   * warp 0 (one thread): per K-slice four MMAs into the unit's 240
+//     accumulator columns in one of two TMEM buffers (columns 0 and 256), so
+//     the epilogue of a unit overlaps the next unit's MMAs; its commits free
+//     the stage and, at the end of a unit, hand the buffer to the epilogue;
 //   * warps 2-5 (epilogue, one TMEM lane quarter each, lane = patient row):
-//     tcgen05.ld the counts of 16 entries at a time and store them into
-//     counts[q][e];
+//     fill the scale columns (240-255 for A, 496-511 for B) with UE8M0 1.0
+//     once, then tcgen05.ld the counts of 16 entries at a time and store them
+//     as 64-byte rows of counts[plane][q][e];
 //   * warp 1 allocates and frees the 512 TMEM columns.
-// The expanded operands pass through shared memory twice (converter stores,
-// tensor-core reads): about 24 bytes of shared-memory traffic per byte of
-// bits, which bounds this design near 8 bytes of bits per cycle per SM.
-// The mask sizes, binary64 scores and each patient's top-k follow in
-// tc_select_kernel.  Every mbarrier wait is bounded; on a timeout the CTA
-// records an error code in `status`, stops, drains its MMAs and copies and
-// frees its TMEM.
+// Per 256-voxel slice the expanded operands (46 KB) pass through shared
+// memory twice (converter stores, tensor-core reads), about 1.5 bytes per
+// entry bit in each direction; that traffic, not the FP4 tensor rate, is the
+// kernel's bound.  The mask sizes, binary64 scores and each patient's top-k
+// follow in tc_select_kernel.  Every mbarrier wait is bounded; on a timeout
+// the CTA records an error code in `status`, stops, drains its MMAs and frees
+// its TMEM.
 #include "kernels.h"
 #include "tcgen05.cuh"
 #include "topk.cuh"
@@ -50,45 +57,42 @@ namespace dbq {
 namespace {
 
 constexpr int kTcQ = 128;                    // query rows of the MMA (M), zero-padded
-constexpr int kTcE = 256;                    // entries per tile (MMA N)
+constexpr int kTcE = 240;                    // entries per tile (MMA N)
 constexpr int kTcMaxN = 128;                 // queries per launch
-constexpr int kTcStages = 4;                 // operand stages, 48 KiB each
-constexpr int kTcAhead = 4;                  // K-slices in flight per converter thread
-constexpr int kTcConv = kTcE + kTcQ;         // converter threads: 256 entry rows + 128 query rows
+constexpr int kTcStages = 4;                 // operand stages, 46 KiB each
+constexpr int kTcConv = 384;                 // converter threads: 240 entry + 128 query rows + 16 idle
 constexpr int kTcConvWarps = kTcConv / 32;
 constexpr int kTcConv0 = 192;                // first converter thread (warps 0-5: MMA, TMEM, epilogue)
 constexpr int kTcThreads = kTcConv0 + kTcConv;
-constexpr int kTcSliceWords = 4;             // 128 voxels per K-slice and row
+constexpr int kTcSliceWords = 8;             // 256 voxels per K-slice and row
 constexpr int kTcABytes = kTcQ * 128;        // query operand of a stage
 constexpr int kTcBBytes = kTcE * 128;        // entry operand of a stage
 constexpr int kTcStageBytes = kTcABytes + kTcBBytes;
+constexpr uint32_t kTcBufCols = 256;         // TMEM columns between the two accumulators
+constexpr uint32_t kTcScaleA = 240;          // TMEM columns of the unit scales
+constexpr uint32_t kTcScaleB = 496;
+constexpr uint32_t kUnitScales = 0x7F7F7F7Fu;   // four UE8M0 bytes of 2^0
 
-__host__ __device__ constexpr size_t ring_bytes() { return (size_t)kTcAhead * kTcConv * 16; }
+static_assert(kTcE % 16 == 0 && kTcE <= 256, "MMA N");
+static_assert(kTcScaleA >= kTcE && kTcScaleA + 16 <= kTcBufCols, "scale columns");
+static_assert(kTcScaleB >= kTcBufCols + kTcE && kTcScaleB + 16 <= 512, "scale columns");
+static_assert(kTcABytes % 1024 == 0 && kTcStageBytes % 1024 == 0, "swizzle atoms");
 
-// 1 KiB of alignment slack, the stages, the cp.async ring, the mbarriers
-// (full and empty per stage, two accumulator pairs, the drain), TMEM slot and
+// 1 KiB of alignment slack, the stages, the mbarriers (full and empty per
+// stage, two accumulator pairs, the drain, the test stall), TMEM slot and
 // abort flag.
 size_t smem_bytes()
 {
-    return 1024 + (size_t)kTcStages * kTcStageBytes + ring_bytes() + (2 * kTcStages + 5) * 8 + 16;
+    return 1024 + (size_t)kTcStages * kTcStageBytes + (2 * kTcStages + 6) * 8 + 16;
 }
 
-__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid)
+__device__ __forceinline__ uint4 ldg_stream(const uint32_t* p)
 {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
-                 "r"(valid ? 16 : 0)
-                 : "memory");
-}
-
-__device__ __forceinline__ void cp_async_commit()
-{
-    asm volatile("cp.async.commit_group;" ::: "memory");
-}
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait()
-{
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+    uint4 v;
+    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
 }
 
 __device__ __forceinline__ void fence_proxy_async()
@@ -104,13 +108,23 @@ __device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t a, uint32_t
                  : "memory");
 }
 
-__device__ __forceinline__ void umma_f8(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
-                                        uint32_t idesc, uint32_t accumulate)
+__device__ __forceinline__ void st_global_v4(uint32_t* p, uint32_t a, uint32_t b, uint32_t c,
+                                             uint32_t d)
+{
+    asm volatile("st.global.v4.b32 [%0], {%1, %2, %3, %4};" ::"l"(p), "r"(a), "r"(b), "r"(c),
+                 "r"(d)
+                 : "memory");
+}
+
+__device__ __forceinline__ void umma_f4(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                        uint32_t idesc, uint32_t sfa, uint32_t sfb,
+                                        uint32_t accumulate)
 {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], "
+        "[%5], p;\n}\n" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(sfa), "r"(sfb), "r"(accumulate)
         : "memory");
 }
 
@@ -122,26 +136,18 @@ __device__ __forceinline__ void umma_commit(uint32_t bar)
                  : "memory");
 }
 
-// Four mask bits (x < 16) -> four E4M3 bytes, 2.0 (0x40) where a bit is set:
-// x * 0x204081 places bit j of x at bit 8j (the four shifted copies do not
-// overlap, so nothing carries); shifted by 6 more, at bit 8j + 6.
-__device__ __forceinline__ uint32_t expand4(uint32_t x)
+// 256 mask bits (eight words, voxel 32i + b = bit b of word i) -> one
+// 128-byte operand row of E2M1 nibbles: chunk c (the 32 voxels of word c)
+// goes to chunk position c ^ (row mod 8) of the row, the 128-byte swizzle.
+__device__ __forceinline__ void expand_row(uint32_t row_base, int row, const uint4& lo,
+                                           const uint4& hi)
 {
-    return (x * (0x00204081u << 6)) & 0x40404040u;
-}
-
-// 128 mask bits (four words, voxel 32i + b = bit b of word i) -> one
-// 128-byte operand row: 16-byte chunk c (voxels 16c .. 16c + 15) goes to
-// chunk position c ^ (row mod 8) of the row, the 128-byte swizzle.
-__device__ __forceinline__ void expand_row(uint32_t row_base, int row, const uint4& bits)
-{
-    const uint32_t w[4] = {bits.x, bits.y, bits.z, bits.w};
+    const uint32_t w[8] = {lo.x, lo.y, lo.z, lo.w, hi.x, hi.y, hi.z, hi.w};
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-        const uint32_t h = w[c >> 1] >> ((c & 1) * 16);
-        st_shared_v4(row_base + (uint32_t)(((c ^ (row & 7)) & 7) << 4), expand4(h & 0xFu),
-                     expand4((h >> 4) & 0xFu), expand4((h >> 8) & 0xFu),
-                     expand4((h >> 12) & 0xFu));
+        const uint32_t u = w[c];
+        st_shared_v4(row_base + (uint32_t)(((c ^ (row & 7)) & 7) << 4), (u << 1) & 0x22222222u,
+                     u & 0x22222222u, (u >> 1) & 0x22222222u, (u >> 2) & 0x22222222u);
     }
 }
 
@@ -158,9 +164,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* stages = base;                                  // kTcStages x (A | B)
-    unsigned char* ring = stages + (size_t)kTcStages * kTcStageBytes;   // [ahead][kTcConv] x 16 B
-    uint64_t* bars = reinterpret_cast<uint64_t*>(ring + ring_bytes());
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 5);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(stages + (size_t)kTcStages * kTcStageBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 6);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -176,6 +181,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
     const uint32_t acc_full0 = smem_u32(bars + 2 * kTcStages);
     const uint32_t acc_free0 = smem_u32(bars + 2 * kTcStages + 2);
     const uint32_t drain = smem_u32(bars + 2 * kTcStages + 4);
+    const uint32_t stall = smem_u32(bars + 2 * kTcStages + 5);    // nothing ever arrives here
 
     // the query rows past nq stay zero in every stage: cleared once here
     for (int i = threadIdx.x; i < kTcStages * (kTcABytes / 16); i += blockDim.x) {
@@ -196,6 +202,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
             mbar_init(acc_free0 + 8 * b, 128);
         }
         mbar_init(drain, 1);
+        mbar_init(stall, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -209,15 +216,38 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
+    if (warp >= 2 && warp < 6) {
+        // unit scales for both operands, every lane of this warp's quarter
+        const uint32_t lanes = tmem + ((uint32_t)((warp & 3) * 32) << 16);
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, "
+            "%1, %1, %1, %1, %1, %1, %1};" ::"r"(lanes + kTcScaleA),
+            "r"(kUnitScales)
+            : "memory");
+        asm volatile(
+            "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %1, %1, %1, %1, %1, %1, %1, %1, "
+            "%1, %1, %1, %1, %1, %1, %1};" ::"r"(lanes + kTcScaleB),
+            "r"(kUnitScales)
+            : "memory");
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
 
     if (warp == 0) {
         if (lane == 0) {
-            // D f32, A and B E4M3, K-major, N = 256 entries, M = 128 query rows
-            const uint32_t idesc =
-                (1u << 4) | ((uint32_t)(kTcE >> 3) << 17) | ((uint32_t)(kTcQ >> 4) << 24);
+            // block-scaled descriptor: A and B E2M1 (MXF4 format 1), K-major,
+            // UE8M0 scales, N = 240 entries, M = 128 query rows, K = 64
+            const uint32_t idesc = (1u << 7) | (1u << 10) | ((uint32_t)(kTcE >> 3) << 17) |
+                                   (1u << 23) | ((uint32_t)(kTcQ >> 4) << 24);
             int s = 0;
             uint32_t phase = 0;
             bool ok = true;
+            if (a.stall_ns && !mbar_wait_for(stall, 0, abort_flag, a.stall_ns)) {
+                a.status[0] = 5;           // the test stall ran out, as it must
+                ok = false;
+            }
             const uint64_t desc0 = sw128_desc(smem_u32(stages));
             const uint64_t b_off = (uint64_t)(kTcABytes >> 4);
             uint64_t sdesc = desc0;
@@ -228,7 +258,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
                     break;
                 }
                 tc_fence_after();
-                const uint32_t d_tmem = tmem + (uint32_t)(buf * kTcE);
+                const uint32_t d_tmem = tmem + (uint32_t)buf * kTcBufCols;
                 for (int64_t kc = 0; kc < nk; ++kc) {
                     if (!mbar_wait(full0 + 8 * s, phase, abort_flag)) {
                         ok = false;
@@ -236,9 +266,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
                     }
                     tc_fence_after();
 #pragma unroll
-                    for (int kk = 0; kk < 4; ++kk)
-                        umma_f8(d_tmem, sdesc + (uint64_t)(2 * kk), sdesc + b_off + (uint64_t)(2 * kk),
-                                idesc, (kc > 0 || kk > 0) ? 1u : 0u);
+                    for (int kk = 0; kk < 4; ++kk)   // 64 voxels = 32 bytes per row each
+                        umma_f4(d_tmem, sdesc + (uint64_t)(2 * kk), sdesc + b_off + (uint64_t)(2 * kk),
+                                idesc, tmem + kTcScaleA, tmem + kTcScaleB,
+                                (kc > 0 || kk > 0) ? 1u : 0u);
                     umma_commit(empty0 + 8 * s);
                     sdesc += kTcStageBytes >> 4;
                     if (++s == kTcStages) {
@@ -250,21 +281,20 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
                 if (ok) umma_commit(acc_full0 + 8 * buf);
             }
             if (!ok) {
-                a.status[0] = 2;
+                if (a.status[0] == 0) a.status[0] = 2;
                 *abort_flag = 1;
             }
             umma_commit(drain);
             if (!mbar_wait(drain, 0, nullptr)) a.status[0] = 3;
         }
     } else if (warp >= 2 && warp < 6) {
-        // lane = query row; columns = the unit's 256 entries
+        // lane = query row; columns = the unit's 240 entries
         const int quarter = warp & 3;
         const int q = quarter * 32 + lane;
-        uint32_t* cnt = reinterpret_cast<uint32_t*>(a.counts);
         for (int64_t u = 0; u < my_units; ++u) {
             const int buf = (int)(u & 1);
             if (!mbar_wait(acc_full0 + 8 * buf, (uint32_t)((u >> 1) & 1), abort_flag)) {
-                a.status[0] = 4;
+                if (a.status[0] == 0) a.status[0] = 4;
                 *abort_flag = 1;
                 break;
             }
@@ -272,18 +302,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
             const int64_t unit = blockIdx.x + u * gridDim.x;
             const int64_t e0 = (unit >> 1) * kTcE;
             const int plane = (int)(unit & 1);
-            const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * kTcE);
+            const uint32_t lane_base = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)buf * kTcBufCols;
             for (int c0 = 0; c0 < kTcE; c0 += 16) {
                 uint32_t r[16];
                 tmem_ld16(lane_base + c0, r);
                 tmem_wait_ld();
                 if (q < a.nq) {
+                    uint32_t* row = a.counts + ((int64_t)plane * a.nq + q) * a.stride;
+                    uint32_t v[16];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int64_t e = e0 + c0 + j;
-                        if (e < a.n)   // 4 x the count, exact
-                            cnt[((int64_t)q * a.n + e) * 2 + plane] =
-                                (uint32_t)(__uint_as_float(r[j]) * 0.25f);
+                    for (int j = 0; j < 16; ++j) v[j] = (uint32_t)__uint_as_float(r[j]);   // exact
+                    const int64_t e = e0 + c0;
+                    if (e + 16 <= a.n) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4)
+                            st_global_v4(row + e + j, v[j], v[j + 1], v[j + 2], v[j + 3]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (e + j < a.n) row[e + j] = v[j];
                     }
                 }
             }
@@ -291,14 +328,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
             mbar_arrive(acc_free0 + 8 * buf);
         }
     } else if (warp >= kTcConv0 / 32) {
-        // converters: thread ct < 256 expands entry row ct of the tile, thread
-        // 256 + r query row r (r < nq)
+        // converters: thread ct < 240 expands entry row ct of the tile, thread
+        // 240 + r query row r (r < nq); threads past 367 only take part in the
+        // warps' barrier arrivals
         const int ct = threadIdx.x - kTcConv0;
         const bool is_b = ct < kTcE;
         const int row = is_b ? ct : ct - kTcE;
         const bool active = is_b || row < a.nq;
         int64_t i_u = 0, i_kc = 0;
-        int i_slot = 0;
         const uint32_t* src_row = nullptr;
         bool row_ok = false;
         auto row_start = [&]() {
@@ -313,44 +350,42 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
                 src_row = a.qplanes + ((int64_t)row * 2 + plane) * a.wp;
             }
         };
-        if (active) row_start();
-        const uint32_t ring0 = smem_u32(ring) + (uint32_t)(ct * 16);
-        auto issue = [&]() {
+        if (active && my_units > 0) row_start();
+        // the bits of the next K-slice of this thread's row (zeros past the
+        // row's end, for a missing entry and for inactive threads)
+        auto load_next = [&](uint4& lo, uint4& hi) {
+            lo = make_uint4(0, 0, 0, 0);
+            hi = lo;
             if (active && i_u < my_units) {
                 const int64_t w = i_kc * kTcSliceWords;
-                const bool v = row_ok && w < a.wp;
-                cp_async16(ring0 + (uint32_t)(i_slot * kTcConv * 16), v ? src_row + w : a.planes, v);
+                if (row_ok) {
+                    if (w < a.wp) lo = ldg_stream(src_row + w);
+                    if (w + 4 < a.wp) hi = ldg_stream(src_row + w + 4);
+                }
                 if (++i_kc == nk) {
                     i_kc = 0;
                     ++i_u;
                     if (i_u < my_units) row_start();
                 }
             }
-            cp_async_commit();
-            if (++i_slot == kTcAhead) i_slot = 0;
         };
-        for (int d = 0; d < kTcAhead; ++d) issue();
-        int c_slot = 0, s = 0;
+        int s = 0;
         uint32_t phase = 0;
-        const uint32_t dst = (is_b ? (uint32_t)kTcABytes : 0u) + row_offset(row);
+        const uint32_t dst = (is_b ? (uint32_t)kTcABytes : 0u) + row_offset(active ? row : 0);
         const uint32_t stage0 = smem_u32(stages);
-        for (int64_t it = 0; it < total; ++it) {
-            cp_async_wait<kTcAhead - 1>();
-            uint4 bits = make_uint4(0, 0, 0, 0);
-            if (active) bits = *reinterpret_cast<const uint4*>(ring + ct * 16 + c_slot * kTcConv * 16);
-            if (++c_slot == kTcAhead) c_slot = 0;
+        // expand one K-slice into the next stage; false after an abort
+        auto step = [&](const uint4& lo, const uint4& hi) -> bool {
             int ok = 1;
             if (lane == 0) ok = mbar_wait(empty0 + 8 * s, phase ^ 1u, abort_flag);
             ok = __shfl_sync(0xffffffffu, ok, 0);
-            __syncwarp();
             if (!ok) {
                 if (lane == 0) {
-                    a.status[0] = 1;
+                    if (a.status[0] == 0) a.status[0] = 1;
                     *abort_flag = 1;
                 }
-                break;
+                return false;
             }
-            if (active) expand_row(stage0 + (uint32_t)(s * kTcStageBytes) + dst, row, bits);
+            if (active) expand_row(stage0 + (uint32_t)(s * kTcStageBytes) + dst, row, lo, hi);
             fence_proxy_async();
             __syncwarp();
             if (lane == 0) mbar_arrive(full0 + 8 * s);
@@ -358,11 +393,25 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
                 s = 0;
                 phase ^= 1u;
             }
-            issue();
+            return true;
+        };
+        uint4 p0l, p0h, p1l, p1h, p2l, p2h;
+        load_next(p0l, p0h);
+        load_next(p1l, p1h);
+        load_next(p2l, p2h);
+        for (int64_t it = 0; it < total; it += 3) {
+            if (!step(p0l, p0h)) break;
+            load_next(p0l, p0h);
+            if (it + 1 >= total) break;
+            if (!step(p1l, p1h)) break;
+            load_next(p1l, p1h);
+            if (it + 2 >= total) break;
+            if (!step(p2l, p2h)) break;
+            load_next(p2l, p2h);
         }
-        cp_async_wait<0>();
     }
 
+    tc_fence_before();
     __syncthreads();
     if (warp == 1) {
         tc_fence_after();
@@ -374,8 +423,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
 // Scores and top-k of one patient (one CTA per patient) from its counts:
 // the same binary64 Dice scores, keys and order as the fused scans.
 __global__ void __launch_bounds__(1024, 1)
-tc_select_kernel(const QueryTask* __restrict__ tasks, int task0, const uint2* __restrict__ counts,
-                 int64_t n)
+tc_select_kernel(const QueryTask* __restrict__ tasks, int task0, int nq,
+                 const uint32_t* __restrict__ counts, int64_t n, int64_t stride)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     TopK tk;
@@ -384,15 +433,16 @@ tc_select_kernel(const QueryTask* __restrict__ tasks, int task0, const uint2* __
     const int k = t.k;
     const uint32_t P1 = t.pcount[0], P2 = t.pcount[1];
     const uint2* ecount2 = reinterpret_cast<const uint2*>(t.ecount);
-    const uint2* row = counts + (int64_t)blockIdx.x * n;
+    const uint32_t* row1 = counts + (int64_t)blockIdx.x * stride;
+    const uint32_t* row2 = counts + ((int64_t)nq + blockIdx.x) * stride;
     topk_init(tk);
     for (int64_t b0 = 0; b0 < n; b0 += blockDim.x) {
         const int64_t e = b0 + threadIdx.x;
         if (e < n) {
-            const uint2 I = row[e];
+            const uint32_t I1 = row1[e], I2 = row2[e];
             const uint2 E = ecount2[e];
-            topk_offer(tk, k, score_key(score_rn(I.x, I.y, E.x, E.y, P1, P2)), e,
-                       (uint64_t)I.x | ((uint64_t)I.y << 32),
+            topk_offer(tk, k, score_key(score_rn(I1, I2, E.x, E.y, P1, P2)), e,
+                       (uint64_t)I1 | ((uint64_t)I2 << 32),
                        (uint64_t)E.x | ((uint64_t)E.y << 32));
         }
         __syncthreads();
@@ -418,10 +468,14 @@ tc_select_kernel(const QueryTask* __restrict__ tasks, int task0, const uint2* __
 
 int tc_scan_max_queries() { return kTcMaxN; }
 
+int64_t tc_counts_stride(int64_t n) { return (n + 3) / 4 * 4; }
+
 cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream)
 {
     if (a.nq < 1 || a.nq > kTcMaxN || a.n < 1 || a.wp < 4 || a.wp % 4 != 0 ||
-        (reinterpret_cast<uintptr_t>(a.planes) & 15) || (reinterpret_cast<uintptr_t>(a.qplanes) & 15))
+        a.stride < a.n || a.stride % 4 != 0 ||
+        (reinterpret_cast<uintptr_t>(a.planes) & 15) || (reinterpret_cast<uintptr_t>(a.qplanes) & 15) ||
+        (reinterpret_cast<uintptr_t>(a.counts) & 15))
         return cudaErrorInvalidValue;
     const size_t smem = smem_bytes();
     cudaError_t err = cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -434,15 +488,15 @@ cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream)
     return cudaGetLastError();
 }
 
-cudaError_t launch_tc_select(const QueryTask* tasks, int task0, int nq, const uint2* counts,
-                             int64_t n, cudaStream_t stream)
+cudaError_t launch_tc_select(const QueryTask* tasks, int task0, int nq, const uint32_t* counts,
+                             int64_t n, int64_t stride, cudaStream_t stream)
 {
-    if (nq < 1 || n < 1) return cudaErrorInvalidValue;
+    if (nq < 1 || n < 1 || stride < n) return cudaErrorInvalidValue;
     const size_t smem = topk_smem_bytes();
     cudaError_t err = cudaFuncSetAttribute(tc_select_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
-    tc_select_kernel<<<nq, 1024, smem, stream>>>(tasks, task0, counts, n);
+    tc_select_kernel<<<nq, 1024, smem, stream>>>(tasks, task0, nq, counts, n, stride);
     return cudaGetLastError();
 }
 

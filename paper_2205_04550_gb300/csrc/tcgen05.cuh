@@ -58,9 +58,11 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return ok != 0;
 }
 
-// Bounded wait; false after the time limit, or -- when `abort_flag` is given
-// -- as soon as another role has aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag)
+// Bounded wait; false after `limit_ns`, or -- when `abort_flag` is given --
+// as soon as another role has aborted.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity,
+                                              volatile int* abort_flag,
+                                              unsigned long long limit_ns)
 {
     if (mbar_try(bar, parity)) return true;
     const unsigned long long t0 = now_ns();
@@ -68,9 +70,15 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
         if (mbar_try(bar, parity)) return true;
         if ((i & 63) == 63) {
             if (abort_flag && *abort_flag) return false;
-            if (now_ns() - t0 > kTcWaitNs) return false;
+            if (now_ns() - t0 > limit_ns) return false;
         }
     }
+}
+
+// Bounded wait with the default limit (kTcWaitNs).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag)
+{
+    return mbar_wait_for(bar, parity, abort_flag, kTcWaitNs);
 }
 
 // Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups

@@ -319,3 +319,33 @@ def test_plan_tensor_core_counts_near_the_binary32_limit(torch, shape, n):
         assert_hits_equal(tc[q], ref, k)
     # the full patient against a full entry: I = E = P = V exactly
     assert int(tc[0]["i2"][0]) == nx * ny * nz and tc[0]["score"][0] == 1.0
+
+
+def test_plan_tensor_core_timeout_path_reports_and_recovers(torch, two_dbs):
+    """The bounded-wait path of the tensor-core kernel: with the test stall
+    on, the kernel's first wait is on a barrier nothing arrives at; it gives
+    up after 1 ms, records the timeout, drains and frees its tensor memory,
+    and db_plan_status reports DBQ_ETIMEOUT.  The next call, with the stall
+    off, returns the oracle's hits on the same plan."""
+    (d1, v1), _ = two_dbs
+    rng = np.random.default_rng(99)
+    pats = _patients(rng, v1, 4)
+    which = [0] * len(pats)
+    k = 5
+    with Plan([d1], len(pats), k) as plan:
+        plan.set_tc_min_queries(1)
+        dev = [torch.from_numpy(p).cuda() for p in pats]
+        hits = torch.zeros((len(pats), k * 40), dtype=torch.uint8, device="cuda")
+        _dbq.db_plan_set(plan.handle, _dbq.DBQ_PLAN_TEST_STALL_NS, 1_000_000)
+        plan.query(which, dev, hits)
+        with pytest.raises(DbqError) as e:
+            plan.status()
+        assert e.value.status == _dbq.DBQ_ETIMEOUT
+        plan.status()                                    # the condition was cleared
+        _dbq.db_plan_set(plan.handle, _dbq.DBQ_PLAN_TEST_STALL_NS, 0)
+        plan.query(which, dev, hits)
+        plan.status()
+        torch.cuda.synchronize()
+        got = hits.cpu().numpy().view(_dbq.HIT_DTYPE)
+        for q, p in enumerate(pats):
+            assert_hits_equal(got[q], oracle.query(v1, p, T1, T2, k), k)
