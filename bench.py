@@ -126,6 +126,7 @@ TRAFFIC = {
 }
 METRIC = "DB entries/s per query (HBM GB/s vs peak); batched queries/s at top-1 match"
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 7900.0              # GB300 HBM3e, nominal
 L2_BYTES = 129_000_000                # GB300 L2
 FLUSH_BYTES = 256 << 20               # written between timed steps when the DB fits on chip
 
@@ -329,6 +330,7 @@ def _oracle_pass(wl, sample, nthreads: int = 0):
 def cpu_baseline(wl, sample_entries: int, min_seconds: float, nthreads: int = 0):
     """The oracle as it stands on a bounded sample of the workload's entries."""
     import oracle
+    prev_threads = oracle.num_threads()
     sample = _oracle_sample(wl, sample_entries)
     reps, t0 = 0, time.perf_counter()
     while True:
@@ -339,6 +341,9 @@ def cpu_baseline(wl, sample_entries: int, min_seconds: float, nthreads: int = 0)
             break
     rate = reps * sample_entries / el
     cores = nthreads if nthreads > 0 else oracle.num_threads()
+    if nthreads > 0:     # the thread count is process-wide in OpenMP: put it back
+        oracle.counts(np.zeros((1, 8), np.float32), np.zeros((2, 8), np.uint8), 0.5, 0.5,
+                      prev_threads)
     shape = wl["shape"]
     return {"value": rate, "unit": "entries/s", "cores": cores, "kind": "oracle",
             "sample": f"{sample_entries} of {wl['n']:,} entries ({shape[0]}^3 "
@@ -387,47 +392,60 @@ def run_reference(args, wl):
 
 
 def _embed_distance_error(db, plist, mode, wl, stream, n_q=16, n_e=64):
-    """Prefilter distances L = d_1 + d_2 from the GPU against binary64
-    distances of the exact 8^3 block means (the embedding before any
-    encoding), on a sample of queries and entries: the error of the chosen
-    precision (encoding and binary32 accumulation together)."""
-    from paper_2205_04550_gb300 import _dbq
+    """Prefilter distances L = d_1 + d_2 from the GPU against the CPU
+    oracle's binary64 distances of the exact 8^3 block means (the embedding
+    before any encoding): entry volumes regenerated from their seeds and
+    patients thresholded, block-averaged and compared by the oracle on the
+    host, outside every timed region.  The error of the chosen precision
+    (encoding and binary32 accumulation together) on a sample of queries and
+    entries."""
+    import oracle
+    from paper_2205_04550_gb300 import _dbq, synth
     nx, ny, nz = wl["shape"]
     n = wl["n"]
     dist = np.zeros((n_q, n), np.float32)
     _dbq.db_prefilter(db.handle, plist[:n_q], mode, 0, dist=dist, stream=stream)
     ents = np.linspace(0, n - 1, n_e).astype(np.int64)
-
-    def block_means(mask):       # mask [nz, ny, nx] of 0/1
-        b = mask.reshape(nz // 8, 8, ny // 8, 8, nx // 8, 8).sum(axis=(1, 3, 5))
-        return b.reshape(-1).astype(np.float64) / 512.0
-
+    t1, t2 = np.float32(wl["t1"]), np.float32(wl["t2"])
+    vols, _ = synth.generate_device(wl["shape"], synth.DB_SEED, ents)
     emb_e = []
-    for e in ents:
-        planes, _ = db.masks(int(e), 1)
-        bits = np.unpackbits(planes[0].view(np.uint8), axis=-1, bitorder="little")
-        bits = bits[:, :nx * ny * nz].reshape(2, nz, ny, nx)
-        emb_e.append([block_means(bits[k]) for k in range(2)])
-    t = (np.float32(wl["t1"]), np.float32(wl["t2"]))
+    for j in range(n_e):
+        m = oracle.threshold(vols[j].cpu().numpy(), t1, t2)
+        emb_e.append([oracle.block_mean(m[k], nx, ny, nz, 8) for k in range(2)])
+    del vols
     err, rel = [], []
     for q in range(n_q):
-        vol = plist[q].cpu().numpy()
-        eq = [block_means((vol >= t[k]).astype(np.uint8)) for k in range(2)]
+        m = oracle.threshold(plist[q].cpu().numpy(), t1, t2)
+        eq = [oracle.block_mean(m[k], nx, ny, nz, 8) for k in range(2)]
         for j, e in enumerate(ents):
-            ref = sum(float(np.sqrt(np.sum((eq[k] - emb_e[j][k]) ** 2))) for k in range(2))
+            ref = oracle.l2(eq[0], emb_e[j][0]) + oracle.l2(eq[1], emb_e[j][1])
             d = abs(float(dist[q, e]) - ref)
             err.append(d)
             rel.append(d / ref if ref > 0 else 0.0)
     return {"pairs": n_q * n_e, "max_abs": max(err), "mean_abs": float(np.mean(err)),
             "max_rel": max(rel), "mean_rel": float(np.mean(rel)),
-            "reference": "binary64 L2 of the exact block means (before encoding)"}
+            "reference": "CPU oracle: binary64 L2 (oracle.l2) of the exact 8^3 block means "
+                         "(oracle.block_mean) of the oracle's thresholded volumes"}
 
 
 def run_embed(args, wl, torch):
     """Batched queries through the embedding prefilter + exact re-ranking,
     compared with the exact scan of the same queries on the same GPU."""
+    line = measure_embed(wl, torch, args.steps, args.warmup, args.workload)
+    if _dist_env()[0] == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def measure_embed(wl, torch, steps, warmup, workload):
+    """The embedding path's bench record (see run_embed)."""
     from paper_2205_04550_gb300 import (DBQ_MODE_EMBED_BF16, DBQ_MODE_EMBED_FP8, DBQ_MODE_EXACT,
                                         DBQ_MODE_HASH, SKETCH_DIMS, _dbq, synth)
+
+    class _A:
+        pass
+    args = _A()
+    args.steps, args.warmup, args.workload = steps, warmup, workload
     rank, world, local = _dist_env()
     db = build_database(torch, wl)
     shape, nq, k, c = wl["shape"], wl["queries"], wl["k"], wl["candidates"]
@@ -580,9 +598,36 @@ def run_embed(args, wl, torch):
         "clocks": clk,
     }
     db.close()
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    return 0
+    return line
+
+
+def batched_record(torch, steps: int, warmup: int):
+    """The second half of the metric, "batched queries/s at top-1 match", on
+    its own configuration (100,000 x 128^3 bit-packed with 2 x 4096-d bf16
+    embeddings, 256 queries per launch, prefilter 512, exact re-rank,
+    top-10), condensed from the embedding path's record."""
+    name = "embed_100k_128"
+    full = measure_embed(WORKLOADS[name], torch, steps, warmup, name)
+    gemm = full["gemm"]
+    return {
+        "workload": name, "desc": WORKLOADS[name]["desc"],
+        "value": full["value"], "unit": "queries/s",
+        "ms_per_launch": full["ms_per_step"], "steps": steps, "warmup": warmup,
+        "sparse_rerank_queries_per_s": full["sparse_rerank"]["queries_per_s"],
+        "agreement_vs_exact_gpu_scan": full["agreement_vs_exact_gpu_scan"],
+        "prefilter_ranking_vs_exact": full["prefilter_ranking_vs_exact"],
+        "distance_error_vs_fp64": full["distance_error_vs_fp64"],
+        "exact_scan_queries_per_s": full["exact_scan_queries_per_s"],
+        "speedup_vs_exact_gpu_scan": full["speedup_vs_exact_gpu_scan"],
+        "stages_ms": full["stages_ms"],
+        "gemm_roofline": {"bound": "tensor", "kernel": "prefilter_gemm_kernel",
+                          "achieved": gemm["tflops"], "peak": gemm["peak"],
+                          "peak_kind": gemm["peak_kind"], "unit": "TFLOP/s",
+                          "frac": gemm["tensor_frac"], "hbm_frac": gemm["hbm_frac"]},
+        "roofline": full["roofline"],
+        "clocks": full["clocks"],
+        "gpu_launches": full["gpu_launches"],
+    }
 
 
 def run_pde(args, wl, torch):
@@ -789,7 +834,12 @@ def run_plan_mix(args, wl, torch):
                 "ms_per_launch": 1000.0 * el / args.steps,
                 "bytes_per_launch": nbytes, "gbs": nbytes / (el / args.steps) / 1e9,
                 "items_per_sm": tuned["items_per_sm"], "tuning_ms": tuned.get("ms"),
-                "tuning_cached": tuned.get("cached")}
+                "tuning_cached": tuned.get("cached"),
+                # per database: batch size from which it is scanned on the
+                # tensor cores (the tuned crossover; dense only)
+                "tc_min_queries": {f"{wl['mix'][int(d)]['shape'][0]}^3 x "
+                                   f"{wl['mix'][int(d)]['n']:,}": v
+                                   for d, v in (tuned.get("tc_min") or {}).items()}}
     dense = results["dense"]
     line = {"metric": METRIC, "value": dense["queries_per_s"], "unit": "queries/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -801,8 +851,8 @@ def run_plan_mix(args, wl, torch):
                        "l2": "inputs larger than L2 (32.8 GB of packed databases); no flush"},
             "dense": dense, "sparse": results["sparse"],
             # per dense launch: a patient-packing kernel per database, and for
-            # each database with >= 16 queries the tensor-core contraction and
-            # its selection kernel (every database here has more)
+            # each database past its tuned crossover the tensor-core
+            # contraction and its selection kernel (both databases here)
             "gpu_launches": 3 * len(wl["mix"]) * args.steps}
     for d in dbs:
         d.close()
@@ -925,6 +975,8 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched (embedding + re-rank) record of the default line")
     args = ap.parse_args(argv)
     wl = WORKLOADS[args.workload]
     if args.warmup < 3:
@@ -1130,9 +1182,15 @@ def main(argv=None):
         sparse["roofline"]["peak"] = peak
         sparse["roofline"]["frac"] = sparse["roofline"]["achieved"] / peak
         line["sparse_scan"] = sparse
+    line["roofline"]["frac_of_nominal"] = achieved / NOMINAL_HBM_GBS
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_sample, args.cpu_seconds)
+        one = cpu_baseline(wl, max(4, args.cpu_sample // 4), args.cpu_seconds / 2, nthreads=1)
+        line["cpu_baseline"]["single_thread"] = {"value": one["value"], "unit": one["unit"],
+                                                 "cores": 1, "sample": one["sample"]}
     db.close()
+    if args.workload == DEFAULT_WORKLOAD and not args.no_batched:
+        line["batched"] = batched_record(torch, steps=min(args.steps, 10), warmup=3)
     if dist:
         dist.destroy_process_group()
     if rank == 0:

@@ -308,6 +308,11 @@ enum dbq_plan_param {
 };
 int db_plan_create(dbq_plan** out, dbq_db* const* dbs, int ndb, int max_queries, int k);
 int db_plan_set(dbq_plan* plan, int param, int64_t value);
+/* db_plan_set_for -- DBQ_PLAN_TC_MIN_QUERIES for database dbs[db_index] of
+ * the plan alone (the crossover between the two paths depends on the
+ * database's resolution and size); -1 returns it to the plan-wide value.
+ * DBQ_ERANGE for an index outside the plan. */
+int db_plan_set_for(dbq_plan* plan, int db_index, int param, int64_t value);
 int db_plan_query(dbq_plan* plan, const int* db_of_query, int nq, const void* const* patients_dev,
                   int kind, const float* t1, const float* t2, dbq_hit* hits_dev, void* stream);
 int db_plan_status(dbq_plan* plan, void* stream);

@@ -200,10 +200,14 @@ class Plan:
     def set_items_per_sm(self, value: int):
         db_plan_set(self.handle, DBQ_PLAN_ITEMS_PER_SM, int(value))
 
-    def set_tc_min_queries(self, value: int):
+    def set_tc_min_queries(self, value: int, db: int | None = None):
         """Dense queries per database from which that database is scanned for
-        all of them at once on the tensor cores (0 = never)."""
-        db_plan_set(self.handle, DBQ_PLAN_TC_MIN_QUERIES, int(value))
+        all of them at once on the tensor cores (0 = never); for database
+        ``db`` of the plan alone when given (-1 = back to the plan-wide value)."""
+        if db is None:
+            db_plan_set(self.handle, DBQ_PLAN_TC_MIN_QUERIES, int(value))
+        else:
+            _dbq.db_plan_set_for(self.handle, int(db), DBQ_PLAN_TC_MIN_QUERIES, int(value))
 
     def status(self, stream=None):
         db_plan_status(self.handle, stream)

@@ -103,6 +103,7 @@ _SIGS = [
     ("db_plan_create", ctypes.c_int, [ctypes.POINTER(_P), _P, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int]),
     ("db_plan_set", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int64]),
+    ("db_plan_set_for", ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_int64]),
     ("db_plan_query", ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int, _P, _P, _P, _P]),
     ("db_plan_status", ctypes.c_int, [_P, _P]),
     ("db_plan_destroy", ctypes.c_int, [_P]),
@@ -321,6 +322,10 @@ def db_plan_create(dbs, max_queries: int, k: int) -> int:
 
 def db_plan_set(plan: int, param: int, value: int):
     _check(load().db_plan_set(plan, param, value))
+
+
+def db_plan_set_for(plan: int, db_index: int, param: int, value: int):
+    _check(load().db_plan_set_for(plan, db_index, param, value))
 
 
 def db_plan_query(plan: int, db_of_query, patients_dev, hits_dev, kind: int | None = None,

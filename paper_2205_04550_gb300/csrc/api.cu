@@ -614,6 +614,7 @@ struct dbq_plan {
     bool copy_pending = false;
     // tensor-core path for databases queried by many dense queries at once
     int tc_min = 16;                  // queries per database that switch it on (0 = never)
+    std::vector<int> tc_min_db;       // per-database override, -1 = tc_min
     int tc_rows = 0;                  // queries per tensor-core launch (0 = unavailable)
     uint32_t* tc_counts = nullptr;    // [2][tc_rows][stride of the largest n] intersections
     unsigned long long tc_stall_ns = 0;   // DBQ_PLAN_TEST_STALL_NS
@@ -1474,6 +1475,20 @@ int db_plan_set(dbq_plan* plan, int param, int64_t value)
     return fail(DBQ_EINVAL, "unknown plan parameter %d", param);
 }
 
+int db_plan_set_for(dbq_plan* plan, int db_index, int param, int64_t value)
+{
+    if (!plan) return fail(DBQ_EINVAL, "plan is NULL");
+    if (db_index < 0 || db_index >= (int)plan->dbs.size())
+        return fail(DBQ_ERANGE, "database index %d outside the plan", db_index);
+    if (param != DBQ_PLAN_TC_MIN_QUERIES)
+        return fail(DBQ_EINVAL, "plan parameter %d has no per-database value", param);
+    if (value < -1 || value > 65535)
+        return fail(DBQ_EINVAL, "tensor-core query threshold must be in [-1, 65535]");
+    if (plan->tc_min_db.size() != plan->dbs.size()) plan->tc_min_db.assign(plan->dbs.size(), -1);
+    plan->tc_min_db[(size_t)db_index] = (int)value;
+    return DBQ_OK;
+}
+
 int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const* patients_dev,
                   int kind, const float* t1, const float* t2, dbq_hit* hits_dev, void* stream)
 {
@@ -1512,8 +1527,10 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
     std::vector<char> use_tc((size_t)ndb, 0);
     for (int d = 0; d < ndb; ++d) {
         const dbq_db* db = p->dbs[d];
-        use_tc[d] = p->tc_rows > 0 && p->tc_min > 0 && per_db[d] >= p->tc_min && !db->sparse &&
-                    db->v <= ((int64_t)1 << 24);
+        const int thr = (size_t)d < p->tc_min_db.size() && p->tc_min_db[(size_t)d] >= 0
+                            ? p->tc_min_db[(size_t)d] : p->tc_min;
+        use_tc[d] = p->tc_rows > 0 && thr > 0 && per_db[d] >= thr && !db->sparse &&
+                    db->v <= ((int64_t)1 << 24) && db->wp >= dbq::tc_scan_min_words();
     }
     // work-item budget: items_per_sm * SMs, shared in proportion to bytes
     double total = 0;

@@ -226,6 +226,7 @@ struct TcScanArgs {
                                   // nothing arrives at (the timeout path; status 5)
 };
 int tc_scan_max_queries();
+int64_t tc_scan_min_words();     // words per plane the contraction needs at least
 int64_t tc_counts_stride(int64_t n);
 // Exact only while V <= 2^24 (the binary32 accumulators count voxels).
 cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream);

@@ -23,32 +23,41 @@
 // that word, one per nibble ((u >> j) & 0x11111111, shifted to the 1.0 code
 // 0x2).  That is two integer instructions per 8 voxels.
 //
-//   * work units are (240-entry tile, segmentation), round-robin over one
+//   * work units are (224-entry tile, segmentation), round-robin over one
 //     persistent CTA per SM; each unit writes its own component of the
 //     counts, so no unit waits for another;
-//   * warps 6-17 (converters): thread t < 240 expands entry row t of the
-//     tile, thread 240 + r patient row r < Q; each keeps the 32 bytes of bits
-//     of the next three K-slices in registers (loads issued three slices
-//     ahead), expands one slice into a 4-stage ring of operand tiles and makes
-//     the stores visible to the tensor core (fence.proxy.async); one lane per
-//     warp then arrives on the stage's full barrier, and one lane per warp
-//     waits for a stage to be free.  The patient rows past Q are cleared once;
-//   * warp 0 (one thread): per K-slice four MMAs into the unit's 240
+//   * warp 1 (one thread, after allocating the 512 TMEM columns): TMA
+//     producer.  Per 1024-voxel chunk of a unit it copies 128 bytes of every
+//     entry row of the tile and of every patient row (3-D tensor maps over
+//     [entry][plane][word], 128-byte swizzle) into one of two bit slots;
+//     rows past the database's end and words past the plane's end arrive as
+//     zeros.  Each row segment is one 128-byte request, which the memory
+//     system serves far better than the 16- or 32-byte pieces that
+//     per-thread loads of 240 scattered rows make;
+//   * warps 6-16 (converters): thread t < 224 expands entry row t of the
+//     tile, thread 224 + r patient row r < Q; per K-slice each reads its
+//     row's 32 bytes of bits from the bit slot, expands them into a 3-stage
+//     ring of operand tiles and makes the stores visible to the tensor core
+//     (fence.proxy.async); one lane per warp then arrives on the stage's full
+//     barrier, and (after a chunk's fourth slice) on the bit slot's empty
+//     barrier.  The patient rows past Q are cleared once;
+//   * warp 0 (one thread): per K-slice four MMAs into the unit's 224
 //     accumulator columns in one of two TMEM buffers (columns 0 and 256), so
 //     the epilogue of a unit overlaps the next unit's MMAs; its commits free
 //     the stage and, at the end of a unit, hand the buffer to the epilogue;
 //   * warps 2-5 (epilogue, one TMEM lane quarter each, lane = patient row):
 //     fill the scale columns (240-255 for A, 496-511 for B) with UE8M0 1.0
 //     once, then tcgen05.ld the counts of 16 entries at a time and store them
-//     as 64-byte rows of counts[plane][q][e];
-//   * warp 1 allocates and frees the 512 TMEM columns.
-// Per 256-voxel slice the expanded operands (46 KB) pass through shared
-// memory twice (converter stores, tensor-core reads), about 1.5 bytes per
-// entry bit in each direction; that traffic, not the FP4 tensor rate, is the
-// kernel's bound.  The mask sizes, binary64 scores and each patient's top-k
-// follow in tc_select_kernel.  Every mbarrier wait is bounded; on a timeout
-// the CTA records an error code in `status`, stops, drains its MMAs and frees
-// its TMEM.
+//     as 64-byte rows of counts[plane][q][e].
+// Shared memory: three operand stages of 44 KiB and two bit slots of
+// 44 KiB.  Per 256-voxel slice the expanded operands pass through shared
+// memory twice (converter stores, tensor-core reads); with the loads on the
+// TMA the remaining limit is the round trip of a stage between the
+// converters and the MMA thread, which three stages do not fully hide.  The
+// mask sizes, binary64 scores and each patient's top-k follow in
+// tc_select_kernel.  Every mbarrier wait is bounded; on a timeout the CTA
+// records an error code in `status`, stops, lets its copies and MMAs finish
+// and frees its TMEM.
 #include "kernels.h"
 #include "tcgen05.cuh"
 #include "topk.cuh"
@@ -57,42 +66,60 @@ namespace dbq {
 namespace {
 
 constexpr int kTcQ = 128;                    // query rows of the MMA (M), zero-padded
-constexpr int kTcE = 240;                    // entries per tile (MMA N)
+constexpr int kTcE = 224;                    // entries per tile (MMA N)
 constexpr int kTcMaxN = 128;                 // queries per launch
-constexpr int kTcStages = 4;                 // operand stages, 46 KiB each
-constexpr int kTcConv = 384;                 // converter threads: 240 entry + 128 query rows + 16 idle
+constexpr int kTcStages = 3;                 // operand stages, 44 KiB each
+constexpr int kTcSlots = 2;                  // bit slots, 44 KiB each
+constexpr int kTcConv = 352;                 // converter threads: 224 entry + 128 query rows
 constexpr int kTcConvWarps = kTcConv / 32;
-constexpr int kTcConv0 = 192;                // first converter thread (warps 0-5: MMA, TMEM, epilogue)
+constexpr int kTcConv0 = 192;                // first converter thread (warps 0-5: MMA, TMA, epilogue)
 constexpr int kTcThreads = kTcConv0 + kTcConv;
 constexpr int kTcSliceWords = 8;             // 256 voxels per K-slice and row
-constexpr int kTcABytes = kTcQ * 128;        // query operand of a stage
-constexpr int kTcBBytes = kTcE * 128;        // entry operand of a stage
+constexpr int kTcChunkWords = 32;            // 1024 voxels (128 bytes) per row and bit slot
+constexpr int kTcABytes = kTcQ * 128;        // query operand of a stage (and query bits of a slot)
+constexpr int kTcBBytes = kTcE * 128;        // entry operand of a stage (and entry bits of a slot)
 constexpr int kTcStageBytes = kTcABytes + kTcBBytes;
+constexpr int kTcSlotBytes = kTcBBytes + kTcABytes;   // entry bits first, then query bits
 constexpr uint32_t kTcBufCols = 256;         // TMEM columns between the two accumulators
 constexpr uint32_t kTcScaleA = 240;          // TMEM columns of the unit scales
 constexpr uint32_t kTcScaleB = 496;
 constexpr uint32_t kUnitScales = 0x7F7F7F7Fu;   // four UE8M0 bytes of 2^0
 
-static_assert(kTcE % 16 == 0 && kTcE <= 256, "MMA N");
+static_assert(kTcE % 16 == 0 && kTcE <= 256 && kTcConv >= kTcE + kTcQ, "MMA N, converters");
 static_assert(kTcScaleA >= kTcE && kTcScaleA + 16 <= kTcBufCols, "scale columns");
 static_assert(kTcScaleB >= kTcBufCols + kTcE && kTcScaleB + 16 <= 512, "scale columns");
-static_assert(kTcABytes % 1024 == 0 && kTcStageBytes % 1024 == 0, "swizzle atoms");
+static_assert(kTcABytes % 1024 == 0 && kTcBBytes % 1024 == 0, "swizzle atoms");
 
-// 1 KiB of alignment slack, the stages, the mbarriers (full and empty per
-// stage, two accumulator pairs, the drain, the test stall), TMEM slot and
-// abort flag.
+// 1 KiB of alignment slack, the stages, the bit slots, the mbarriers (full
+// and empty per stage and per slot, two accumulator pairs, the drain, the
+// test stall), TMEM slot and abort flag.
+constexpr int kTcBars = 2 * kTcStages + 2 * kTcSlots + 6;
 size_t smem_bytes()
 {
-    return 1024 + (size_t)kTcStages * kTcStageBytes + (2 * kTcStages + 6) * 8 + 16;
+    return 1024 + (size_t)kTcStages * kTcStageBytes + (size_t)kTcSlots * kTcSlotBytes +
+           kTcBars * 8 + 16;
 }
 
-__device__ __forceinline__ uint4 ldg_stream(const uint32_t* p)
+__device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr)
 {
     uint4 v;
-    asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+    asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
                  : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
+                 : "r"(addr)
+                 : "memory");
     return v;
+}
+
+// 3-D tiled TMA load (x = word, y = plane, z = row), completion counted in
+// bytes on `bar`.  x is a multiple of 32 words, 128 bytes.
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint32_t bar,
+                                            int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bar), "r"(x), "r"(y), "r"(z)
+        : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async()
@@ -158,14 +185,17 @@ __device__ __forceinline__ uint32_t row_offset(int row)
     return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs a)
+__global__ void __launch_bounds__(kTcThreads, 1)
+tc_scan_kernel(const __grid_constant__ CUtensorMap tm_db, const __grid_constant__ CUtensorMap tm_q,
+               const TcScanArgs a)
 {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
     unsigned char* stages = base;                                  // kTcStages x (A | B)
-    uint64_t* bars = reinterpret_cast<uint64_t*>(stages + (size_t)kTcStages * kTcStageBytes);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * kTcStages + 6);
+    unsigned char* slots = stages + (size_t)kTcStages * kTcStageBytes;   // kTcSlots x (B | A) bits
+    uint64_t* bars = reinterpret_cast<uint64_t*>(slots + (size_t)kTcSlots * kTcSlotBytes);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + kTcBars);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -173,15 +203,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
     const int64_t ntiles = (a.n + kTcE - 1) / kTcE;
     const int64_t nunits = ntiles * 2;                             // (tile, plane)
     const int64_t my_units = nunits > blockIdx.x ? (nunits - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t nk = (a.wp + kTcSliceWords - 1) / kTcSliceWords;
-    const int64_t total = my_units * nk;
+    const int64_t nk = (a.wp + kTcSliceWords - 1) / kTcSliceWords;       // K-slices per unit
+    const int64_t nchunks = (a.wp + kTcChunkWords - 1) / kTcChunkWords;  // bit slots per unit
 
     const uint32_t full0 = smem_u32(bars);
     const uint32_t empty0 = smem_u32(bars + kTcStages);
-    const uint32_t acc_full0 = smem_u32(bars + 2 * kTcStages);
-    const uint32_t acc_free0 = smem_u32(bars + 2 * kTcStages + 2);
-    const uint32_t drain = smem_u32(bars + 2 * kTcStages + 4);
-    const uint32_t stall = smem_u32(bars + 2 * kTcStages + 5);    // nothing ever arrives here
+    const uint32_t bfull0 = smem_u32(bars + 2 * kTcStages);
+    const uint32_t bempty0 = smem_u32(bars + 2 * kTcStages + kTcSlots);
+    const uint32_t acc_full0 = smem_u32(bars + 2 * kTcStages + 2 * kTcSlots);
+    const uint32_t acc_free0 = acc_full0 + 16;
+    const uint32_t drain = acc_full0 + 32;
+    const uint32_t stall = acc_full0 + 40;                        // nothing ever arrives here
 
     // the query rows past nq stay zero in every stage: cleared once here
     for (int i = threadIdx.x; i < kTcStages * (kTcABytes / 16); i += blockDim.x) {
@@ -196,6 +228,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
         for (int s = 0; s < kTcStages; ++s) {
             mbar_init(full0 + 8 * s, kTcConvWarps);
             mbar_init(empty0 + 8 * s, 1);
+        }
+        for (int s = 0; s < kTcSlots; ++s) {
+            mbar_init(bfull0 + 8 * s, 1);
+            mbar_init(bempty0 + 8 * s, kTcConvWarps);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(acc_full0 + 8 * b, 1);
@@ -238,7 +274,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
     if (warp == 0) {
         if (lane == 0) {
             // block-scaled descriptor: A and B E2M1 (MXF4 format 1), K-major,
-            // UE8M0 scales, N = 240 entries, M = 128 query rows, K = 64
+            // UE8M0 scales, N = 224 entries, M = 128 query rows, K = 64
             const uint32_t idesc = (1u << 7) | (1u << 10) | ((uint32_t)(kTcE >> 3) << 17) |
                                    (1u << 23) | ((uint32_t)(kTcQ >> 4) << 24);
             int s = 0;
@@ -287,8 +323,50 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
             umma_commit(drain);
             if (!mbar_wait(drain, 0, nullptr)) a.status[0] = 3;
         }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // TMA producer: per unit and 1024-voxel chunk, the 128-byte row
+            // segments of the tile's entries and of the patients
+            int slot = 0;
+            uint32_t phase = 0;
+            bool issued[kTcSlots] = {};
+            uint32_t issued_parity[kTcSlots] = {};
+            const uint32_t slot0 = smem_u32(slots);
+            const uint32_t bytes = (uint32_t)(kTcE + a.nq) * 128u;
+            bool ok = true;
+            for (int64_t u = 0; u < my_units && ok; ++u) {
+                const int64_t unit = blockIdx.x + u * gridDim.x;
+                const int plane = (int)(unit & 1);
+                const int e0 = (int)((unit >> 1) * kTcE);
+                for (int64_t j = 0; j < nchunks; ++j) {
+                    if (!mbar_wait(bempty0 + 8 * slot, phase ^ 1u, abort_flag)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t dst = slot0 + (uint32_t)(slot * kTcSlotBytes);
+                    mbar_arrive_expect_tx(bfull0 + 8 * slot, bytes);
+                    tma_load_3d(dst, &tm_db, bfull0 + 8 * slot, (int)(j * kTcChunkWords), plane, e0);
+                    tma_load_3d(dst + kTcBBytes, &tm_q, bfull0 + 8 * slot, (int)(j * kTcChunkWords),
+                                plane, 0);
+                    issued[slot] = true;
+                    issued_parity[slot] = phase;
+                    if (++slot == kTcSlots) {
+                        slot = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            if (!ok) {
+                if (a.status[0] == 0) a.status[0] = 6;
+                *abort_flag = 1;
+            }
+            // no copy may still be writing shared memory when the CTA exits
+            for (int sl = 0; sl < kTcSlots; ++sl)
+                if (issued[sl] && !mbar_wait(bfull0 + 8 * sl, issued_parity[sl], nullptr))
+                    a.status[0] = 7;
+        }
     } else if (warp >= 2 && warp < 6) {
-        // lane = query row; columns = the unit's 240 entries
+        // lane = query row; columns = the unit's 224 entries
         const int quarter = warp & 3;
         const int q = quarter * 32 + lane;
         for (int64_t u = 0; u < my_units; ++u) {
@@ -328,86 +406,63 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_scan_kernel(const TcScanArgs
             mbar_arrive(acc_free0 + 8 * buf);
         }
     } else if (warp >= kTcConv0 / 32) {
-        // converters: thread ct < 240 expands entry row ct of the tile, thread
-        // 240 + r query row r (r < nq); threads past 367 only take part in the
-        // warps' barrier arrivals
+        // converters: thread ct < 224 expands entry row ct of the tile, thread
+        // 224 + r query row r (r < nq)
         const int ct = threadIdx.x - kTcConv0;
         const bool is_b = ct < kTcE;
         const int row = is_b ? ct : ct - kTcE;
         const bool active = is_b || row < a.nq;
-        int64_t i_u = 0, i_kc = 0;
-        const uint32_t* src_row = nullptr;
-        bool row_ok = false;
-        auto row_start = [&]() {
-            const int64_t unit = blockIdx.x + i_u * gridDim.x;
-            const int plane = (int)(unit & 1);
-            if (is_b) {
-                const int64_t e = (unit >> 1) * kTcE + row;
-                row_ok = e < a.n;
-                src_row = a.planes + (e * 2 + plane) * a.wp;
-            } else {
-                row_ok = true;
-                src_row = a.qplanes + ((int64_t)row * 2 + plane) * a.wp;
-            }
-        };
-        if (active && my_units > 0) row_start();
-        // the bits of the next K-slice of this thread's row (zeros past the
-        // row's end, for a missing entry and for inactive threads)
-        auto load_next = [&](uint4& lo, uint4& hi) {
-            lo = make_uint4(0, 0, 0, 0);
-            hi = lo;
-            if (active && i_u < my_units) {
-                const int64_t w = i_kc * kTcSliceWords;
-                if (row_ok) {
-                    if (w < a.wp) lo = ldg_stream(src_row + w);
-                    if (w + 4 < a.wp) hi = ldg_stream(src_row + w + 4);
-                }
-                if (++i_kc == nk) {
-                    i_kc = 0;
-                    ++i_u;
-                    if (i_u < my_units) row_start();
-                }
-            }
-        };
-        int s = 0;
-        uint32_t phase = 0;
-        const uint32_t dst = (is_b ? (uint32_t)kTcABytes : 0u) + row_offset(active ? row : 0);
+        const int srow = active ? row : 0;
+        const uint32_t dst = (is_b ? (uint32_t)kTcABytes : 0u) + row_offset(srow);
+        const uint32_t src = smem_u32(slots) + (is_b ? 0u : (uint32_t)kTcBBytes) + (uint32_t)(srow * 128);
         const uint32_t stage0 = smem_u32(stages);
-        // expand one K-slice into the next stage; false after an abort
-        auto step = [&](const uint4& lo, const uint4& hi) -> bool {
-            int ok = 1;
-            if (lane == 0) ok = mbar_wait(empty0 + 8 * s, phase ^ 1u, abort_flag);
-            ok = __shfl_sync(0xffffffffu, ok, 0);
-            if (!ok) {
-                if (lane == 0) {
-                    if (a.status[0] == 0) a.status[0] = 1;
-                    *abort_flag = 1;
+        int s = 0, slot = 0;
+        uint32_t phase = 0, bphase = 0;
+        bool ok = true;
+        for (int64_t u = 0; u < my_units && ok; ++u) {
+            for (int64_t kc = 0; kc < nk; ++kc) {
+                const int c4 = (int)(kc & 3);      // slice within the bit slot's chunk
+                int r = 1;
+                if (c4 == 0) {
+                    if (lane == 0) r = mbar_wait(bfull0 + 8 * slot, bphase, abort_flag);
+                    r = __shfl_sync(0xffffffffu, r, 0);
+                    if (!r) {
+                        ok = false;
+                        break;
+                    }
                 }
-                return false;
+                uint4 lo = make_uint4(0, 0, 0, 0), hi = lo;
+                if (active) {   // the slot holds the row's 128 bytes swizzled like the operands
+                    const uint32_t sb = src + (uint32_t)(slot * kTcSlotBytes);
+                    lo = ld_shared_v4(sb + (uint32_t)((((2 * c4) ^ (srow & 7)) & 7) << 4));
+                    hi = ld_shared_v4(sb + (uint32_t)((((2 * c4 + 1) ^ (srow & 7)) & 7) << 4));
+                }
+                if (lane == 0) r = mbar_wait(empty0 + 8 * s, phase ^ 1u, abort_flag);
+                r = __shfl_sync(0xffffffffu, r, 0);
+                if (!r) {
+                    ok = false;
+                    break;
+                }
+                if (active) expand_row(stage0 + (uint32_t)(s * kTcStageBytes) + dst, row, lo, hi);
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(full0 + 8 * s);
+                if (++s == kTcStages) {
+                    s = 0;
+                    phase ^= 1u;
+                }
+                if (c4 == 3 || kc == nk - 1) {   // the chunk's bits are no longer needed
+                    if (lane == 0) mbar_arrive(bempty0 + 8 * slot);
+                    if (++slot == kTcSlots) {
+                        slot = 0;
+                        bphase ^= 1u;
+                    }
+                }
             }
-            if (active) expand_row(stage0 + (uint32_t)(s * kTcStageBytes) + dst, row, lo, hi);
-            fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(full0 + 8 * s);
-            if (++s == kTcStages) {
-                s = 0;
-                phase ^= 1u;
-            }
-            return true;
-        };
-        uint4 p0l, p0h, p1l, p1h, p2l, p2h;
-        load_next(p0l, p0h);
-        load_next(p1l, p1h);
-        load_next(p2l, p2h);
-        for (int64_t it = 0; it < total; it += 3) {
-            if (!step(p0l, p0h)) break;
-            load_next(p0l, p0h);
-            if (it + 1 >= total) break;
-            if (!step(p1l, p1h)) break;
-            load_next(p1l, p1h);
-            if (it + 2 >= total) break;
-            if (!step(p2l, p2h)) break;
-            load_next(p2l, p2h);
+        }
+        if (!ok && lane == 0) {
+            if (a.status[0] == 0) a.status[0] = 1;
+            *abort_flag = 1;
         }
     }
 
@@ -470,12 +525,32 @@ int tc_scan_max_queries() { return kTcMaxN; }
 
 int64_t tc_counts_stride(int64_t n) { return (n + 3) / 4 * 4; }
 
+// 3-D map [rows][2 planes][wp words] of uint32 with a box of 32 words x 1
+// plane x box_rows rows, 128-byte swizzle; out-of-range rows and words read
+// as zeros.
+static bool make_bits_map(CUtensorMap* m, const void* base, int64_t wp, int64_t rows, int box_rows)
+{
+    EncodeTiledFn enc = tensor_map_encoder();
+    if (!enc) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)wp, 2, (cuuint64_t)rows};
+    const cuuint64_t strides[2] = {(cuuint64_t)wp * 4, (cuuint64_t)wp * 8};
+    const cuuint32_t box[3] = {(cuuint32_t)kTcChunkWords, 1, (cuuint32_t)box_rows};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void*>(base), dims, strides, box,
+               estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream)
 {
-    if (a.nq < 1 || a.nq > kTcMaxN || a.n < 1 || a.wp < 4 || a.wp % 4 != 0 ||
-        a.stride < a.n || a.stride % 4 != 0 ||
+    if (a.nq < 1 || a.nq > kTcMaxN || a.n < 1 || a.n > INT32_MAX || a.wp < kTcChunkWords ||
+        a.wp % 4 != 0 || a.stride < a.n || a.stride % 4 != 0 ||
         (reinterpret_cast<uintptr_t>(a.planes) & 15) || (reinterpret_cast<uintptr_t>(a.qplanes) & 15) ||
         (reinterpret_cast<uintptr_t>(a.counts) & 15))
+        return cudaErrorInvalidValue;
+    CUtensorMap tm_db, tm_q;
+    if (!make_bits_map(&tm_db, a.planes, a.wp, a.n, kTcE) ||
+        !make_bits_map(&tm_q, a.qplanes, a.wp, a.nq, a.nq))
         return cudaErrorInvalidValue;
     const size_t smem = smem_bytes();
     cudaError_t err = cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -484,9 +559,11 @@ cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream)
     const int64_t nunits = (a.n + kTcE - 1) / kTcE * 2;
     if (grid > nunits) grid = (int)nunits;
     if (grid < 1) grid = 1;
-    tc_scan_kernel<<<grid, kTcThreads, smem, stream>>>(a);
+    tc_scan_kernel<<<grid, kTcThreads, smem, stream>>>(tm_db, tm_q, a);
     return cudaGetLastError();
 }
+
+int64_t tc_scan_min_words() { return kTcChunkWords; }
 
 cudaError_t launch_tc_select(const QueryTask* tasks, int task0, int nq, const uint32_t* counts,
                              int64_t n, int64_t stride, cudaStream_t stream)

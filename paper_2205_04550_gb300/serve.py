@@ -21,7 +21,10 @@ Two query paths, matching the library's modes:
 Results are per request (the ranked hits), latency is completion minus
 arrival, and ``stats()`` reports p50/p99 latency and completed queries/s.
 Batch composition never changes a request's result: every query is computed
-independently (tested).
+independently (tested).  Each batch's span on its lane's stream (from its
+first copy to its last kernel) is recorded with CUDA events, so
+``device_overlaps()`` can show that batches of different lanes overlapped on
+the device.
 """
 from __future__ import annotations
 
@@ -110,6 +113,10 @@ class Server:
         self._lock = threading.Lock()
         self._lane_free = threading.Condition(self._lock)
         self._done: list[_Request] = []
+        self._spans: list = []          # (lane, start event, end event) per batch
+        self._ref = torch.cuda.Event(enable_timing=True)
+        self._ref.record()
+        torch.cuda.synchronize()
         self._stop = False
         self._t0 = time.perf_counter()
         self._sched = threading.Thread(target=self._schedule, daemon=True)
@@ -147,6 +154,28 @@ class Server:
     def reset_stats(self):
         with self._lock:
             self._done = []
+            self._spans = []
+
+    def device_spans(self) -> list:
+        """[(lane, start_ms, end_ms)] of the recorded batches on the device,
+        relative to the server's start (synchronises the device)."""
+        self.torch.cuda.synchronize()
+        with self._lock:
+            spans = list(self._spans)
+        return [(lane, self._ref.elapsed_time(a), self._ref.elapsed_time(b))
+                for lane, a, b in spans]
+
+    def device_overlaps(self) -> int:
+        """Pairs of batches from different lanes whose device spans overlap."""
+        spans = sorted(self.device_spans(), key=lambda t: t[1])
+        pairs = 0
+        for i, (li, a0, a1) in enumerate(spans):
+            for lj, b0, b1 in spans[i + 1:]:
+                if b0 >= a1:
+                    break
+                if lj != li:
+                    pairs += 1
+        return pairs
 
     def close(self):
         self._stop = True
@@ -215,7 +244,10 @@ class Server:
         torch = self.torch
         try:
             n = len(batch)
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(lane.stream):
+                ev0.record(lane.stream)
                 for i, r in enumerate(batch):
                     lane.pinned[i, :r.patient.size].numpy()[:] = r.patient
                     lane.slots[i, :r.patient.size].copy_(lane.pinned[i, :r.patient.size],
@@ -224,6 +256,7 @@ class Server:
                 if self.mode == DBQ_MODE_EXACT:
                     lane.plan.query(which, [lane.slots[i] for i in range(n)], lane.hits[:n],
                                     kind=_dbq.DBQ_F32, stream=lane.stream)
+                    ev1.record(lane.stream)
                     lane.hits_host[:n].copy_(lane.hits[:n], non_blocking=True)
                     lane.stream.synchronize()
                     hits = lane.hits_host[:n].numpy().view(HIT_DTYPE).reshape(n, self.k)
@@ -236,12 +269,15 @@ class Server:
                             [lane.slots[i] for i in idx], self.k, self.mode,
                             self.n_candidates, kind=_dbq.DBQ_F32, stream=lane.stream)
                         hits[idx] = h
+                    ev1.record(lane.stream)
             now = time.perf_counter()
             for i, r in enumerate(batch):
                 r.t_done = now
                 r.future.set_result(hits[i].copy())
             with self._lock:
                 self._done.extend(batch)
+                if len(self._spans) < 100_000:
+                    self._spans.append((self._lanes.index(lane), ev0, ev1))
         except Exception as exc:  # deliver the failure to every request of the batch
             for r in batch:
                 if not r.future.done():

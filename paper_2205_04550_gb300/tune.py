@@ -1,12 +1,20 @@
 """Autotuner for query plans.
 
-The persistent plan launch splits every query into work items (slices of
-its database entries); how many items per SM balance the grid best depends
-on the GPU, the databases' sizes and resolutions, the batch size and whether
-the scans are sparse.  ``tune_plan`` times the candidate settings with CUDA
-events on the real inputs, keeps the fastest, and caches it per
-(GPU, workload key) in a JSON file so later runs reuse it without timing.
-Every setting returns identical hits; only the speed differs.
+Two choices are tuned, both timed with CUDA events on the real inputs and
+cached in a JSON file so later runs reuse them without timing; every setting
+returns identical hits, only the speed differs.
+
+* Per database, the batch size from which its dense queries are scanned all
+  at once as a tensor-core contraction instead of one CUDA-core loop per
+  query (DBQ_PLAN_TC_MIN_QUERIES for that database).  The loop's cost grows
+  with the batch (one AND + POPC per word per query) while the contraction's
+  barely does, and where they cross depends on the GPU and on the database's
+  resolution and size: ``tune_crossover`` times both paths at batch sizes
+  TC_BATCHES and keeps the smallest at which the contraction is no slower
+  (cached per GPU, grid and entry count).
+* The number of work items per SM of the persistent CUDA-core launch, which
+  balances the grid differently for each mix of databases, batch size and
+  sparse setting (``tune_plan``, cached per workload).
 """
 from __future__ import annotations
 
@@ -17,6 +25,7 @@ import threading
 _HERE = os.path.dirname(os.path.abspath(__file__))
 CACHE = os.path.join(_HERE, "_build", "autotune.json")
 CANDIDATES = (1, 2, 4, 8, 16, 32, 64)
+TC_BATCHES = (2, 4, 6, 8, 12, 16, 24, 32)
 _lock = threading.Lock()
 
 
@@ -49,17 +58,86 @@ def workload_key(plan, which, sparse_flags=None) -> str:
                       sort_keys=True)
 
 
-def tune_plan(plan, which, patients_dev, hits_dev, candidates=CANDIDATES, reps: int = 3,
-              use_cache: bool = True, sparse_flags=None) -> dict:
-    """Choose DBQ_PLAN_ITEMS_PER_SM for this plan and workload; sets it on the
-    plan and returns {"items_per_sm": best, "ms": {candidate: ms}}."""
+def _time_plan(plan, which, patients, hits_dev, reps: int, stream) -> float:
     import torch
-    key = workload_key(plan, list(which), sparse_flags)
+    plan.query(which, patients, hits_dev, stream=stream)             # warm-up
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(reps):
+        plan.query(which, patients, hits_dev, stream=stream)
+    end.record(stream)
+    torch.cuda.synchronize()
+    return start.elapsed_time(end) / reps
+
+
+def crossover_key(db) -> str:
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return json.dumps({"gpu": props.name, "sms": props.multi_processor_count,
+                       "crossover": [list(db.shape), db.capacity]}, sort_keys=True)
+
+
+def tune_crossover(plan, d: int, patients_dev, hits_dev, batches=TC_BATCHES, reps: int = 2,
+                   use_cache: bool = True) -> dict:
+    """The smallest batch of TC_BATCHES at which database ``d`` of the plan
+    is scanned no slower as a tensor-core contraction than by the CUDA-core
+    loop; sets it as that database's threshold and returns {"tc_min": B,
+    "ms": {B: [contraction, loop]}}.  ``patients_dev`` are patients of
+    database d (cycled to fill a batch); ``hits_dev`` holds k hits for up to
+    max(batches) queries.  If the loop wins at every size, the threshold is
+    twice the largest size tried."""
+    import torch
+    db = plan.databases[d]
+    key = crossover_key(db)
+    if use_cache:
+        hit = _load_cache().get(key)
+        if hit:
+            plan.set_tc_min_queries(int(hit["tc_min"]), db=d)
+            return dict(hit, cached=True)
+    stream = torch.cuda.current_stream()
+    timings, best = {}, None
+    for b in batches:
+        if b > plan.max_queries:
+            break
+        pats = [patients_dev[i % len(patients_dev)] for i in range(b)]
+        which = [d] * b
+        plan.set_tc_min_queries(1, db=d)
+        t_tc = _time_plan(plan, which, pats, hits_dev, reps, stream)
+        plan.set_tc_min_queries(0, db=d)
+        t_cc = _time_plan(plan, which, pats, hits_dev, reps, stream)
+        timings[str(b)] = [t_tc, t_cc]
+        if t_tc <= t_cc:
+            best = b
+            break
+    if best is None:
+        best = 2 * max(batches)
+    plan.set_tc_min_queries(best, db=d)
+    out = {"tc_min": best, "ms": timings}
+    _store(key, out)
+    return dict(out, cached=False)
+
+
+def tune_plan(plan, which, patients_dev, hits_dev, candidates=CANDIDATES, reps: int = 3,
+              use_cache: bool = True, sparse_flags=None, crossover: bool = True) -> dict:
+    """Choose the plan's settings for this workload: first, per database with
+    dense queries, the tensor-core crossover (``tune_crossover``), then
+    DBQ_PLAN_ITEMS_PER_SM; sets them on the plan and returns
+    {"items_per_sm": best, "ms": {candidate: ms}, "tc_min": {db: B}}."""
+    import torch
+    which = list(which)
+    tc_min = {}
+    if crossover:
+        for d, db in enumerate(plan.databases):
+            mine = [patients_dev[q] for q in range(len(which)) if which[q] == d]
+            if mine and not sparse_flags:
+                tc_min[str(d)] = tune_crossover(plan, d, mine, hits_dev,
+                                                use_cache=use_cache)["tc_min"]
+    key = workload_key(plan, which, sparse_flags)
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
             plan.set_items_per_sm(int(hit["items_per_sm"]))
-            return dict(hit, cached=True)
+            return dict(hit, cached=True, tc_min=tc_min)
     stream = torch.cuda.current_stream()
     timings = {}
     for c in candidates:
@@ -76,4 +154,4 @@ def tune_plan(plan, which, patients_dev, hits_dev, candidates=CANDIDATES, reps: 
     plan.set_items_per_sm(best)
     out = {"items_per_sm": best, "ms": {str(c): t for c, t in timings.items()}}
     _store(key, out)
-    return dict(out, cached=False)
+    return dict(out, cached=False, tc_min=tc_min)

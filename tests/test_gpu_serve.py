@@ -59,7 +59,7 @@ def test_results_in_the_mix_equal_results_alone(dbs, mode):
         srv.close()
     assert st["completed"] == len(reqs) and st["p99_ms"] >= st["p50_ms"] > 0
     databases = [d1, d2]
-    for i in range(0, len(reqs), 7):
+    for i in range(len(reqs)):
         p, db = reqs[i]
         if mode == "exact":
             alone, _ = databases[db].query(p, 10)
@@ -114,10 +114,32 @@ def test_hash_mode_in_the_mix_equals_alone():
         finally:
             srv.close()
         databases = [d1, d2]
-        for i in range(0, len(reqs), 5):
+        for i in range(len(reqs)):
             p, db = reqs[i]
             alone, _ = databases[db].query_batch([p], 10, DBQ_MODE_HASH, 64)
             assert results[i].tobytes() == alone[0].tobytes(), i
     finally:
         d1.close()
         d2.close()
+
+
+def test_batches_of_different_lanes_overlap_on_the_device(dbs):
+    """Requests that arrive while earlier ones are on the GPU run on the
+    other lane at the same time: a burst of small batches leaves at least one
+    pair of batches from different lanes whose device spans overlap, and
+    every result still equals the query alone."""
+    (d1, v1), (d2, v2) = dbs
+    reqs = _requests(v1, v2, 96, seed=21)
+    srv = serve.Server([d1, d2], mode="exact", k=10, max_batch=4, lanes=2, max_wait_s=0.0)
+    try:
+        results = serve.run_open_loop(srv, reqs, np.zeros(len(reqs)))
+        overlaps = srv.device_overlaps()
+        spans = srv.device_spans()
+    finally:
+        srv.close()
+    assert len({lane for lane, _, _ in spans}) == 2
+    assert overlaps > 0, spans[:8]
+    databases = [d1, d2]
+    for i, (p, db) in enumerate(reqs):
+        alone, _ = databases[db].query(p, 10)
+        assert results[i].tobytes() == alone.tobytes(), i
