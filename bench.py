@@ -879,7 +879,7 @@ def run_serve(args, wl, torch):
         d = 0 if rng.random() < wl["share"][0] else 1
         reqs.append((host[d][rng.integers(0, len(host[d]))], d))
     arrivals = serve.poisson_arrivals(wl["rate"], count, seed=7)
-    out = {}
+    out, sweeps = {}, {}
     for mode in ("exact", "embed_bf16"):
         srv = serve.Server(dbs, mode=mode, k=wl["k"], n_candidates=wl["candidates"],
                            max_batch=wl["max_batch"], lanes=2)
@@ -889,6 +889,26 @@ def run_serve(args, wl, torch):
             t0 = time.perf_counter()
             serve.run_open_loop(srv, reqs, arrivals)
             out[mode] = dict(srv.stats(), wall_s=time.perf_counter() - t0)
+            # open-loop rate sweep: offered load doubled until the server falls
+            # behind (completed < 95 % of offered) or p99 passes the SLO
+            sweep = []
+            rate = wl["rate"]
+            while rate <= wl.get("sweep_max_rate", 25600):
+                n = int(min(len(reqs), max(200, rate * wl.get("sweep_seconds", 1.5))))
+                srv.reset_stats()
+                serve.run_open_loop(srv, reqs[:n], serve.poisson_arrivals(rate, n, seed=11))
+                st = srv.stats()
+                sweep.append({"offered_per_s": rate, "requests": n,
+                              "queries_per_s": st["queries_per_s"], "p50_ms": st["p50_ms"],
+                              "p99_ms": st["p99_ms"]})
+                if st["queries_per_s"] < 0.95 * rate or st["p99_ms"] > wl.get("slo_p99_ms", 100.0):
+                    break
+                rate *= 2
+            ok = [r for r in sweep if r["queries_per_s"] >= 0.95 * r["offered_per_s"]
+                  and r["p99_ms"] <= wl.get("slo_p99_ms", 100.0)]
+            sweeps[mode] = {"slo_p99_ms": wl.get("slo_p99_ms", 100.0), "points": sweep,
+                            "max_sustained_per_s": ok[-1]["offered_per_s"] if ok else None,
+                            "peak_completed_per_s": max(r["queries_per_s"] for r in sweep)}
         finally:
             srv.close()
     line = {"metric": METRIC, "value": out["exact"]["queries_per_s"], "unit": "queries/s",
@@ -898,8 +918,10 @@ def run_serve(args, wl, torch):
             "config": {"workload": args.workload, "desc": wl["desc"], "requests": count,
                        "rate_per_s": wl["rate"], "max_batch": wl["max_batch"]},
             "exact": out["exact"], "embed_bf16": out["embed_bf16"],
+            "capacity_sweep": sweeps,
             "note": "offered load 200 queries/s: queries/s is bounded by the arrival rate; "
-                    "latency is the measure"}
+                    "latency is the measure there; capacity_sweep doubles the offered "
+                    "load until completions fall below 95 % of it or p99 exceeds the SLO"}
     for d in dbs:
         d.close()
     if rank == 0:

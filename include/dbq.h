@@ -274,12 +274,15 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
  * db_plan_set     DBQ_PLAN_ITEMS_PER_SM: work items (query slices) per SM
  *                 of one launch (default 4; chosen by the autotuner).
  *                 DBQ_PLAN_TC_MIN_QUERIES: a database queried by at least
- *                 this many dense (not DBQ_OPT_SPARSE) queries in one call,
- *                 with V <= 2^24 voxels, is scanned for all of them at once
+ *                 this many queries in one call, with V <= 2^24 voxels and
+ *                 at least 32 words per plane, is scanned for all of them at once
  *                 as a contraction on the tensor cores (the intersections
  *                 of Section 2.3 as 0/1 dot products over the voxels, exact
  *                 in binary32; up to 128 queries per pass), then scored and
  *                 ranked per query -- the same hits as the CUDA-core loop.
+ *                 A contraction reads every word, whatever the database's
+ *                 DBQ_OPT_SPARSE setting (which then only selects the
+ *                 CUDA-core loop's variant below the threshold).
  *                 Default 16; 0 keeps every query on the CUDA-core loop.
  * db_plan_query   patients_dev[nq] device pointers (kind DBQ_F32 / DBQ_F16
  *                 volumes or DBQ_BITS planes of the query's database),

@@ -1529,7 +1529,7 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
         const dbq_db* db = p->dbs[d];
         const int thr = (size_t)d < p->tc_min_db.size() && p->tc_min_db[(size_t)d] >= 0
                             ? p->tc_min_db[(size_t)d] : p->tc_min;
-        use_tc[d] = p->tc_rows > 0 && thr > 0 && per_db[d] >= thr && !db->sparse &&
+        use_tc[d] = p->tc_rows > 0 && thr > 0 && per_db[d] >= thr &&
                     db->v <= ((int64_t)1 << 24) && db->wp >= dbq::tc_scan_min_words();
     }
     // work-item budget: items_per_sm * SMs, shared in proportion to bytes

@@ -4,9 +4,10 @@ Two choices are tuned, both timed with CUDA events on the real inputs and
 cached in a JSON file so later runs reuse them without timing; every setting
 returns identical hits, only the speed differs.
 
-* Per database, the batch size from which its dense queries are scanned all
-  at once as a tensor-core contraction instead of one CUDA-core loop per
-  query (DBQ_PLAN_TC_MIN_QUERIES for that database).  The loop's cost grows
+* Per database, the batch size from which its queries are scanned all at
+  once as a tensor-core contraction instead of one CUDA-core loop per query
+  (DBQ_PLAN_TC_MIN_QUERIES for that database; the loop's cost, and so the
+  crossover, differs between the dense and the sparse loop).  The loop's cost grows
   with the batch (one AND + POPC per word per query) while the contraction's
   barely does, and where they cross depends on the GPU and on the database's
   resolution and size: ``tune_crossover`` times both paths at batch sizes
@@ -70,25 +71,27 @@ def _time_plan(plan, which, patients, hits_dev, reps: int, stream) -> float:
     return start.elapsed_time(end) / reps
 
 
-def crossover_key(db) -> str:
+def crossover_key(db, sparse=False) -> str:
     import torch
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     return json.dumps({"gpu": props.name, "sms": props.multi_processor_count,
-                       "crossover": [list(db.shape), db.capacity]}, sort_keys=True)
+                       "crossover": [list(db.shape), db.capacity], "sparse": bool(sparse)},
+                      sort_keys=True)
 
 
 def tune_crossover(plan, d: int, patients_dev, hits_dev, batches=TC_BATCHES, reps: int = 2,
-                   use_cache: bool = True) -> dict:
+                   use_cache: bool = True, sparse: bool = False) -> dict:
     """The smallest batch of TC_BATCHES at which database ``d`` of the plan
     is scanned no slower as a tensor-core contraction than by the CUDA-core
     loop; sets it as that database's threshold and returns {"tc_min": B,
     "ms": {B: [contraction, loop]}}.  ``patients_dev`` are patients of
     database d (cycled to fill a batch); ``hits_dev`` holds k hits for up to
     max(batches) queries.  If the loop wins at every size, the threshold is
-    twice the largest size tried."""
+    twice the largest size tried.  ``sparse`` names the database's
+    DBQ_OPT_SPARSE setting, which changes the loop's cost (cached apart)."""
     import torch
     db = plan.databases[d]
-    key = crossover_key(db)
+    key = crossover_key(db, sparse)
     if use_cache:
         hit = _load_cache().get(key)
         if hit:
@@ -120,7 +123,7 @@ def tune_crossover(plan, d: int, patients_dev, hits_dev, batches=TC_BATCHES, rep
 def tune_plan(plan, which, patients_dev, hits_dev, candidates=CANDIDATES, reps: int = 3,
               use_cache: bool = True, sparse_flags=None, crossover: bool = True) -> dict:
     """Choose the plan's settings for this workload: first, per database with
-    dense queries, the tensor-core crossover (``tune_crossover``), then
+    queries, the tensor-core crossover (``tune_crossover``), then
     DBQ_PLAN_ITEMS_PER_SM; sets them on the plan and returns
     {"items_per_sm": best, "ms": {candidate: ms}, "tc_min": {db: B}}."""
     import torch
@@ -129,9 +132,9 @@ def tune_plan(plan, which, patients_dev, hits_dev, candidates=CANDIDATES, reps: 
     if crossover:
         for d, db in enumerate(plan.databases):
             mine = [patients_dev[q] for q in range(len(which)) if which[q] == d]
-            if mine and not sparse_flags:
-                tc_min[str(d)] = tune_crossover(plan, d, mine, hits_dev,
-                                                use_cache=use_cache)["tc_min"]
+            if mine:
+                tc_min[str(d)] = tune_crossover(plan, d, mine, hits_dev, use_cache=use_cache,
+                                                sparse=bool(sparse_flags))["tc_min"]
     key = workload_key(plan, which, sparse_flags)
     if use_cache:
         hit = _load_cache().get(key)

@@ -135,6 +135,7 @@ def test_plan_sparse_items_ordered_by_support(torch, two_dbs):
     which = [which[i] for i in perm]
     k = 12
     with Plan([d1, d2], len(pats), k) as plan:
+        plan.set_tc_min_queries(0)                  # the CUDA-core loop's item ordering
         for ips in (2, 16):
             plan.set_items_per_sm(ips)
             dev = [torch.from_numpy(p).cuda() for p in pats]
@@ -173,10 +174,12 @@ def test_plan_errors(torch, two_dbs):
         plan.status()                                       # nothing timed out
 
 
-def _run_plan(torch, dbs, which, pats, k, tc_min, items_per_sm=4):
+def _run_plan(torch, dbs, which, pats, k, tc_min, items_per_sm=4, tc_min_db=None):
     with Plan(dbs, len(pats), k) as plan:
         plan.set_items_per_sm(items_per_sm)
         plan.set_tc_min_queries(tc_min)
+        for d, v in (tc_min_db or {}).items():
+            plan.set_tc_min_queries(v, db=d)
         dev = [torch.from_numpy(p).cuda() for p in pats]
         hits = torch.zeros((len(pats), k * 40), dtype=torch.uint8, device="cuda")
         plan.query(which, dev, hits)
@@ -227,7 +230,8 @@ def test_plan_tensor_core_ragged_sizes(torch, shape, n):
         allp = pats + sp
         which = [0] * len(pats) + [1] * len(sp)
         k = 9
-        tc = _run_plan(torch, [db, ds], which, allp, k, tc_min=16)
+        # the sparse database stays on the CUDA-core loop (its own threshold 0)
+        tc = _run_plan(torch, [db, ds], which, allp, k, tc_min=16, tc_min_db={1: 0})
         cc = _run_plan(torch, [db, ds], which, allp, k, tc_min=0)
     assert tc.tobytes() == cc.tobytes()
     for q in list(range(0, 131, 13)) + [130]:
@@ -349,3 +353,39 @@ def test_plan_tensor_core_timeout_path_reports_and_recovers(torch, two_dbs):
         got = hits.cpu().numpy().view(_dbq.HIT_DTYPE)
         for q, p in enumerate(pats):
             assert_hits_equal(got[q], oracle.query(v1, p, T1, T2, k), k)
+
+
+def test_plan_sparse_database_on_the_tensor_cores(torch, two_dbs):
+    """A database with the sparse option and many queries in one call is
+    scanned as a contraction (which reads every word) when it passes its
+    threshold: the hits equal the sparse CUDA-core loop's and the oracle's.
+    Per-database thresholds: database 0 on the contraction, database 1 kept
+    on the loop."""
+    (d1, v1), (d2, v2) = two_dbs
+    d1.set_sparse(True)
+    d2.set_sparse(True)
+    try:
+        rng = np.random.default_rng(31)
+        pats = _patients(rng, v1, 20) + _patients(rng, v2, 20)
+        which = [0] * 20 + [1] * 20
+        k = 7
+        tc = _run_plan(torch, [d1, d2], which, pats, k, tc_min=1, tc_min_db={1: 0})
+        cc = _run_plan(torch, [d1, d2], which, pats, k, tc_min=0)
+    finally:
+        d1.set_sparse(False)
+        d2.set_sparse(False)
+    assert tc.tobytes() == cc.tobytes()
+    for q in (0, 7, 19, 20, 39):
+        vols = v1 if which[q] == 0 else v2
+        assert_hits_equal(tc[q], oracle.query(vols, pats[q], T1, T2, k), k)
+
+
+def test_plan_per_database_threshold_errors(torch, two_dbs):
+    (d1, _), (d2, _) = two_dbs
+    with Plan([d1, d2], 4, 3) as plan:
+        with pytest.raises(DbqError) as e:
+            plan.set_tc_min_queries(5, db=2)
+        assert e.value.status == _dbq.DBQ_ERANGE
+        with pytest.raises(DbqError):
+            plan.set_tc_min_queries(-2, db=0)
+        plan.set_tc_min_queries(-1, db=0)             # back to the plan-wide value
