@@ -104,6 +104,10 @@ WORKLOADS = {
                            share=[0.7, 0.3], queries=128, k=10, t1=0.6, t2=0.25,
                            desc="plan_mix with 8,000 x 64^3 and 1,000 x 128^3 (1.0 GB on the "
                                 "device, profiling size)"),
+    "plan_tc_17k_64": dict(mix=[dict(shape=(64, 64, 64), n=17_024)], share=[1.0], queries=128,
+                           k=10, t1=0.6, t2=0.25,
+                           desc="128 queries against 17,024 x 64^3 bit-packed (1.1 GB, profiling "
+                                "size: 152 work units of the tensor-core contraction, one per SM)"),
     "ds_2k_128": dict(shape=(128, 128, 128), n=2000, k=15, t1=0.6, t2=0.25, patients=50,
                       desc="ds_agreement on 2,000 x 128^3 and 50 patients (profiling size)"),
     "exact_packed_1k_64": dict(shape=(64, 64, 64), n=1024, k=10, t1=0.6, t2=0.25,
@@ -847,8 +851,11 @@ def run_plan_mix(args, wl, torch):
             "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": args.workload, "desc": wl["desc"],
                        "queries_per_launch": nq,
-                       "queries_per_db": [which.count(0), which.count(1)],
-                       "l2": "inputs larger than L2 (32.8 GB of packed databases); no flush"},
+                       "queries_per_db": [which.count(d) for d in range(len(wl["mix"]))],
+                       "l2": "inputs larger than L2 ({:.1f} GB of packed databases); no "
+                             "flush".format(sum(part["n"] * 32 * ((part["shape"][0] * part["shape"][1]
+                                                                   * part["shape"][2] + 127) // 128)
+                                                for part in wl["mix"]) / 1e9)},
             "dense": dense, "sparse": results["sparse"],
             # per dense launch: a patient-packing kernel per database, and for
             # each database past its tuned crossover the tensor-core
@@ -1019,7 +1026,7 @@ def main(argv=None):
         return run_embed(args, wl, torch)
     if args.workload == "pde_db_128":
         return run_pde(args, wl, torch)
-    if args.workload in ("plan_mix", "plan_mix_small"):
+    if args.workload in ("plan_mix", "plan_mix_small", "plan_tc_17k_64"):
         return run_plan_mix(args, wl, torch)
     if args.workload == "serve_mix":
         return run_serve(args, wl, torch)
