@@ -127,6 +127,11 @@ void scan_packed_chunking(int wp4, int* chunk4, int* nchunks)
     *nchunks = (wp4 + c4 - 1) / c4;
 }
 
+bool topk_one_level_merge(int lists, int k)
+{
+    return (int64_t)lists * k + k + kThreads / 32 <= kTopkCap;
+}
+
 int scan_packed_grid(int device)
 {
     int sms = 0;

@@ -99,17 +99,66 @@ __device__ __forceinline__ void bitonic_sort_topk(TopK& t, int n)
 }
 
 // Merge the appended candidates into slots [0, k).  Starts and ends with a
-// barrier.
+// barrier.  When the k slots and the appended candidates fit in one element
+// per thread, every element's new position is counted directly -- its rank
+// among the sorted k (a binary search, or its own slot) plus the appended
+// candidates better than it -- and written in one step: three barriers in all,
+// where a bitonic sort of the same elements takes one per stage (15 for 32
+// elements, 45 for 512), and a barrier of a 1024-thread block is the
+// expensive part here.  Larger rounds use the bitonic sort.
 __device__ __forceinline__ void topk_flush(TopK& t, int k)
 {
     __syncthreads();
     const int added = t.misc[0];
     if (added > 0) {
-        const int n2 = next_pow2(k + added);
-        bitonic_sort_topk(t, n2);
-        for (int i = k + threadIdx.x; i < n2; i += blockDim.x) topk_clear_slot(t, i);
+        const int n = k + added;
+        if (n <= (int)blockDim.x) {
+            const int i = threadIdx.x;
+            uint64_t ki = 0, p0 = 0, p1 = 0;
+            int64_t ii = kSentinelIndex;
+            int rank = k;
+            if (i < n) {
+                ki = t.key[i];
+                ii = t.idx[i];
+                p0 = t.pay0[i];
+                p1 = t.pay1[i];
+                if (ii != kSentinelIndex) {
+                    int r;
+                    if (i < k) {
+                        r = i;                      // the sorted slots before it are better
+                    } else {                        // sorted slots better than it
+                        int lo = 0, hi = k;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (better(t.key[mid], t.idx[mid], ki, ii)) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        r = lo;
+                    }
+                    for (int j = k; j < n && r < k; ++j)      // appended candidates better than it
+                        if (j != i && better(t.key[j], t.idx[j], ki, ii)) ++r;
+                    rank = r;
+                }
+            }
+            __syncthreads();   // every element read before any is moved
+            if (i < n) {
+                // ranks are distinct and below k, so no move lands in [k, n),
+                // which is cleared; slots of [0, k) left unwritten already hold
+                // sentinels (the k best never shrink)
+                if (rank < k) {
+                    t.key[rank] = ki;
+                    t.idx[rank] = ii;
+                    t.pay0[rank] = p0;
+                    t.pay1[rank] = p1;
+                }
+                if (i >= k) topk_clear_slot(t, i);
+            }
+        } else {
+            const int n2 = next_pow2(n);
+            bitonic_sort_topk(t, n2);
+            for (int i = k + threadIdx.x; i < n2; i += blockDim.x) topk_clear_slot(t, i);
+        }
     }
-    __syncthreads();
     if (threadIdx.x == 0) t.misc[0] = 0;
     __syncthreads();
 }
@@ -148,68 +197,114 @@ __device__ __forceinline__ bool topk_publish(TopK& t, int k, Cand* cand, unsigne
 }
 
 // Merge of m / k published lists, each sorted best first (every list comes
-// from a flushed or merged TopK), when they fit in half of the shared slots:
-// every candidate's final position is its position in its own list plus the
-// number of candidates of each other list that are better (a binary search
-// per list), and the first k positions are written to the upper half of the
-// slots, then moved down to [0, k).  The order is strict (entry indices are
-// unique), so positions never collide; sentinels are never better than a
-// real candidate and are not placed.
+// from a flushed or merged TopK), when they fit in the shared slots with
+// room for k more and one entry per warp.  The k-th element of every list
+// bounds the answer: the list with the best k-th element alone holds k
+// candidates at least that good, so no candidate worse than T (the best of
+// the k-th elements) can be among the k best.  The few candidates at least
+// as good as T are ranked exactly -- a candidate's final position is the
+// number of candidates better than it, summed over the lists by binary
+// searches that the 32 lanes of a warp share -- and written at that
+// position.  The order is strict (entry indices are unique), so positions
+// never collide; sentinels are never better than a real candidate and are not
+// placed.  Five barriers, whatever the number of lists.
 __device__ __forceinline__ bool topk_merge_sorted(TopK& t, int k, const Cand* cand, int64_t m)
 {
-    constexpr int kHalf = kTopkCap / 2;
-    if (m % k != 0 || m > kHalf || k > kHalf) return false;
-    const int lists = (int)(m / k);
+    const int nwarps = (int)(blockDim.x >> 5);
+    if (m % k != 0 || m + k + nwarps > kTopkCap) return false;
+    const int mm = (int)m;
+    const int lists = mm / k;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) {
-        if (i < (int)m) {
+        if (i < mm) {
             const Cand* src = cand + i;
             t.key[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->key));
             t.idx[i] = __ldcg(reinterpret_cast<const long long*>(&src->index));
             t.pay0[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay0));
             t.pay1[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay1));
-        } else if (i >= kHalf) {
-            topk_clear_slot(t, i);
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < (int)m; i += blockDim.x) {
-        const uint64_t ck = t.key[i];
-        const int64_t ci = t.idx[i];
-        if (ci == kSentinelIndex) continue;
-        const int own = i / k;
-        int r = i - own * k;
-        for (int l = 0; l < lists && r < k; ++l) {
-            if (l == own) continue;
-            // the candidates of list l better than this one form a prefix
-            int lo = 0, hi = k;
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                const int j = l * k + mid;
-                if (better(t.key[j], t.idx[j], ck, ci)) lo = mid + 1;
-                else hi = mid;
-            }
-            r += lo;
-        }
-        if (r < k) {
-            t.key[kHalf + r] = ck;
-            t.idx[kHalf + r] = ci;
-            t.pay0[kHalf + r] = t.pay0[i];
-            t.pay1[kHalf + r] = t.pay1[i];
-        }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < kHalf; i += blockDim.x) {
-        if (i < k) {
-            t.key[i] = t.key[kHalf + i];
-            t.idx[i] = t.idx[kHalf + i];
-            t.pay0[i] = t.pay0[kHalf + i];
-            t.pay1[i] = t.pay1[kHalf + i];
         } else {
             topk_clear_slot(t, i);
         }
     }
     __syncthreads();
-    for (int i = kHalf + threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
+    // T: the best k-th element over the lists (block reduction)
+    uint64_t tk = kSentinelKey;
+    int64_t ti = kSentinelIndex;
+    for (int l = threadIdx.x; l < lists; l += blockDim.x) {
+        const int j = l * k + k - 1;
+        if (better(t.key[j], t.idx[j], tk, ti)) {
+            tk = t.key[j];
+            ti = t.idx[j];
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const uint64_t ok = __shfl_down_sync(0xffffffffu, tk, off);
+        const int64_t oi = __shfl_down_sync(0xffffffffu, ti, off);
+        if (better(ok, oi, tk, ti)) {
+            tk = ok;
+            ti = oi;
+        }
+    }
+    if (lane == 0) {
+        t.key[mm + k + warp] = tk;
+        t.idx[mm + k + warp] = ti;
+    }
+    __syncthreads();
+    tk = kSentinelKey;
+    ti = kSentinelIndex;
+    for (int w = 0; w < nwarps; ++w)
+        if (better(t.key[mm + k + w], t.idx[mm + k + w], tk, ti)) {
+            tk = t.key[mm + k + w];
+            ti = t.idx[mm + k + w];
+        }
+    // every candidate not worse than T: its exact rank, by one warp
+    for (int base = warp * 32; base < mm; base += (int)blockDim.x) {
+        const int i = base + lane;
+        uint64_t ck = 0;
+        int64_t ci = kSentinelIndex;
+        if (i < mm) {
+            ck = t.key[i];
+            ci = t.idx[i];
+        }
+        const bool keep = ci != kSentinelIndex && !better(tk, ti, ck, ci);
+        unsigned int todo = __ballot_sync(0xffffffffu, keep);
+        while (todo) {
+            const int src = __ffs(todo) - 1;
+            todo &= todo - 1;
+            const uint64_t xk = __shfl_sync(0xffffffffu, ck, src);
+            const int64_t xi = __shfl_sync(0xffffffffu, ci, src);
+            int r = 0;
+            for (int l = lane; l < lists; l += 32) {    // candidates of list l better than x
+                int lo = 0, hi = k;
+                while (lo < hi) {
+                    const int mid = (lo + hi) >> 1;
+                    const int j = l * k + mid;
+                    if (better(t.key[j], t.idx[j], xk, xi)) lo = mid + 1;
+                    else hi = mid;
+                }
+                r += lo;
+            }
+            r = __reduce_add_sync(0xffffffffu, r);
+            if (lane == src && r < k) {
+                t.key[mm + r] = ck;
+                t.idx[mm + r] = ci;
+                t.pay0[mm + r] = t.pay0[i];
+                t.pay1[mm + r] = t.pay1[i];
+            }
+        }
+    }
+    __syncthreads();
+    // move [m, m + k) to [0, k) (m >= k: the ranges do not overlap), then
+    // clear everything after the k slots
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        t.key[i] = t.key[mm + i];
+        t.idx[i] = t.idx[mm + i];
+        t.pay0[i] = t.pay0[mm + i];
+        t.pay1[i] = t.pay1[mm + i];
+    }
+    __syncthreads();
+    for (int i = k + threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
     if (threadIdx.x == 0) t.misc[0] = 0;
     __syncthreads();
     return true;
