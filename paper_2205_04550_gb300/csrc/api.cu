@@ -342,10 +342,7 @@ int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaSt
         a.counts_out = counts_out;
         a.sup_list = db->sparse ? db->plist : nullptr;
         a.sup_len = db->sparse ? db->plen : nullptr;
-        // one merge level when every CTA's list fits the last CTA's slots at
-        // once, two (groups first) otherwise
-        a.group_lists = (db->grid <= 8 * 63 && !dbq::topk_one_level_merge(db->grid, k))
-                            ? db->group_lists : nullptr;
+        a.group_lists = db->grid <= 8 * 63 ? db->group_lists : nullptr;
         a.tickets = db->tickets;
         cudaError_t err = dbq::launch_scan_packed(a, db->grid, s);
         if (err != cudaSuccess) return cuda_fail(err, "scan_packed launch");

@@ -62,9 +62,7 @@ struct ScanPackedArgs {
 int scan_packed_grid(int device);
 size_t scan_packed_smem(int chunk4);
 void scan_packed_chunking(int wp4, int* chunk4, int* nchunks);
-// Whether the last CTA merges `lists` published lists of k candidates in one
-// step (they fit its shared-memory slots together).
-bool topk_one_level_merge(int lists, int k);
+
 cudaError_t launch_scan_packed(const ScanPackedArgs& a, int grid, cudaStream_t stream);
 
 // Arguments of the fused half-precision scan (per-query thresholds).

@@ -106,8 +106,7 @@ rerank_kernel(const RerankArgs a)
             const int64_t e = list[i];
             const uint32_t I1 = icnt[2 * i], I2 = icnt[2 * i + 1];
             const uint2 E = ecount2[e];
-            topk_offer(tk, a.k, score_key(score_rn(I1, I2, E.x, E.y, P1, P2)), e,
-                       (uint64_t)I1 | ((uint64_t)I2 << 32), (uint64_t)E.x | ((uint64_t)E.y << 32));
+            topk_offer_counts(tk, a.k, I1, I2, E.x, E.y, P1, P2, e);
         }
         topk_flush(tk, a.k);
         Cand* rows = a.scratch + (int64_t)q * a.slices * a.k;

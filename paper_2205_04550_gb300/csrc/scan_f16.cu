@@ -173,9 +173,7 @@ scan_f16_kernel(const ScanF16Args a)
             if (a.counts_out)
                 reinterpret_cast<uint4*>(a.counts_out)[e] = make_uint4(I1, I2, E1, E2);
             if (want_topk)
-                topk_offer(tk, k, score_key(score_rn(I1, I2, E1, E2, P1, P2)), e,
-                           (uint64_t)I1 | ((uint64_t)I2 << 32),
-                           (uint64_t)E1 | ((uint64_t)E2 << 32));
+                topk_offer_counts(tk, k, I1, I2, E1, E2, P1, P2, e);
         }
         if (want_topk) topk_flush(tk, k);
         else __syncthreads();

@@ -81,9 +81,7 @@ scan_packed_kernel(const ScanPackedArgs a)
             if (a.counts_out)
                 reinterpret_cast<uint4*>(a.counts_out)[e] = make_uint4(I1, I2, E.x, E.y);
             if (want_topk)
-                topk_offer(tk, k, score_key(score_rn(I1, I2, E.x, E.y, P1, P2)), e,
-                           (uint64_t)I1 | ((uint64_t)I2 << 32),
-                           (uint64_t)E.x | ((uint64_t)E.y << 32));
+                topk_offer_counts(tk, k, I1, I2, E.x, E.y, P1, P2, e);
         }
         if (want_topk) topk_flush(tk, k);
         else __syncthreads();
@@ -125,11 +123,6 @@ void scan_packed_chunking(int wp4, int* chunk4, int* nchunks)
     if (c4 < 1) c4 = 1;
     *chunk4 = c4;
     *nchunks = (wp4 + c4 - 1) / c4;
-}
-
-bool topk_one_level_merge(int lists, int k)
-{
-    return (int64_t)lists * k + k + kThreads / 32 <= kTopkCap;
 }
 
 int scan_packed_grid(int device)

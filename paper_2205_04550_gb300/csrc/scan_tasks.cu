@@ -97,9 +97,7 @@ scan_tasks_kernel(const QueryTask* __restrict__ tasks, const int2* __restrict__ 
                 const int64_t e = g0 + i;
                 const uint32_t I1 = icnt[2 * i], I2 = icnt[2 * i + 1];
                 const uint2 E = ecount2[e];
-                topk_offer(tk, t.k, score_key(score_rn(I1, I2, E.x, E.y, P1, P2)), e,
-                           (uint64_t)I1 | ((uint64_t)I2 << 32),
-                           (uint64_t)E.x | ((uint64_t)E.y << 32));
+                topk_offer_counts(tk, t.k, I1, I2, E.x, E.y, P1, P2, e);
             }
             topk_flush(tk, t.k);
         }

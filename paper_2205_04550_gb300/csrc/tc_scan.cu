@@ -496,9 +496,7 @@ tc_select_kernel(const QueryTask* __restrict__ tasks, int task0, int nq,
         if (e < n) {
             const uint32_t I1 = row1[e], I2 = row2[e];
             const uint2 E = ecount2[e];
-            topk_offer(tk, k, score_key(score_rn(I1, I2, E.x, E.y, P1, P2)), e,
-                       (uint64_t)I1 | ((uint64_t)I2 << 32),
-                       (uint64_t)E.x | ((uint64_t)E.y << 32));
+            topk_offer_counts(tk, k, I1, I2, E.x, E.y, P1, P2, e);
         }
         __syncthreads();
         // room for another round of offers

@@ -77,6 +77,37 @@ __device__ __forceinline__ void topk_offer(TopK& t, int k, uint64_t key, int64_t
     }
 }
 
+// Binary32 Dice: 2 I / (P + E) with both operands and the quotient rounded
+// to nearest, each within a relative 2^-24 of exact; both empty -> 1.
+__device__ __forceinline__ float dice_f32(uint32_t inter, uint32_t a, uint32_t b)
+{
+    const uint32_t den = a + b;
+    if (den == 0u) return 1.0f;
+    return __fdiv_rn((float)(2u * inter), (float)den);
+}
+
+// Offer an entry by its counts.  The binary64 score (the ranking key) costs
+// two binary64 divisions, which are slow on this GPU; most entries of a scan
+// cannot reach the current k-th best, and a binary32 bound shows it first:
+// each binary32 Dice is within a relative 3 x 2^-24 of the exact quotient and
+// their sum within one more 2^-24, so the score times (1 + 2^-20) is an upper
+// bound of the exact score and of its binary64 rounding.  An entry whose bound
+// is below the k-th best score is strictly worse than it (no tie is possible)
+// and is skipped; every other entry is scored exactly and offered as before,
+// so the result is the same.
+__device__ __forceinline__ void topk_offer_counts(TopK& t, int k, uint32_t i1, uint32_t i2,
+                                                  uint32_t e1, uint32_t e2, uint32_t p1,
+                                                  uint32_t p2, int64_t index)
+{
+    const uint64_t kth = t.key[k - 1];
+    if (kth != kSentinelKey) {
+        const float up = (dice_f32(i1, p1, e1) + dice_f32(i2, p2, e2)) * (0.5f + 0x1p-21f);
+        if ((double)up < key_score(kth)) return;
+    }
+    topk_offer(t, k, score_key(score_rn(i1, i2, e1, e2, p1, p2)), index,
+               (uint64_t)i1 | ((uint64_t)i2 << 32), (uint64_t)e1 | ((uint64_t)e2 << 32));
+}
+
 __device__ __forceinline__ void bitonic_sort_topk(TopK& t, int n)
 {
     for (int size = 2; size <= n; size <<= 1) {
@@ -99,20 +130,24 @@ __device__ __forceinline__ void bitonic_sort_topk(TopK& t, int n)
 }
 
 // Merge the appended candidates into slots [0, k).  Starts and ends with a
-// barrier.  When the k slots and the appended candidates fit in one element
-// per thread, every element's new position is counted directly -- its rank
-// among the sorted k (a binary search, or its own slot) plus the appended
-// candidates better than it -- and written in one step: three barriers in all,
-// where a bitonic sort of the same elements takes one per stage (15 for 32
-// elements, 45 for 512), and a barrier of a 1024-thread block is the
-// expensive part here.  Larger rounds use the bitonic sort.
+// barrier.  A round of at most kRankFlush appended candidates (the common
+// case once the k best are established, and in small scans) is merged by
+// counting every element's new position directly -- its rank among the
+// sorted k (a binary search, or its own slot) plus the appended candidates
+// better than it -- and writing it there: three barriers, where a bitonic
+// sort of the same elements takes one per stage (15 for 32 elements), and the
+// barriers of a 1024-thread block are the expensive part.  Larger rounds use
+// the bitonic sort, whose cost does not grow with the round as fast as the
+// direct count does.
+constexpr int kRankFlush = 64;
+
 __device__ __forceinline__ void topk_flush(TopK& t, int k)
 {
     __syncthreads();
     const int added = t.misc[0];
     if (added > 0) {
         const int n = k + added;
-        if (n <= (int)blockDim.x) {
+        if (added <= kRankFlush && n <= (int)blockDim.x) {
             const int i = threadIdx.x;
             uint64_t ki = 0, p0 = 0, p1 = 0;
             int64_t ii = kSentinelIndex;
@@ -135,8 +170,14 @@ __device__ __forceinline__ void topk_flush(TopK& t, int k)
                         }
                         r = lo;
                     }
-                    for (int j = k; j < n && r < k; ++j)      // appended candidates better than it
-                        if (j != i && better(t.key[j], t.idx[j], ki, ii)) ++r;
+                    // appended candidates better than it (itself is not)
+                    int j = k;
+                    for (; j + 8 <= n; j += 8) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u)
+                            r += better(t.key[j + u], t.idx[j + u], ki, ii) ? 1 : 0;
+                    }
+                    for (; j < n; ++j) r += better(t.key[j], t.idx[j], ki, ii) ? 1 : 0;
                     rank = r;
                 }
             }
@@ -197,114 +238,68 @@ __device__ __forceinline__ bool topk_publish(TopK& t, int k, Cand* cand, unsigne
 }
 
 // Merge of m / k published lists, each sorted best first (every list comes
-// from a flushed or merged TopK), when they fit in the shared slots with
-// room for k more and one entry per warp.  The k-th element of every list
-// bounds the answer: the list with the best k-th element alone holds k
-// candidates at least that good, so no candidate worse than T (the best of
-// the k-th elements) can be among the k best.  The few candidates at least
-// as good as T are ranked exactly -- a candidate's final position is the
-// number of candidates better than it, summed over the lists by binary
-// searches that the 32 lanes of a warp share -- and written at that
-// position.  The order is strict (entry indices are unique), so positions
-// never collide; sentinels are never better than a real candidate and are not
-// placed.  Five barriers, whatever the number of lists.
+// from a flushed or merged TopK), when they fit in half of the shared slots:
+// every candidate's final position is its position in its own list plus the
+// number of candidates of each other list that are better (a binary search
+// per list), and the first k positions are written to the upper half of the
+// slots, then moved down to [0, k).  The order is strict (entry indices are
+// unique), so positions never collide; sentinels are never better than a
+// real candidate and are not placed.
 __device__ __forceinline__ bool topk_merge_sorted(TopK& t, int k, const Cand* cand, int64_t m)
 {
-    const int nwarps = (int)(blockDim.x >> 5);
-    if (m % k != 0 || m + k + nwarps > kTopkCap) return false;
-    const int mm = (int)m;
-    const int lists = mm / k;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kHalf = kTopkCap / 2;
+    if (m % k != 0 || m > kHalf || k > kHalf) return false;
+    const int lists = (int)(m / k);
     for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) {
-        if (i < mm) {
+        if (i < (int)m) {
             const Cand* src = cand + i;
             t.key[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->key));
             t.idx[i] = __ldcg(reinterpret_cast<const long long*>(&src->index));
             t.pay0[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay0));
             t.pay1[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay1));
+        } else if (i >= kHalf) {
+            topk_clear_slot(t, i);
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < (int)m; i += blockDim.x) {
+        const uint64_t ck = t.key[i];
+        const int64_t ci = t.idx[i];
+        if (ci == kSentinelIndex) continue;
+        const int own = i / k;
+        int r = i - own * k;
+        for (int l = 0; l < lists && r < k; ++l) {
+            if (l == own) continue;
+            // the candidates of list l better than this one form a prefix
+            int lo = 0, hi = k;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const int j = l * k + mid;
+                if (better(t.key[j], t.idx[j], ck, ci)) lo = mid + 1;
+                else hi = mid;
+            }
+            r += lo;
+        }
+        if (r < k) {
+            t.key[kHalf + r] = ck;
+            t.idx[kHalf + r] = ci;
+            t.pay0[kHalf + r] = t.pay0[i];
+            t.pay1[kHalf + r] = t.pay1[i];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < kHalf; i += blockDim.x) {
+        if (i < k) {
+            t.key[i] = t.key[kHalf + i];
+            t.idx[i] = t.idx[kHalf + i];
+            t.pay0[i] = t.pay0[kHalf + i];
+            t.pay1[i] = t.pay1[kHalf + i];
         } else {
             topk_clear_slot(t, i);
         }
     }
     __syncthreads();
-    // T: the best k-th element over the lists (block reduction)
-    uint64_t tk = kSentinelKey;
-    int64_t ti = kSentinelIndex;
-    for (int l = threadIdx.x; l < lists; l += blockDim.x) {
-        const int j = l * k + k - 1;
-        if (better(t.key[j], t.idx[j], tk, ti)) {
-            tk = t.key[j];
-            ti = t.idx[j];
-        }
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const uint64_t ok = __shfl_down_sync(0xffffffffu, tk, off);
-        const int64_t oi = __shfl_down_sync(0xffffffffu, ti, off);
-        if (better(ok, oi, tk, ti)) {
-            tk = ok;
-            ti = oi;
-        }
-    }
-    if (lane == 0) {
-        t.key[mm + k + warp] = tk;
-        t.idx[mm + k + warp] = ti;
-    }
-    __syncthreads();
-    tk = kSentinelKey;
-    ti = kSentinelIndex;
-    for (int w = 0; w < nwarps; ++w)
-        if (better(t.key[mm + k + w], t.idx[mm + k + w], tk, ti)) {
-            tk = t.key[mm + k + w];
-            ti = t.idx[mm + k + w];
-        }
-    // every candidate not worse than T: its exact rank, by one warp
-    for (int base = warp * 32; base < mm; base += (int)blockDim.x) {
-        const int i = base + lane;
-        uint64_t ck = 0;
-        int64_t ci = kSentinelIndex;
-        if (i < mm) {
-            ck = t.key[i];
-            ci = t.idx[i];
-        }
-        const bool keep = ci != kSentinelIndex && !better(tk, ti, ck, ci);
-        unsigned int todo = __ballot_sync(0xffffffffu, keep);
-        while (todo) {
-            const int src = __ffs(todo) - 1;
-            todo &= todo - 1;
-            const uint64_t xk = __shfl_sync(0xffffffffu, ck, src);
-            const int64_t xi = __shfl_sync(0xffffffffu, ci, src);
-            int r = 0;
-            for (int l = lane; l < lists; l += 32) {    // candidates of list l better than x
-                int lo = 0, hi = k;
-                while (lo < hi) {
-                    const int mid = (lo + hi) >> 1;
-                    const int j = l * k + mid;
-                    if (better(t.key[j], t.idx[j], xk, xi)) lo = mid + 1;
-                    else hi = mid;
-                }
-                r += lo;
-            }
-            r = __reduce_add_sync(0xffffffffu, r);
-            if (lane == src && r < k) {
-                t.key[mm + r] = ck;
-                t.idx[mm + r] = ci;
-                t.pay0[mm + r] = t.pay0[i];
-                t.pay1[mm + r] = t.pay1[i];
-            }
-        }
-    }
-    __syncthreads();
-    // move [m, m + k) to [0, k) (m >= k: the ranges do not overlap), then
-    // clear everything after the k slots
-    for (int i = threadIdx.x; i < k; i += blockDim.x) {
-        t.key[i] = t.key[mm + i];
-        t.idx[i] = t.idx[mm + i];
-        t.pay0[i] = t.pay0[mm + i];
-        t.pay1[i] = t.pay1[mm + i];
-    }
-    __syncthreads();
-    for (int i = k + threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
+    for (int i = kHalf + threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
     if (threadIdx.x == 0) t.misc[0] = 0;
     __syncthreads();
     return true;
