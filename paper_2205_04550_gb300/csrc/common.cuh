@@ -9,6 +9,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "dice.cuh"
+
 namespace dbq {
 
 // Ranking keys are unsigned 64-bit integers whose order is the ranking order:
@@ -71,12 +73,11 @@ __device__ __forceinline__ uint32_t popc_and4(const uint4& a, const uint4& b)
     return __popc(a.x & b.x) + __popc(a.y & b.y) + __popc(a.z & b.z) + __popc(a.w & b.w);
 }
 
-// Dice from exact counts, IEEE binary64 round-to-nearest; both empty -> 1.
+// Dice from exact counts, IEEE binary64 round-to-nearest; both empty -> 1
+// (integer arithmetic, see dice.cuh).
 __device__ __forceinline__ double dice_rn(uint32_t inter, uint32_t a, uint32_t b)
 {
-    const uint32_t den = a + b;
-    if (den == 0u) return 1.0;
-    return __ddiv_rn((double)(2u * inter), (double)den);
+    return bits_to_double(dice_bits(inter, a, b));
 }
 
 __device__ __forceinline__ double score_rn(uint32_t i1, uint32_t i2, uint32_t e1, uint32_t e2,
