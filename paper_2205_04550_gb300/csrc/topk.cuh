@@ -268,28 +268,17 @@ __device__ __forceinline__ bool topk_merge_sorted(TopK& t, int k, const Cand* ca
         if (ci == kSentinelIndex) continue;
         const int own = i / k;
         int r = i - own * k;
-        // the candidates of list l better than this one form a prefix; its
-        // length is found by halving power-of-two steps, for eight lists at a
-        // time in lock step, so that the eight loads of a step are independent
-        // (one search at a time waits out a shared-memory latency per step)
-        int top = 1;
-        while (top * 2 <= k) top *= 2;
-        for (int l0 = 0; l0 < lists && r < k; l0 += 8) {
-            int lo[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) lo[u] = 0;
-            for (int step = top; step > 0; step >>= 1) {
-#pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int l = l0 + u;
-                    const int j = lo[u] + step - 1;
-                    if (l < lists && l != own && j < k &&
-                        better(t.key[l * k + j], t.idx[l * k + j], ck, ci))
-                        lo[u] += step;
-                }
+        for (int l = 0; l < lists && r < k; ++l) {
+            if (l == own) continue;
+            // the candidates of list l better than this one form a prefix
+            int lo = 0, hi = k;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                const int j = l * k + mid;
+                if (better(t.key[j], t.idx[j], ck, ci)) lo = mid + 1;
+                else hi = mid;
             }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) r += lo[u];
+            r += lo;
         }
         if (r < k) {
             t.key[kHalf + r] = ck;
