@@ -120,12 +120,12 @@ DEFAULT_WORKLOAD = "exact_packed_50k_128"
 TRAFFIC = {
     "scan_packed_kernel": dict(files=("scan_packed.cu", "scan_core.cuh", "topk.cuh",
                                       "common.cuh"),
-                               sha="28b320973988c1aa", entries=2000, grid=(128, 128, 128),
-                               read_bytes=1049206272, write_bytes=3647488,
+                               sha="0d26828a1ac97946", entries=2000, grid=(128, 128, 128),
+                               read_bytes=1049235968, write_bytes=3343360,
                                capture="profiles/scan_packed_2k_128_ncu_full.md"),
     "scan_f16_kernel": dict(files=("scan_f16.cu", "topk.cuh", "common.cuh"),
-                            sha="bea418ed01a7b08d", entries=4000, grid=(64, 64, 64),
-                            read_bytes=2097377536, write_bytes=3295744,
+                            sha="3259e1100a767964", entries=4000, grid=(64, 64, 64),
+                            read_bytes=2097310976, write_bytes=3080704,
                             capture="profiles/scan_f16_4k_64_ncu_full.md"),
 }
 METRIC = "DB entries/s per query (HBM GB/s vs peak); batched queries/s at top-1 match"
