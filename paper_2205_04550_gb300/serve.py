@@ -226,11 +226,11 @@ class Server:
                 self._lane_free.wait(timeout=0.05)
 
     def _schedule(self):
+        # A lane is claimed before the batch is gathered: while every lane is
+        # busy, arriving requests wait in the queue and all of them (up to
+        # max_batch) form the next batch, so batches grow with the load and
+        # each scan of a database serves as many queries as are waiting.
         while not self._stop:
-            batch = self._take_batch()
-            if batch is None:
-                return
-            batch, used = self._admit(batch)
             with self._lock:
                 while True:
                     lane = next((l for l in self._lanes if not l.busy), None)
@@ -238,6 +238,13 @@ class Server:
                         lane.busy = True
                         break
                     self._lane_free.wait(timeout=0.05)
+            batch = self._take_batch()
+            if batch is None:
+                with self._lock:
+                    lane.busy = False
+                    self._lane_free.notify_all()
+                return
+            batch, used = self._admit(batch)
             threading.Thread(target=self._run, args=(lane, batch, used), daemon=True).start()
 
     def _run(self, lane: _Lane, batch, used: int):
