@@ -887,9 +887,12 @@ def run_serve(args, wl, torch):
         reqs.append((host[d][rng.integers(0, len(host[d]))], d))
     arrivals = serve.poisson_arrivals(wl["rate"], count, seed=7)
     out, sweeps = {}, {}
+    tc_min = None
     for mode in ("exact", "embed_bf16"):
         srv = serve.Server(dbs, mode=mode, k=wl["k"], n_candidates=wl["candidates"],
                            max_batch=wl["max_batch"], lanes=2)
+        if mode == "exact":
+            tc_min = {f"{wl['mix'][d]['shape'][0]}^3": v for d, v in srv.tc_min.items()}
         try:
             serve.run_open_loop(srv, reqs[:200], serve.poisson_arrivals(wl["rate"], 200, 1))
             srv.reset_stats()
@@ -910,7 +913,7 @@ def run_serve(args, wl, torch):
                               "p99_ms": st["p99_ms"]})
                 if st["queries_per_s"] < 0.95 * rate or st["p99_ms"] > wl.get("slo_p99_ms", 100.0):
                     break
-                rate *= 2
+                rate *= 1.5
             ok = [r for r in sweep if r["queries_per_s"] >= 0.95 * r["offered_per_s"]
                   and r["p99_ms"] <= wl.get("slo_p99_ms", 100.0)]
             sweeps[mode] = {"slo_p99_ms": wl.get("slo_p99_ms", 100.0), "points": sweep,
@@ -925,10 +928,11 @@ def run_serve(args, wl, torch):
             "config": {"workload": args.workload, "desc": wl["desc"], "requests": count,
                        "rate_per_s": wl["rate"], "max_batch": wl["max_batch"]},
             "exact": out["exact"], "embed_bf16": out["embed_bf16"],
-            "capacity_sweep": sweeps,
+            "capacity_sweep": sweeps, "tc_min_queries": tc_min,
             "note": "offered load 200 queries/s: queries/s is bounded by the arrival rate; "
-                    "latency is the measure there; capacity_sweep doubles the offered "
-                    "load until completions fall below 95 % of it or p99 exceeds the SLO"}
+                    "latency is the measure there; capacity_sweep raises the offered "
+                    "load by 1.5x until completions fall below 95 % of it or p99 exceeds "
+                    "the SLO"}
     for d in dbs:
         d.close()
     if rank == 0:

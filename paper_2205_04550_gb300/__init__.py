@@ -79,6 +79,7 @@ class Database:
                  sketch: bool = False):
         nx, ny, nz = shape
         self.shape = (int(nx), int(ny), int(nz))
+        self.sparse = False
         self.capacity = int(capacity)
         self.storage = storage
         self.t1, self.t2 = float(np.float32(t1)), float(np.float32(t2))
@@ -133,6 +134,7 @@ class Database:
     def set_sparse(self, on: bool = True):
         """Exact scans read only the patient's support (identical results)."""
         db_set_option(self.handle, DBQ_OPT_SPARSE, 1 if on else 0)
+        self.sparse = bool(on)
 
     def embeddings(self, first: int, count: int):
         """-> dict of bf16 bits [count,2,d] uint16, e4m3 codes [count,2,d] uint8,

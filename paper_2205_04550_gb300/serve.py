@@ -88,11 +88,15 @@ class Server:
     budget      device bytes the server may hold for requests in flight
                 (patient slots and hit buffers); None = 90 % of the free
                 memory at start.
+    tune        exact mode: time, once per database (cached by ``tune``),
+                the batch size from which a batch's queries of that database
+                are scanned together on the tensor cores, and use it on every
+                lane; otherwise the plans' default threshold applies.
     """
 
     def __init__(self, databases, mode: str = "exact", k: int = 10, n_candidates: int = 512,
                  max_batch: int = 128, lanes: int = 2, budget: int | None = None,
-                 max_wait_s: float = 0.002):
+                 max_wait_s: float = 0.002, tune: bool = True):
         import torch
         self.torch = torch
         self.databases = list(databases)
@@ -109,6 +113,9 @@ class Server:
         self.budget = int(0.9 * free) if budget is None else int(budget)
         self.reserved = 0
         self._lanes = [_Lane(torch, self.databases, max_batch, k, max_vox) for _ in range(lanes)]
+        self.tc_min = {}
+        if tune and self.mode == DBQ_MODE_EXACT:
+            self._tune_crossovers()
         self._pending: "queue.Queue[_Request]" = queue.Queue()
         self._lock = threading.Lock()
         self._lane_free = threading.Condition(self._lock)
@@ -186,6 +193,24 @@ class Server:
             lane.close()
 
     # ------------------------------------------------------------ internals
+    def _tune_crossovers(self):
+        """Per database, the tuned tensor-core crossover (zero patients: the
+        cost of either dense path does not depend on the patient; a sparse
+        database's loop is timed on them as well), set on every lane's plan."""
+        from . import tune as _tune
+        torch = self.torch
+        plan = self._lanes[0].plan
+        if plan.max_queries < max(_tune.TC_BATCHES):
+            return
+        for d, db in enumerate(self.databases):
+            pats = [torch.zeros(self.voxels[d], dtype=torch.float32, device="cuda")]
+            res = _tune.tune_crossover(plan, d, pats, self._lanes[0].hits,
+                                       sparse=getattr(db, "sparse", False))
+            self.tc_min[d] = int(res["tc_min"])
+            for lane in self._lanes:
+                lane.plan.set_tc_min_queries(self.tc_min[d], db=d)
+        torch.cuda.synchronize()
+
     def _take_batch(self):
         """Block for the first request, then gather more for up to
         max_wait_s while the batch and the memory budget have room."""
