@@ -23,9 +23,6 @@
 // that word, one per nibble ((u >> j) & 0x11111111, shifted to the 1.0 code
 // 0x2).  That is two integer instructions per 8 voxels.
 //
-// Up to 64 queries run with M = 64 (half the query operand read per MMA, a
-// fourth operand stage), more with M = 128.
-//
 //   * work units are (224-entry tile, segmentation), round-robin over one
 //     persistent CTA per SM; each unit writes its own component of the
 //     counts, so no unit waits for another;
@@ -68,48 +65,40 @@
 namespace dbq {
 namespace {
 
+constexpr int kTcQ = 128;                    // query rows of the MMA (M), zero-padded
 constexpr int kTcE = 224;                    // entries per tile (MMA N)
 constexpr int kTcMaxN = 128;                 // queries per launch
-constexpr int kTcSlots = 2;                  // bit slots
+constexpr int kTcStages = 3;                 // operand stages, 44 KiB each
+constexpr int kTcSlots = 2;                  // bit slots, 44 KiB each
+constexpr int kTcConv = 352;                 // converter threads: 224 entry + 128 query rows
+constexpr int kTcConvWarps = kTcConv / 32;
 constexpr int kTcConv0 = 192;                // first converter thread (warps 0-5: MMA, TMA, epilogue)
+constexpr int kTcThreads = kTcConv0 + kTcConv;
 constexpr int kTcSliceWords = 8;             // 256 voxels per K-slice and row
 constexpr int kTcChunkWords = 32;            // 1024 voxels (128 bytes) per row and bit slot
+constexpr int kTcABytes = kTcQ * 128;        // query operand of a stage (and query bits of a slot)
 constexpr int kTcBBytes = kTcE * 128;        // entry operand of a stage (and entry bits of a slot)
+constexpr int kTcStageBytes = kTcABytes + kTcBBytes;
+constexpr int kTcSlotBytes = kTcBBytes + kTcABytes;   // entry bits first, then query bits
 constexpr uint32_t kTcBufCols = 256;         // TMEM columns between the two accumulators
 constexpr uint32_t kTcScaleA = 240;          // TMEM columns of the unit scales
 constexpr uint32_t kTcScaleB = 496;
 constexpr uint32_t kUnitScales = 0x7F7F7F7Fu;   // four UE8M0 bytes of 2^0
 
-// The two shapes of the contraction: M = 128 query rows, or M = 64 for up
-// to 64 queries, which halves the query operand that the tensor core reads
-// from shared memory for every MMA and leaves room for a fourth stage.  An
-// M = 64 accumulator keeps its rows in the first 16 lanes of each 32-lane
-// TMEM quarter.
-template <int M>
-struct TcShape {
-    static constexpr int kQ = M;                                   // MMA M (rows past nq zero)
-    static constexpr int kStages = M == 64 ? 4 : 3;                // operand stages
-    static constexpr int kConv = (kTcE + M + 31) / 32 * 32;        // converter threads
-    static constexpr int kConvWarps = kConv / 32;
-    static constexpr int kThreads = kTcConv0 + kConv;
-    static constexpr int kABytes = M * 128;                        // query operand / bits
-    static constexpr int kStageBytes = kABytes + kTcBBytes;
-    static constexpr int kSlotBytes = kTcBBytes + kABytes;         // entry bits, then query bits
-    static constexpr int kRowsPerQuarter = M / 4;                  // accumulator rows per TMEM quarter
-    // 1 KiB of alignment slack, the stages, the bit slots, the mbarriers
-    // (full and empty per stage and per slot, two accumulator pairs, the
-    // drain, the test stall), TMEM slot and abort flag.
-    static constexpr int kBars = 2 * kStages + 2 * kTcSlots + 6;
-    static constexpr size_t kSmem = 1024 + (size_t)kStages * kStageBytes +
-                                    (size_t)kTcSlots * kSlotBytes + kBars * 8 + 16;
-    static_assert(M == 64 || M == 128, "MMA M");
-    static_assert(kABytes % 1024 == 0 && kTcBBytes % 1024 == 0, "swizzle atoms");
-    static_assert(kSmem <= 232448, "shared memory per block");
-};
-
-static_assert(kTcE % 16 == 0 && kTcE <= 256, "MMA N");
+static_assert(kTcE % 16 == 0 && kTcE <= 256 && kTcConv >= kTcE + kTcQ, "MMA N, converters");
 static_assert(kTcScaleA >= kTcE && kTcScaleA + 16 <= kTcBufCols, "scale columns");
 static_assert(kTcScaleB >= kTcBufCols + kTcE && kTcScaleB + 16 <= 512, "scale columns");
+static_assert(kTcABytes % 1024 == 0 && kTcBBytes % 1024 == 0, "swizzle atoms");
+
+// 1 KiB of alignment slack, the stages, the bit slots, the mbarriers (full
+// and empty per stage and per slot, two accumulator pairs, the drain, the
+// test stall), TMEM slot and abort flag.
+constexpr int kTcBars = 2 * kTcStages + 2 * kTcSlots + 6;
+size_t smem_bytes()
+{
+    return 1024 + (size_t)kTcStages * kTcStageBytes + (size_t)kTcSlots * kTcSlotBytes +
+           kTcBars * 8 + 16;
+}
 
 __device__ __forceinline__ uint4 ld_shared_v4(uint32_t addr)
 {
@@ -196,19 +185,10 @@ __device__ __forceinline__ uint32_t row_offset(int row)
     return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128);
 }
 
-template <int M>
-__global__ void __launch_bounds__(TcShape<M>::kThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
 tc_scan_kernel(const __grid_constant__ CUtensorMap tm_db, const __grid_constant__ CUtensorMap tm_q,
                const TcScanArgs a)
 {
-    using S = TcShape<M>;
-    constexpr int kTcQ = S::kQ;
-    constexpr int kTcStages = S::kStages;
-    constexpr int kTcConvWarps = S::kConvWarps;
-    constexpr int kTcABytes = S::kABytes;
-    constexpr int kTcStageBytes = S::kStageBytes;
-    constexpr int kTcSlotBytes = S::kSlotBytes;
-    constexpr int kTcBars = S::kBars;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -386,10 +366,9 @@ tc_scan_kernel(const __grid_constant__ CUtensorMap tm_db, const __grid_constant_
                     a.status[0] = 7;
         }
     } else if (warp >= 2 && warp < 6) {
-        // lane = query row (the first M / 4 lanes of the quarter); columns =
-        // the unit's 224 entries
+        // lane = query row; columns = the unit's 224 entries
         const int quarter = warp & 3;
-        const int q = lane < S::kRowsPerQuarter ? quarter * S::kRowsPerQuarter + lane : kTcMaxN;
+        const int q = quarter * 32 + lane;
         for (int64_t u = 0; u < my_units; ++u) {
             const int buf = (int)(u & 1);
             if (!mbar_wait(acc_full0 + 8 * buf, (uint32_t)((u >> 1) & 1), abort_flag)) {
@@ -560,18 +539,6 @@ static bool make_bits_map(CUtensorMap* m, const void* base, int64_t wp, int64_t 
                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int M>
-static cudaError_t launch_shape(const CUtensorMap& tm_db, const CUtensorMap& tm_q,
-                                const TcScanArgs& a, int grid, cudaStream_t stream)
-{
-    using S = TcShape<M>;
-    cudaError_t err = cudaFuncSetAttribute(tc_scan_kernel<M>,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S::kSmem);
-    if (err != cudaSuccess) return err;
-    tc_scan_kernel<M><<<grid, S::kThreads, S::kSmem, stream>>>(tm_db, tm_q, a);
-    return cudaGetLastError();
-}
-
 cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream)
 {
     if (a.nq < 1 || a.nq > kTcMaxN || a.n < 1 || a.n > INT32_MAX || a.wp < kTcChunkWords ||
@@ -583,11 +550,15 @@ cudaError_t launch_tc_scan(const TcScanArgs& a, int grid, cudaStream_t stream)
     if (!make_bits_map(&tm_db, a.planes, a.wp, a.n, kTcE) ||
         !make_bits_map(&tm_q, a.qplanes, a.wp, a.nq, a.nq))
         return cudaErrorInvalidValue;
+    const size_t smem = smem_bytes();
+    cudaError_t err = cudaFuncSetAttribute(tc_scan_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+    if (err != cudaSuccess) return err;
     const int64_t nunits = (a.n + kTcE - 1) / kTcE * 2;
     if (grid > nunits) grid = (int)nunits;
     if (grid < 1) grid = 1;
-    return a.nq <= 64 ? launch_shape<64>(tm_db, tm_q, a, grid, stream)
-                      : launch_shape<128>(tm_db, tm_q, a, grid, stream);
+    tc_scan_kernel<<<grid, kTcThreads, smem, stream>>>(tm_db, tm_q, a);
+    return cudaGetLastError();
 }
 
 int64_t tc_scan_min_words() { return kTcChunkWords; }
