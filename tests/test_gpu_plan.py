@@ -389,3 +389,20 @@ def test_plan_per_database_threshold_errors(torch, two_dbs):
         with pytest.raises(DbqError):
             plan.set_tc_min_queries(-2, db=0)
         plan.set_tc_min_queries(-1, db=0)             # back to the plan-wide value
+
+
+@pytest.mark.parametrize("nq", [1, 63, 64, 65, 128])
+def test_plan_tensor_core_query_counts(torch, two_dbs, nq):
+    """One query to a full pass of 128 on the contraction (M = 128 rows, the
+    rows past the last query zero): hits bit-identical to the CUDA-core loop
+    and equal to the oracle."""
+    (d1, v1), _ = two_dbs
+    rng = np.random.default_rng(400 + nq)
+    pats = _patients(rng, v1, nq)
+    which = [0] * nq
+    k = 6
+    tc = _run_plan(torch, [d1], which, pats, k, tc_min=1)
+    cc = _run_plan(torch, [d1], which, pats, k, tc_min=0)
+    assert tc.tobytes() == cc.tobytes()
+    for q in sorted({0, nq // 2, nq - 1}):
+        assert_hits_equal(tc[q], oracle.query(v1, pats[q], T1, T2, k), k)
