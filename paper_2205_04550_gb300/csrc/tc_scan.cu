@@ -5,11 +5,11 @@
 // are dot products of 0/1 vectors over the V voxels: one dense contraction
 // [Q x V] . [V x N] per segmentation.  The masks are stored as bits, which
 // the tensor cores cannot read, so converter warps expand each K-slice of 256
-// voxels of the patients' rows and of 240 entry rows into 4-bit E2M1 values
+// voxels of the patients' rows and of 224 entry rows into 4-bit E2M1 values
 // (1.0 for a set bit, 0 otherwise; two voxels per byte) in the
 // 128-byte-swizzled K-major layout of tcgen05 shared-memory operands, and one
 // thread issues block-scaled tcgen05.mma (kind::mxf4, every UE8M0 scale 1.0;
-// M = 128 patient rows -- the rows past Q are zero --, N = 240 entries,
+// M = 128 patient rows -- the rows past Q are zero --, N = 224 entries,
 // K = 64 per instruction) with binary32 accumulators in tensor memory.  An
 // MMA instruction costs about the same for any N, so the entries, not the
 // few patients, take the N side.  Every product is 0 or 1 and every partial
@@ -33,7 +33,7 @@
 //     rows past the database's end and words past the plane's end arrive as
 //     zeros.  Each row segment is one 128-byte request, which the memory
 //     system serves far better than the 16- or 32-byte pieces that
-//     per-thread loads of 240 scattered rows make;
+//     per-thread loads of the tile's scattered rows make;
 //   * warps 6-16 (converters): thread t < 224 expands entry row t of the
 //     tile, thread 224 + r patient row r < Q; per K-slice each reads its
 //     row's 32 bytes of bits from the bit slot, expands them into a 3-stage
@@ -50,10 +50,11 @@
 //     once, then tcgen05.ld the counts of 16 entries at a time and store them
 //     as 64-byte rows of counts[plane][q][e].
 // Shared memory: three operand stages of 44 KiB and two bit slots of
-// 44 KiB.  Per 256-voxel slice the expanded operands pass through shared
-// memory twice (converter stores, tensor-core reads); with the loads on the
-// TMA the remaining limit is the round trip of a stage between the
-// converters and the MMA thread, which three stages do not fully hide.  The
+// 44 KiB.  Per 256-voxel slice about 114 KB pass through the shared-memory
+// banks at 128 queries (TMA fills of the bits, the converters' reads of
+// them, the expanded operand stores, the tensor core's operand reads), and
+// the banks are busy about 92 % of the time: that traffic is the kernel's
+// bound, not the tensor rate (the tensor pipe is busy about 46 %).  The
 // mask sizes, binary64 scores and each patient's top-k follow in
 // tc_select_kernel.  Every mbarrier wait is bounded; on a timeout the CTA
 // records an error code in `status`, stops, lets its copies and MMAs finish
