@@ -245,11 +245,92 @@ __device__ __forceinline__ bool topk_publish(TopK& t, int k, Cand* cand, unsigne
 // slots, then moved down to [0, k).  The order is strict (entry indices are
 // unique), so positions never collide; sentinels are never better than a
 // real candidate and are not placed.
+// Up to 32 sorted lists of at most kTournamentK candidates are merged by one
+// warp: lane l holds the current head of list l, and each round a butterfly
+// of shuffles finds the best head in every lane, whose lane writes it out and
+// advances.  k rounds of a few dozen instructions, where ranking every
+// candidate by binary searches in every other list reads shared memory at
+// scattered addresses (bank conflicts) and, at these sizes, takes several
+// times longer.
+constexpr int kTournamentK = 16;
+
+__device__ __forceinline__ void topk_tournament(TopK& t, int k, int lists, int out0)
+{
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
+    int pos = 0;
+    uint64_t hk = kSentinelKey;
+    int64_t hi = kSentinelIndex;
+    if (lane < lists) {
+        hk = t.key[lane * k];
+        hi = t.idx[lane * k];
+    }
+    for (int r = 0; r < k; ++r) {
+        uint64_t bk = hk;
+        int64_t bi = hi;
+        int bl = lane;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const uint64_t ok = __shfl_xor_sync(0xffffffffu, bk, off);
+            const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
+            const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
+            if (better(ok, oi, bk, bi)) {
+                bk = ok;
+                bi = oi;
+                bl = ol;
+            }
+        }
+        if (bi == kSentinelIndex) break;               // every list exhausted
+        if (lane == bl) {
+            const int j = lane * k + pos;
+            t.key[out0 + r] = hk;
+            t.idx[out0 + r] = hi;
+            t.pay0[out0 + r] = t.pay0[j];
+            t.pay1[out0 + r] = t.pay1[j];
+            ++pos;
+            if (pos < k) {
+                hk = t.key[j + 1];
+                hi = t.idx[j + 1];
+            } else {
+                hk = kSentinelKey;
+                hi = kSentinelIndex;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ bool topk_merge_sorted(TopK& t, int k, const Cand* cand, int64_t m)
 {
     constexpr int kHalf = kTopkCap / 2;
     if (m % k != 0 || m > kHalf || k > kHalf) return false;
     const int lists = (int)(m / k);
+    if (k <= kTournamentK && lists <= 32) {
+        for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) {
+            if (i < (int)m) {
+                const Cand* src = cand + i;
+                t.key[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->key));
+                t.idx[i] = __ldcg(reinterpret_cast<const long long*>(&src->index));
+                t.pay0[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay0));
+                t.pay1[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay1));
+            } else {
+                topk_clear_slot(t, i);
+            }
+        }
+        __syncthreads();
+        topk_tournament(t, k, lists, kHalf);
+        __syncthreads();
+        for (int i = threadIdx.x; i < k; i += blockDim.x) {   // [kHalf, kHalf + k) -> [0, k)
+            t.key[i] = t.key[kHalf + i];
+            t.idx[i] = t.idx[kHalf + i];
+            t.pay0[i] = t.pay0[kHalf + i];
+            t.pay1[i] = t.pay1[kHalf + i];
+        }
+        __syncthreads();
+        for (int i = k + threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
+        if (threadIdx.x == 0) t.misc[0] = 0;
+        __syncthreads();
+        return true;
+    }
     for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) {
         if (i < (int)m) {
             const Cand* src = cand + i;
