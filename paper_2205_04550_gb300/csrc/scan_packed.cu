@@ -32,6 +32,7 @@ namespace {
 
 constexpr int kThreads = kScanThreads;
 constexpr int kGroup = 1024;        // entries whose counters live in shared memory
+static_assert(kGroup == kThreads, "one entry of a group per thread when scoring");
 constexpr int kMaxChunk4 = 2048;    // uint4 per plane per chunk = 2 per thread
 
 template <int U, int EPI, bool kSparse>
@@ -66,6 +67,14 @@ scan_packed_kernel(const ScanPackedArgs a)
         const int gn = (int)((e_end - g0) < kGroup ? (e_end - g0) : kGroup);
         for (int i = tid; i < 2 * kGroup; i += kThreads) icnt[i] = 0u;
         if (tid == 0) *next = 0;
+        // The entries' mask sizes are fetched before the count, so the
+        // scoring after it does not wait on memory for them (kGroup ==
+        // kThreads: one entry per thread): into registers in the dense scan,
+        // into L2 in the sparse one, whose counts have no register to spare.
+        const bool mine = want_topk && tid < gn;
+        uint2 E = make_uint2(0u, 0u);
+        if (!kSparse && mine) E = ecount2[g0 + tid];
+        if (kSparse && mine) asm volatile("prefetch.global.L2 [%0];" ::"l"(ecount2 + g0 + tid));
         __syncthreads();
         if (warp_mode)
             count_group_warps(a.planes, a.wp4, nullptr, g0, gn, icnt, cache, next);
@@ -77,11 +86,11 @@ scan_packed_kernel(const ScanPackedArgs a)
             const int64_t e = g0 + i;
             const uint32_t I1 = icnt[2 * i];
             const uint32_t I2 = icnt[2 * i + 1];
-            const uint2 E = ecount2[e];
+            const uint2 Ec = kSparse || !want_topk ? ecount2[e] : E;
             if (a.counts_out)
-                reinterpret_cast<uint4*>(a.counts_out)[e] = make_uint4(I1, I2, E.x, E.y);
+                reinterpret_cast<uint4*>(a.counts_out)[e] = make_uint4(I1, I2, Ec.x, Ec.y);
             if (want_topk)
-                topk_offer_counts(tk, k, I1, I2, E.x, E.y, P1, P2, e);
+                topk_offer_counts(tk, k, I1, I2, Ec.x, Ec.y, P1, P2, e);
         }
         if (want_topk) topk_flush(tk, k);
         else __syncthreads();

@@ -129,6 +129,214 @@ __device__ __forceinline__ void bitonic_sort_topk(TopK& t, int n)
     }
 }
 
+// Merge trees for k <= kTreeK.  A sorted list is merged with its neighbour
+// by ranks: an element's position in the merged list is its position in its
+// own list plus the number of elements of the other list before it, found by
+// one binary search.  Ties (only sentinels compare equal) go to the left
+// list, so the positions of a pair are a permutation of [0, LA + LB) and every
+// output slot is written exactly once: no clearing between levels, one
+// barrier per level, and log2(lists) levels of one search each, where ranking
+// against every other list at once costs lists - 1 searches per element (and
+// a bitonic sort one barrier per stage).  Appended candidates are first
+// sorted in runs of 32 by the warps, in registers (shuffles, no barriers).
+constexpr int kTreeK = 64;
+
+// Sort slots [base, base + 32) best first in one warp; lanes at or past `len`
+// count as sentinels and are written as sentinels.
+__device__ __forceinline__ void warp_sort_run(TopK& t, int base, int len)
+{
+    const int lane = threadIdx.x & 31;
+    uint64_t key = kSentinelKey;
+    int64_t idx = kSentinelIndex;
+    int src = lane;
+    if (lane < len) {
+        key = t.key[base + lane];
+        idx = t.idx[base + lane];
+    }
+#pragma unroll
+    for (int size = 2; size <= 32; size <<= 1) {
+#pragma unroll
+        for (int stride = size >> 1; stride > 0; stride >>= 1) {
+            const uint64_t ok = __shfl_xor_sync(0xffffffffu, key, stride);
+            const int64_t oi = __shfl_xor_sync(0xffffffffu, idx, stride);
+            const int os = __shfl_xor_sync(0xffffffffu, src, stride);
+            const bool best_first = (lane & size) == 0;    // direction of this block
+            const bool lower = (lane & stride) == 0;
+            const bool take = (lower == best_first) ? better(ok, oi, key, idx)
+                                                    : better(key, idx, ok, oi);
+            if (take) {
+                key = ok;
+                idx = oi;
+                src = os;
+            }
+        }
+    }
+    uint64_t p0 = 0, p1 = 0;
+    if (src < len) {
+        p0 = t.pay0[base + src];
+        p1 = t.pay1[base + src];
+    }
+    __syncwarp();
+    t.key[base + lane] = key;
+    t.idx[base + lane] = idx;
+    t.pay0[base + lane] = p0;
+    t.pay1[base + lane] = p1;
+}
+
+// Number of the first n slots from `base` better than (key, idx), or, with
+// `or_equal`, better than or equal to it (a prefix of a sorted list).
+__device__ __forceinline__ int count_before(const TopK& t, int base, int n, uint64_t key,
+                                            int64_t idx, bool or_equal)
+{
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        const uint64_t mk = t.key[base + mid];
+        const int64_t mi = t.idx[base + mid];
+        const bool before = or_equal ? !better(key, idx, mk, mi) : better(mk, mi, key, idx);
+        if (before) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Element q of the merge of list A (la slots at a) and list B (lb slots at
+// b; with `b_empty`, lb sentinels that are not stored) goes to dst + its
+// position, if that is below lout.  Reads only A and B; dst is disjoint.
+__device__ __forceinline__ void merge_element(TopK& t, int a, int la, int b, int lb, bool b_empty,
+                                              int q, int dst, int lout)
+{
+    const bool in_b = q >= la;
+    const int pos = in_b ? q - la : q;
+    int from = -1;
+    uint64_t key = kSentinelKey;
+    int64_t idx = kSentinelIndex;
+    if (!in_b) from = a + pos;
+    else if (!b_empty) from = b + pos;
+    if (from >= 0) {
+        key = t.key[from];
+        idx = t.idx[from];
+    }
+    int r = pos;
+    if (!in_b) {
+        if (!b_empty) r += count_before(t, b, lb, key, idx, false);
+    } else {
+        r += b_empty ? la : count_before(t, a, la, key, idx, true);
+    }
+    if (r < lout) {
+        t.key[dst + r] = key;
+        t.idx[dst + r] = idx;
+        t.pay0[dst + r] = from >= 0 ? t.pay0[from] : 0;
+        t.pay1[dst + r] = from >= 0 ? t.pay1[from] : 0;
+    }
+}
+
+// One level: lists i < nl of l slots at src + i * l are merged in pairs
+// (2p, 2p + 1), the first lout slots of pair p going to dst + p * lout; a
+// last unpaired list is merged with an empty one (copied and padded).
+// Ends with a barrier.
+__device__ __forceinline__ void merge_level(TopK& t, int src, int l, int nl, int dst, int lout)
+{
+    const int npairs = (nl + 1) >> 1;
+    const int total = npairs * 2 * l;
+    for (int e = threadIdx.x; e < total; e += blockDim.x) {
+        const int p = e / (2 * l);
+        const int q = e - p * 2 * l;
+        merge_element(t, src + 2 * p * l, l, src + (2 * p + 1) * l, l, 2 * p + 1 >= nl, q,
+                      dst + p * lout, lout);
+    }
+    __syncthreads();
+}
+
+// Slots taken by the levels of a tree over nl lists of l slots, alternating
+// between regions `a` (holding the lists) and `b`: the furthest slot written
+// in each, and the region and length of the result.
+struct TreeSpan {
+    int end_a, end_b, res, len;
+};
+
+__device__ __forceinline__ TreeSpan tree_span(int a, int b, int l, int nl, int k)
+{
+    TreeSpan s{a + l * nl, b, a, l};
+    int src = a, dst = b;
+    while (nl > 1) {
+        const int lout = min(k, 2 * l);
+        nl = (nl + 1) >> 1;
+        const int end = dst + nl * lout;
+        if (dst == b) s.end_b = max(s.end_b, end);
+        else s.end_a = max(s.end_a, end);
+        l = lout;
+        const int tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+    s.res = src;
+    s.len = l;
+    return s;
+}
+
+__device__ __forceinline__ void merge_tree(TopK& t, int a, int b, int l, int nl, int k)
+{
+    int src = a, dst = b;
+    while (nl > 1) {
+        const int lout = min(k, 2 * l);
+        merge_level(t, src, l, nl, dst, lout);
+        nl = (nl + 1) >> 1;
+        l = lout;
+        const int tmp = src;
+        src = dst;
+        dst = tmp;
+    }
+}
+
+// The merge-tree flush and the merge of published lists are not inlined:
+// they run once per round or per scan, and inlined they raised the register
+// pressure of the scan loops around them to the point of spilling.  They
+// take the TopK by value, so its pointers stay in registers.
+//
+// Flush by a merge tree: the appended candidates are sorted in runs of 32,
+// the runs merged pairwise, alternating between their own slots and the
+// slots after them, and the result merged with [0, k).  Returns false, having done
+// nothing, when the levels do not fit the slots.  Slots past k are left
+// holding sentinels.
+static __device__ __noinline__ bool topk_flush_tree(TopK t, int k, int added)
+{
+    const int runs = (added + 31) >> 5;
+    const int b = k + 32 * runs;                         // scratch region after the runs
+    const TreeSpan sp = tree_span(k, b, 32, runs, k);
+    const int fin = sp.res == k ? b : k;                 // the region not holding the runs' result
+    const int end_a = max(sp.end_a, fin == k ? 2 * k : 0);
+    const int end_b = max(sp.end_b, fin == b ? b + k : 0);
+    if (end_a > b || end_b > kTopkCap) return false;
+    const int warp = (int)(threadIdx.x >> 5);
+    const int warps = (int)(blockDim.x >> 5);
+    for (int r = warp; r < runs; r += warps) warp_sort_run(t, k + 32 * r, min(32, added - 32 * r));
+    __syncthreads();
+    merge_tree(t, k, b, 32, runs, k);
+    for (int q = threadIdx.x; q < k + sp.len; q += blockDim.x)
+        merge_element(t, 0, k, sp.res, sp.len, false, q, fin, k);
+    __syncthreads();
+    uint64_t ck = 0, cp0 = 0, cp1 = 0;
+    int64_t ci = 0;
+    const bool mover = (int)threadIdx.x < k;
+    if (mover) {
+        ck = t.key[fin + threadIdx.x];
+        ci = t.idx[fin + threadIdx.x];
+        cp0 = t.pay0[fin + threadIdx.x];
+        cp1 = t.pay1[fin + threadIdx.x];
+    }
+    __syncthreads();
+    if (mover) {
+        t.key[threadIdx.x] = ck;
+        t.idx[threadIdx.x] = ci;
+        t.pay0[threadIdx.x] = cp0;
+        t.pay1[threadIdx.x] = cp1;
+    }
+    for (int i = k + threadIdx.x; i < end_a; i += blockDim.x) topk_clear_slot(t, i);
+    for (int i = b + threadIdx.x; i < end_b; i += blockDim.x) topk_clear_slot(t, i);
+    return true;
+}
+
 // Merge the appended candidates into slots [0, k).  Starts and ends with a
 // barrier.  A round of at most kRankFlush appended candidates (the common
 // case once the k best are established, and in small scans) is merged by
@@ -137,8 +345,8 @@ __device__ __forceinline__ void bitonic_sort_topk(TopK& t, int n)
 // better than it -- and writing it there: three barriers, where a bitonic
 // sort of the same elements takes one per stage (15 for 32 elements), and the
 // barriers of a 1024-thread block are the expensive part.  Larger rounds use
-// the bitonic sort, whose cost does not grow with the round as fast as the
-// direct count does.
+// the merge tree above when k <= kTreeK, else the bitonic sort, whose cost
+// does not grow with the round as fast as the direct count does.
 constexpr int kRankFlush = 64;
 
 __device__ __forceinline__ void topk_flush(TopK& t, int k)
@@ -194,6 +402,7 @@ __device__ __forceinline__ void topk_flush(TopK& t, int k)
                 }
                 if (i >= k) topk_clear_slot(t, i);
             }
+        } else if (k <= kTreeK && topk_flush_tree(t, k, added)) {
         } else {
             const int n2 = next_pow2(n);
             bitonic_sort_topk(t, n2);
@@ -237,52 +446,98 @@ __device__ __forceinline__ bool topk_publish(TopK& t, int k, Cand* cand, unsigne
     return topk_publish_slot(t, k, cand, blockIdx.x, gridDim.x, ticket);
 }
 
-// Merge of m / k published lists, each sorted best first (every list comes
-// from a flushed or merged TopK), when they fit in half of the shared slots:
-// every candidate's final position is its position in its own list plus the
-// number of candidates of each other list that are better (a binary search
-// per list), and the first k positions are written to the upper half of the
-// slots, then moved down to [0, k).  The order is strict (entry indices are
-// unique), so positions never collide; sentinels are never better than a
-// real candidate and are not placed.
-// Up to 32 sorted lists of at most kTournamentK candidates are merged by one
-// warp: lane l holds the current head of list l, and each round a butterfly
-// of shuffles finds the best head in every lane, whose lane writes it out and
-// advances.  k rounds of a few dozen instructions, where ranking every
-// candidate by binary searches in every other list reads shared memory at
-// scattered addresses (bank conflicts) and, at these sizes, takes several
-// times longer.
+// ---- merging published lists (in the last CTA to publish)
+//
+// Every published list is sorted best first (it comes from a flushed or
+// merged TopK).  After a merge the slots past k are unspecified; every user
+// re-initialises (topk_init) before offering again.
+
+// Slots [0, m) := the m published candidates; each thread issues all of its
+// loads (two 16-byte loads per candidate) before its stores.
+__device__ __forceinline__ void topk_load_cands(TopK& t, const Cand* cand, int m)
+{
+    const int stride = (int)blockDim.x;
+    for (int i0 = threadIdx.x; i0 < m; i0 += 2 * stride) {
+        const int i1 = i0 + stride;
+        const ulonglong2* s0 = reinterpret_cast<const ulonglong2*>(cand + i0);
+        const ulonglong2 a0 = __ldcg(s0), b0 = __ldcg(s0 + 1);
+        ulonglong2 a1 = make_ulonglong2(0, 0), b1 = make_ulonglong2(0, 0);
+        if (i1 < m) {
+            const ulonglong2* s1 = reinterpret_cast<const ulonglong2*>(cand + i1);
+            a1 = __ldcg(s1);
+            b1 = __ldcg(s1 + 1);
+        }
+        t.key[i0] = a0.x;
+        t.idx[i0] = (int64_t)a0.y;
+        t.pay0[i0] = b0.x;
+        t.pay1[i0] = b0.y;
+        if (i1 < m) {
+            t.key[i1] = a1.x;
+            t.idx[i1] = (int64_t)a1.y;
+            t.pay0[i1] = b1.x;
+            t.pay1[i1] = b1.y;
+        }
+    }
+}
+
+// Lists of at most kTournamentK candidates are merged by warp tournaments:
+// lane l of a warp holds the current head of list l; each round the warp
+// finds the best head with a max-reduction of the keys' upper words and a
+// ballot (ties, rare, fall through to the lower word and then the index),
+// and the winning lane writes its head out and advances.  k rounds of a few
+// dependent steps, where ranking every candidate by binary searches in every
+// other list reads shared memory at scattered addresses and takes several
+// times longer.  Up to 32 x 32 lists: warp w merges lists [32 w, 32 w + 32)
+// and warp 0 then merges the warps' results.  (One warp holding several
+// lists per lane, rescanning its heads after each win, measured slower.)
 constexpr int kTournamentK = 16;
 
-__device__ __forceinline__ void topk_tournament(TopK& t, int k, int lists, int out0)
+// Best (key descending, index ascending) over the warp; returns its lane in
+// every lane.  Every lane must call it (warp-uniform branches only).
+__device__ __forceinline__ int warp_best_lane(uint64_t key, int64_t idx)
 {
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
+    const unsigned full = 0xffffffffu;
+    const uint32_t kh = (uint32_t)(key >> 32);
+    const uint32_t mh = __reduce_max_sync(full, kh);
+    unsigned c = __ballot_sync(full, kh == mh);
+    if (__popc(c) > 1) {
+        const bool in = kh == mh;
+        const uint32_t kl = in ? (uint32_t)key : 0u;
+        const uint32_t ml = __reduce_max_sync(full, kl);
+        c = __ballot_sync(full, in && kl == ml);
+        if (__popc(c) > 1) {                 // equal keys: the smallest index
+            const bool in2 = in && kl == ml;
+            const uint64_t u = (uint64_t)idx;
+            const uint32_t ih = in2 ? (uint32_t)(u >> 32) : 0xffffffffu;
+            const uint32_t mih = __reduce_min_sync(full, ih);
+            c = __ballot_sync(full, in2 && ih == mih);
+            if (__popc(c) > 1) {
+                const bool in3 = in2 && ih == mih;
+                const uint32_t il = in3 ? (uint32_t)u : 0xffffffffu;
+                const uint32_t mil = __reduce_min_sync(full, il);
+                c = __ballot_sync(full, in3 && il == mil);
+            }
+        }
+    }
+    return __ffs(c) - 1;
+}
+
+// One warp merges `lists` (<= 32) sorted lists of k slots at base + l * k
+// into slots [out0, out0 + k), which must hold sentinels beforehand.
+__device__ __forceinline__ void topk_tournament(TopK& t, int k, int lists, int base, int out0)
+{
+    const int lane = threadIdx.x & 31;
     int pos = 0;
     uint64_t hk = kSentinelKey;
     int64_t hi = kSentinelIndex;
     if (lane < lists) {
-        hk = t.key[lane * k];
-        hi = t.idx[lane * k];
+        hk = t.key[base + lane * k];
+        hi = t.idx[base + lane * k];
     }
     for (int r = 0; r < k; ++r) {
-        uint64_t bk = hk;
-        int64_t bi = hi;
-        int bl = lane;
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const uint64_t ok = __shfl_xor_sync(0xffffffffu, bk, off);
-            const int64_t oi = __shfl_xor_sync(0xffffffffu, bi, off);
-            const int ol = __shfl_xor_sync(0xffffffffu, bl, off);
-            if (better(ok, oi, bk, bi)) {
-                bk = ok;
-                bi = oi;
-                bl = ol;
-            }
-        }
-        if (bi == kSentinelIndex) break;               // every list exhausted
-        if (lane == bl) {
-            const int j = lane * k + pos;
+        if (__ballot_sync(0xffffffffu, hi != kSentinelIndex) == 0u) break;   // all exhausted
+        if (lane == warp_best_lane(hk, hi)) {
+            const int j = base + lane * k + pos;
             t.key[out0 + r] = hk;
             t.idx[out0 + r] = hi;
             t.pay0[out0 + r] = t.pay0[j];
@@ -299,38 +554,83 @@ __device__ __forceinline__ void topk_tournament(TopK& t, int k, int lists, int o
     }
 }
 
-__device__ __forceinline__ bool topk_merge_sorted(TopK& t, int k, const Cand* cand, int64_t m)
+// Whether `lists` sorted lists of k slots fit the tournament merge.
+__device__ __forceinline__ bool topk_tournament_fits(int k, int64_t lists)
+{
+    const int64_t w1 = (lists + 31) >> 5;
+    return k <= kTournamentK && w1 <= 32 && w1 <= (int64_t)(blockDim.x >> 5) &&
+           lists * k + (w1 > 1 ? w1 * k : 0) + k <= kTopkCap;
+}
+
+// Merge of m / k published lists into slots [0, k), when they fit the
+// shared slots (else returns false, having done nothing): by the tournament
+// for k <= kTournamentK, by the merge tree for k <= kTreeK, else by ranks --
+// every candidate's final position is its position in its own list plus the
+// number of candidates of each other list that are better (a binary search
+// per list), the first k positions written to the upper half of the slots,
+// then moved down (the order is strict, so positions never collide;
+// sentinels are not placed).
+static __device__ __noinline__ bool topk_merge_sorted(TopK t, int k, const Cand* cand, int64_t m)
 {
     constexpr int kHalf = kTopkCap / 2;
-    if (m % k != 0 || m > kHalf || k > kHalf) return false;
+    if (m % k != 0 || m > kTopkCap || k > kHalf) return false;
     const int lists = (int)(m / k);
-    if (k <= kTournamentK && lists <= 32) {
-        for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) {
-            if (i < (int)m) {
-                const Cand* src = cand + i;
-                t.key[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->key));
-                t.idx[i] = __ldcg(reinterpret_cast<const long long*>(&src->index));
-                t.pay0[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay0));
-                t.pay1[i] = __ldcg(reinterpret_cast<const unsigned long long*>(&src->pay1));
-            } else {
-                topk_clear_slot(t, i);
+    if (topk_tournament_fits(k, lists)) {
+        const int w1 = (lists + 31) >> 5;                   // first-round warps
+        const int out1 = (int)m;                            // their lists
+        const int out2 = out1 + (w1 > 1 ? w1 * k : 0);      // the final list
+        topk_load_cands(t, cand, (int)m);
+        for (int i = out1 + threadIdx.x; i < out2 + k; i += blockDim.x) topk_clear_slot(t, i);
+        __syncthreads();
+        const int warp = (int)(threadIdx.x >> 5);
+        if (w1 > 1) {
+            if (warp < w1)
+                topk_tournament(t, k, min(32, lists - 32 * warp), 32 * warp * k, out1 + warp * k);
+            __syncthreads();
+        }
+        if (warp == 0) {
+            topk_tournament(t, k, w1 > 1 ? w1 : lists, w1 > 1 ? out1 : 0, out2);
+            __syncwarp();
+            const int lane = threadIdx.x;
+            if (lane < k) {                                 // [out2, out2 + k) -> [0, k), disjoint
+                t.key[lane] = t.key[out2 + lane];
+                t.idx[lane] = t.idx[out2 + lane];
+                t.pay0[lane] = t.pay0[out2 + lane];
+                t.pay1[lane] = t.pay1[out2 + lane];
             }
         }
-        __syncthreads();
-        topk_tournament(t, k, lists, kHalf);
-        __syncthreads();
-        for (int i = threadIdx.x; i < k; i += blockDim.x) {   // [kHalf, kHalf + k) -> [0, k)
-            t.key[i] = t.key[kHalf + i];
-            t.idx[i] = t.idx[kHalf + i];
-            t.pay0[i] = t.pay0[kHalf + i];
-            t.pay1[i] = t.pay1[kHalf + i];
-        }
-        __syncthreads();
-        for (int i = k + threadIdx.x; i < kTopkCap; i += blockDim.x) topk_clear_slot(t, i);
         if (threadIdx.x == 0) t.misc[0] = 0;
         __syncthreads();
         return true;
     }
+    if (k <= kTreeK && m <= kHalf) {
+        topk_load_cands(t, cand, (int)m);
+        __syncthreads();
+        const TreeSpan sp = tree_span(0, kHalf, k, lists, k);
+        merge_tree(t, 0, kHalf, k, lists, k);
+        if (sp.res != 0) {                                  // [kHalf, kHalf + k) -> [0, k)
+            uint64_t ck = 0, cp0 = 0, cp1 = 0;
+            int64_t ci = 0;
+            const bool mover = (int)threadIdx.x < k;
+            if (mover) {
+                ck = t.key[kHalf + threadIdx.x];
+                ci = t.idx[kHalf + threadIdx.x];
+                cp0 = t.pay0[kHalf + threadIdx.x];
+                cp1 = t.pay1[kHalf + threadIdx.x];
+            }
+            __syncthreads();
+            if (mover) {
+                t.key[threadIdx.x] = ck;
+                t.idx[threadIdx.x] = ci;
+                t.pay0[threadIdx.x] = cp0;
+                t.pay1[threadIdx.x] = cp1;
+            }
+        }
+        if (threadIdx.x == 0) t.misc[0] = 0;
+        __syncthreads();
+        return true;
+    }
+    if (m > kHalf) return false;
     for (int i = threadIdx.x; i < kTopkCap; i += blockDim.x) {
         if (i < (int)m) {
             const Cand* src = cand + i;
@@ -423,10 +723,18 @@ constexpr int kMergeGroup = 16;  // CTAs per first-level merge group
 // still be scanning), and the last group merger merges the group lists.
 // tickets[0] is the top-level counter, tickets[1 + g] group g's (all zero
 // between launches).  Returns true, in every thread, in the CTA that then
-// holds the final list in slots [0, k).
+// holds the final list in slots [0, k).  When the whole grid's lists fit one
+// tournament merge, the groups are skipped: every CTA publishes on
+// tickets[0] and the last one merges all lists (one publication and one
+// merge fewer on the critical path).
 __device__ __forceinline__ bool topk_publish_two_level(TopK& t, int k, Cand* cand,
                                                        Cand* group_lists, unsigned int* tickets)
 {
+    if (topk_tournament_fits(k, gridDim.x)) {
+        if (!topk_publish_slot(t, k, cand, blockIdx.x, gridDim.x, tickets)) return false;
+        topk_merge_published(t, k, cand, (int64_t)gridDim.x * k);
+        return true;
+    }
     const int group = blockIdx.x / kMergeGroup;
     const int first = group * kMergeGroup;
     const int members = min(kMergeGroup, (int)gridDim.x - first);
