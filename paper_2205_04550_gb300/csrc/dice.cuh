@@ -2,16 +2,19 @@
 // IEEE binary64 value, 2 I / (P + E) rounded to nearest-even, computed with
 // integer arithmetic.
 //
-// On this GPU a binary64 division costs about 640 cycles of latency and the
-// binary64 pipe is narrow, so scoring every entry of a scan with __ddiv_rn
-// showed up in the scans' tails.  For integer operands the correctly rounded
-// quotient follows from two 64-bit integer divisions: the numerator is first
-// shifted to the denominator's bit length (quotient in [1/2, 1)), the next 64
-// quotient bits are taken as floor(num * 2^64 / den) in two 32-bit steps, and
-// the top 53 of them are rounded to nearest-even with the 54th bit as the
-// round bit and everything below it, remainder included, as the sticky bit.
-// The header compiles for the host as well, where the tests compare it with
-// the host's IEEE division.
+// On this GPU a binary64 division costs about 640 cycles of latency and a
+// 64-bit integer division about 450, so scoring with either showed up in the
+// scans' tails.  For integer operands the correctly rounded quotient follows
+// from long division: the numerator is first shifted to the denominator's
+// bit length (quotient in [1/2, 1)), the next 54 quotient bits are found as
+// three digits of 18 bits, and the top 53 are rounded to nearest-even with
+// the 54th as the round bit and a non-zero remainder as the sticky bit.  Each
+// digit is estimated from a binary32 reciprocal of the denominator -- the
+// estimate is within 1/16 of the exact quotient of the partial remainder,
+// which is below 2^18, since every binary32 operation adds at most 2^-24
+// relative error -- and corrected by at most one from the exact 64-bit
+// remainder, so the digits are exact.  The same code compiles for the host,
+// where the tests compare it with the host's IEEE division.
 #pragma once
 
 #include <cstdint>
@@ -34,6 +37,24 @@ DBQ_HD int clz32(uint32_t x)
 #endif
 }
 
+DBQ_HD float recip_f32(uint32_t den)
+{
+#if defined(__CUDA_ARCH__)
+    return __frcp_rn(__uint2float_rn(den));
+#else
+    return 1.0f / (float)den;
+#endif
+}
+
+DBQ_HD uint32_t digit_estimate(uint32_t x, float r18)
+{
+#if defined(__CUDA_ARCH__)
+    return __float2uint_rz(__fmul_rn(__uint2float_rn(x), r18));
+#else
+    return (uint32_t)((float)x * r18);
+#endif
+}
+
 // Bits of the binary64 nearest to num / den (ties to even), 0 < num < den.
 DBQ_HD uint64_t quotient_bits(uint32_t num, uint32_t den)
 {
@@ -43,16 +64,28 @@ DBQ_HD uint64_t quotient_bits(uint32_t num, uint32_t den)
         --sh;
         a >>= 1;
     }
-    const uint64_t a1 = (uint64_t)a << 32;
-    const uint64_t q1 = a1 / den;              // in [2^31, 2^32)
-    const uint64_t r1 = a1 - q1 * den;
-    const uint64_t a2 = r1 << 32;
-    const uint64_t q2 = a2 / den;              // below 2^32
-    const uint64_t r2 = a2 - q2 * den;
-    const uint64_t q = (q1 << 32) | q2;        // floor(a * 2^64 / den), in [2^63, 2^64)
-    uint64_t m = q >> 11;                      // 53 bits, leading bit 52
-    const bool round = (q >> 10) & 1u;
-    const bool sticky = (q & 0x3FFu) != 0 || r2 != 0;
+    // q = floor(a * 2^54 / den), in [2^53, 2^54), three digits of 18 bits;
+    // x is the partial remainder, below den
+    const float r18 = recip_f32(den) * 262144.0f;        // 2^18 / den, scaled exactly
+    uint64_t q = 0;
+    uint32_t x = a;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        int64_t digit = (int64_t)digit_estimate(x, r18);
+        int64_t rem = ((int64_t)x << 18) - digit * (int64_t)den;
+        if (rem < 0) {
+            --digit;
+            rem += den;
+        } else if (rem >= (int64_t)den) {
+            ++digit;
+            rem -= den;
+        }
+        q = (q << 18) | (uint64_t)digit;
+        x = (uint32_t)rem;
+    }
+    uint64_t m = q >> 1;                       // 53 bits, leading bit 52
+    const bool round = q & 1u;
+    const bool sticky = x != 0u;
     int e = -1 - sh;                           // num / den = m * 2^(e - 52), m in [2^52, 2^53)
     if (round && (sticky || (m & 1u))) ++m;
     if (m >> 53) {                             // rounded up to the next power of two

@@ -65,11 +65,24 @@ __device__ __forceinline__ void topk_init(TopK& t)
     __syncthreads();
 }
 
+// The offering lanes of a warp that are converged here take their slots with
+// one shared-memory atomic (a ballot and a prefix count), not one each: in a
+// round where most candidates pass (the first group of a scan) hundreds of
+// same-address atomics otherwise serialise.
 __device__ __forceinline__ void topk_offer(TopK& t, int k, uint64_t key, int64_t index,
                                            uint64_t p0, uint64_t p1)
 {
-    if (better(key, index, t.key[k - 1], t.idx[k - 1])) {
-        const int pos = k + atomicAdd(&t.misc[0], 1);
+    const bool pass = better(key, index, t.key[k - 1], t.idx[k - 1]);
+    const unsigned act = __activemask();
+    const unsigned want = __ballot_sync(act, pass);
+    if (want == 0u) return;
+    const int lane = (int)(threadIdx.x & 31);
+    const int leader = __ffs(want) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&t.misc[0], __popc(want));
+    base = __shfl_sync(act, base, leader);
+    if (pass) {
+        const int pos = k + base + __popc(want & ((1u << lane) - 1u));
         t.key[pos] = key;
         t.idx[pos] = index;
         t.pay0[pos] = p0;
@@ -100,12 +113,19 @@ __device__ __forceinline__ void topk_offer_counts(TopK& t, int k, uint32_t i1, u
                                                   uint32_t p2, int64_t index)
 {
     const uint64_t kth = t.key[k - 1];
+    bool maybe = true;
     if (kth != kSentinelKey) {
         const float up = (dice_f32(i1, p1, e1) + dice_f32(i2, p2, e2)) * (0.5f + 0x1p-21f);
-        if ((double)up < key_score(kth)) return;
+        maybe = !((double)up < key_score(kth));
     }
-    topk_offer(t, k, score_key(score_rn(i1, i2, e1, e2, p1, p2)), index,
-               (uint64_t)i1 | ((uint64_t)i2 << 32), (uint64_t)e1 | ((uint64_t)e2 << 32));
+    uint64_t key = kSentinelKey;                // a sentinel is never offered
+    int64_t idx = kSentinelIndex;
+    if (maybe) {
+        key = score_key(score_rn(i1, i2, e1, e2, p1, p2));
+        idx = index;
+    }
+    topk_offer(t, k, key, idx, (uint64_t)i1 | ((uint64_t)i2 << 32),
+               (uint64_t)e1 | ((uint64_t)e2 << 32));
 }
 
 __device__ __forceinline__ void bitonic_sort_topk(TopK& t, int n)
@@ -192,8 +212,11 @@ __device__ __forceinline__ int count_before(const TopK& t, int base, int n, uint
     while (lo < hi) {
         const int mid = (lo + hi) >> 1;
         const uint64_t mk = t.key[base + mid];
-        const int64_t mi = t.idx[base + mid];
-        const bool before = or_equal ? !better(key, idx, mk, mi) : better(mk, mi, key, idx);
+        bool before = mk > key;
+        if (mk == key) {                        // the index decides (read only then)
+            const int64_t mi = t.idx[base + mid];
+            before = or_equal ? mi <= idx : mi < idx;
+        }
         if (before) lo = mid + 1;
         else hi = mid;
     }

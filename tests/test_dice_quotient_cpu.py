@@ -1,6 +1,8 @@
-"""The library's integer computation of the binary64 Dice quotient
-(``csrc/dice.cuh``, used by every scan kernel) against the host's IEEE
-division, bit for bit.
+"""The library's computation of the binary64 Dice quotient
+(``csrc/dice.cuh``, used by every scan kernel: integer long division whose
+18-bit digits are estimated from a binary32 reciprocal and corrected by the
+exact remainder) against the host's IEEE division, bit for bit.  Removing
+either digit correction fails these cases.
 
 The header is compiled for the host with g++ into a small shared library;
 the expected values come from numpy's binary64 division, which is correctly
@@ -89,3 +91,20 @@ def test_dice_conventions(lib):
     assert lib.dice(0, 3, 4) == 0              # disjoint
     want = (np.float64(2 * 3) / np.float64(7 + 11)).view(np.uint64)
     assert lib.dice(3, 7, 11) == want
+
+
+def test_denominators_next_to_powers_of_two(lib):
+    rng = np.random.default_rng(11)
+    dens = []
+    for j in range(2, 33):
+        for off in (-3, -1, 1, 3):
+            d = 2 ** j + off
+            if 2 < d < 2 ** 32:
+                dens.append(d)
+    den = np.repeat(np.array(dens, dtype=np.uint64), 4000)
+    num = (rng.random(den.size) * (den - 1)).astype(np.uint64) + 1
+    num = np.minimum(num, den - 1)
+    _check(lib, num, den)
+    half = den // 2
+    _check(lib, np.maximum(half, 1), den)
+    _check(lib, np.minimum(half + 1, den - 1), den)
