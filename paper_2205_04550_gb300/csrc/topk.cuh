@@ -577,6 +577,30 @@ __device__ __forceinline__ void topk_tournament(TopK& t, int k, int lists, int b
     }
 }
 
+// Threads i < m rank candidate base + i by counting the candidates of
+// [base, base + m) better than it and write it to out0 + rank if the rank is
+// below k (ranks are distinct: the order is strict; sentinels are not
+// placed, so [out0, out0 + k) must hold sentinels beforehand).  Every thread
+// reads the same candidate at the same time (shared-memory broadcasts).
+constexpr int kRankMerge = 256;
+
+__device__ __forceinline__ void topk_rank_small(TopK& t, int k, int base, int m, int out0)
+{
+    const int i = threadIdx.x;
+    if (i >= m) return;
+    const uint64_t ck = t.key[base + i];
+    const int64_t ci = t.idx[base + i];
+    if (ci == kSentinelIndex) return;
+    int r = 0;
+    for (int j = 0; j < m; ++j) r += better(t.key[base + j], t.idx[base + j], ck, ci) ? 1 : 0;
+    if (r < k) {
+        t.key[out0 + r] = ck;
+        t.idx[out0 + r] = ci;
+        t.pay0[out0 + r] = t.pay0[base + i];
+        t.pay1[out0 + r] = t.pay1[base + i];
+    }
+}
+
 // Whether `lists` sorted lists of k slots fit the tournament merge.
 __device__ __forceinline__ bool topk_tournament_fits(int k, int64_t lists)
 {
@@ -611,16 +635,22 @@ static __device__ __noinline__ bool topk_merge_sorted(TopK t, int k, const Cand*
                 topk_tournament(t, k, min(32, lists - 32 * warp), 32 * warp * k, out1 + warp * k);
             __syncthreads();
         }
-        if (warp == 0) {
-            topk_tournament(t, k, w1 > 1 ? w1 : lists, w1 > 1 ? out1 : 0, out2);
-            __syncwarp();
-            const int lane = threadIdx.x;
-            if (lane < k) {                                 // [out2, out2 + k) -> [0, k), disjoint
-                t.key[lane] = t.key[out2 + lane];
-                t.idx[lane] = t.idx[out2 + lane];
-                t.pay0[lane] = t.pay0[out2 + lane];
-                t.pay1[lane] = t.pay1[out2 + lane];
-            }
+        // the last level: few candidates are ranked directly, in parallel
+        // (every thread counts the candidates better than its own: k rounds
+        // of a tournament cost more below kRankMerge candidates)
+        const int last_base = w1 > 1 ? out1 : 0;
+        const int last_m = w1 > 1 ? w1 * k : (int)m;
+        if (last_m <= kRankMerge && last_m <= (int)blockDim.x)
+            topk_rank_small(t, k, last_base, last_m, out2);
+        else if (warp == 0)
+            topk_tournament(t, k, w1 > 1 ? w1 : lists, last_base, out2);
+        __syncthreads();
+        if ((int)threadIdx.x < k) {                         // [out2, out2 + k) -> [0, k), disjoint
+            const int i = threadIdx.x;
+            t.key[i] = t.key[out2 + i];
+            t.idx[i] = t.idx[out2 + i];
+            t.pay0[i] = t.pay0[out2 + i];
+            t.pay1[i] = t.pay1[out2 + i];
         }
         if (threadIdx.x == 0) t.misc[0] = 0;
         __syncthreads();
