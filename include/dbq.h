@@ -86,7 +86,9 @@ enum dbq_storage {
 enum dbq_option {
     DBQ_OPT_SPARSE = 1   /* 1: exact scans of a bit-packed database read only the
                             words where the patient's mask is non-zero (exact
-                            counts, fewer bytes); 0 (default): read every word */
+                            counts, fewer bytes); 2: the same from a word-major
+                            copy of the planes (faster, twice the planes' memory);
+                            0 (default): read every word */
 };
 
 /* Query modes of db_query_batch. */
@@ -340,7 +342,14 @@ int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int 
  * 64-byte granules first and reads only those words of each entry.  Results
  * are identical; the bytes read per entry shrink to the patient's support.
  * Ignored by half-precision databases (their mask sizes are computed at
- * query time from every voxel).
+ * query time from every voxel).  Value 2 does the same for the
+ * single-patient scans (db_query, db_query_async, db_query_prepared,
+ * db_scan_counts) over a word-major copy of the planes ([2 wp][n] 16-byte
+ * words: each support word of every entry is one contiguous run), which
+ * the library allocates here (DBQ_ENOMEM if the device lacks room: N x 2 x
+ * words-per-plane x 4 bytes plus N x 8) and rebuilds at the first such scan
+ * after db_build_masks; the other paths treat 2 as 1.  DBQ_EINVAL for 2 on
+ * half-precision storage or for any value outside 0..2.
  */
 int db_set_option(dbq_db* db, int option, int64_t value);
 

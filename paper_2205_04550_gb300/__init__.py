@@ -131,10 +131,13 @@ class Database:
         obj.handle = db_create_downsampled(self.handle, factor)
         return obj
 
-    def set_sparse(self, on: bool = True):
-        """Exact scans read only the patient's support (identical results)."""
-        db_set_option(self.handle, DBQ_OPT_SPARSE, 1 if on else 0)
-        self.sparse = bool(on)
+    def set_sparse(self, on=True):
+        """Exact scans read only the patient's support (identical results):
+        True / 1, or 2 for single-patient scans over a word-major copy of the
+        planes (twice the planes' memory); False / 0 reads every word."""
+        mode = 2 if on == 2 else (1 if on else 0)
+        db_set_option(self.handle, DBQ_OPT_SPARSE, mode)
+        self.sparse = bool(mode)
 
     def embeddings(self, first: int, count: int):
         """-> dict of bf16 bits [count,2,d] uint16, e4m3 codes [count,2,d] uint8,

@@ -155,7 +155,11 @@ struct dbq_db {
     int ds_nx = 0, ds_ny = 0, ds_nz = 0;   // source grid: patients come at this size
     int64_t ds_v = 0, ds_words = 0, ds_wp = 0;
     uint32_t* ds_pplanes = nullptr;        // [2][ds_wp] source-resolution patient planes
-    bool sparse = false;            // DBQ_OPT_SPARSE
+    bool sparse = false;            // DBQ_OPT_SPARSE 1 or 2
+    int sparse_mode = 0;            // DBQ_OPT_SPARSE: 0, 1, 2 (word-major copy)
+    uint4* planes_t = nullptr;      // [2 wp4][n] word-major copy of planes (mode 2)
+    bool planes_t_valid = false;    // the copy matches planes
+    uint32_t* tcounts = nullptr;    // [n][2] counts of the word-major sparse scan
     uint32_t* plist = nullptr;      // [2][wp4] patient support lists
     uint32_t* plen = nullptr;       // [2]
     uint32_t* bsup = nullptr;       // [bq][2][wp4]
@@ -211,6 +215,8 @@ struct dbq_db {
         cudaFree(bstatus);
         cudaFree(plist);
         cudaFree(plen);
+        cudaFree(planes_t);
+        cudaFree(tcounts);
         cudaFree(ds_pplanes);
         cudaFree(bsup);
         cudaFree(bsuplen);
@@ -326,6 +332,21 @@ int check_query_args(dbq_db* db, int kind, float* t1, float* t2, int k)
 int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaStream_t s)
 {
     if (db->storage == DBQ_STORE_BITS) {
+        const bool word_major = db->sparse_mode == 2;
+        if (word_major) {           // counts over the word-major copy, ranked below
+            const int w4 = 2 * (int)db->wp4;
+            if (!db->planes_t_valid) {
+                cudaError_t err = dbq::launch_transpose_planes(
+                    reinterpret_cast<const uint4*>(db->planes), db->n, w4, db->planes_t, s);
+                if (err != cudaSuccess) return cuda_fail(err, "word-major copy launch");
+                db->planes_t_valid = true;
+            }
+            DBQ_CUDA(cudaMemsetAsync(db->tcounts, 0, (size_t)db->n * 2 * sizeof(uint32_t), s));
+            cudaError_t err = dbq::launch_sparse_t_count(
+                db->planes_t, db->n, reinterpret_cast<const uint4*>(db->pplanes), (int)db->wp4,
+                db->plist, db->plen, db->tcounts, db->grid, s);
+            if (err != cudaSuccess) return cuda_fail(err, "word-major sparse count launch");
+        }
         dbq::ScanPackedArgs a;
         a.planes = reinterpret_cast<const uint4*>(db->planes);
         a.ecount = db->ecount;
@@ -340,10 +361,11 @@ int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaSt
         a.ticket = db->ticket;
         a.hits = hits;
         a.counts_out = counts_out;
-        a.sup_list = db->sparse ? db->plist : nullptr;
-        a.sup_len = db->sparse ? db->plen : nullptr;
+        a.sup_list = db->sparse && !word_major ? db->plist : nullptr;
+        a.sup_len = db->sparse && !word_major ? db->plen : nullptr;
         a.group_lists = db->grid <= 8 * 63 ? db->group_lists : nullptr;
         a.tickets = db->tickets;
+        a.counts_in = word_major ? db->tcounts : nullptr;
         cudaError_t err = dbq::launch_scan_packed(a, db->grid, s);
         if (err != cudaSuccess) return cuda_fail(err, "scan_packed launch");
         return DBQ_OK;
@@ -932,6 +954,7 @@ int db_build_masks(dbq_db* db, void* stream)
     }
     DBQ_CUDA(cudaStreamSynchronize(s));
     db->built = true;
+    db->planes_t_valid = false;     // rebuilt before the next word-major sparse scan
     return DBQ_OK;
 }
 
@@ -1325,8 +1348,28 @@ int db_set_option(dbq_db* db, int option, int64_t value)
     if (!db) return fail(DBQ_EINVAL, "db is NULL");
     std::lock_guard<std::mutex> lock(db->mu);
     if (option == DBQ_OPT_SPARSE) {
-        if (value != 0 && value != 1) return fail(DBQ_EINVAL, "DBQ_OPT_SPARSE takes 0 or 1");
-        db->sparse = value == 1;
+        if (value < 0 || value > 2) return fail(DBQ_EINVAL, "DBQ_OPT_SPARSE takes 0, 1 or 2");
+        if (value == 2) {
+            if (db->storage != DBQ_STORE_BITS)
+                return fail(DBQ_EINVAL, "the word-major sparse scan needs bit-packed storage");
+            if (!db->planes_t) {
+                DeviceGuard guard(db->device);
+                if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+                int rc = dev_alloc(db, &db->planes_t, (size_t)db->n * 2 * db->wp * 4,
+                                   "word-major planes");
+                if (!rc) rc = dev_alloc(db, &db->tcounts, (size_t)db->n * 2 * 4,
+                                        "word-major sparse counts");
+                if (rc) {
+                    if (db->planes_t) db->bytes_held -= (size_t)db->n * 2 * db->wp * 4;
+                    cudaFree(db->planes_t);
+                    db->planes_t = nullptr;
+                    return rc;
+                }
+                db->planes_t_valid = false;
+            }
+        }
+        db->sparse = value != 0;
+        db->sparse_mode = (int)value;
         db->prepared = false;   // a prepared patient has no support lists yet
         return DBQ_OK;
     }

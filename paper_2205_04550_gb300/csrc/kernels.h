@@ -56,6 +56,8 @@ struct ScanPackedArgs {
     const uint32_t* sup_len;  // [2]
     Cand* group_lists;        // [ceil(grid / 8)][k]: two-level merge; null = one-level
     unsigned int* tickets;    // [1 + ceil(grid / 8)] counters of the two-level merge
+    const uint32_t* counts_in = nullptr;   // [n][2] intersection counts already computed (the
+                                 // word-major sparse scan), or null: the scan counts them
 };
 
 // Grid size (CTAs) the scan uses on this device, and its shared memory bytes.
@@ -64,6 +66,16 @@ size_t scan_packed_smem(int chunk4);
 void scan_packed_chunking(int wp4, int* chunk4, int* nchunks);
 
 cudaError_t launch_scan_packed(const ScanPackedArgs& a, int grid, cudaStream_t stream);
+
+// Word-major copy of the planes: planes [n][w4] -> planes_t [w4][n] (16-byte
+// words; w4 = 2 wp4), and the sparse counts over it: counts [n][2] += the
+// intersections of every entry with the patient over its support lists
+// ([2][wp4] and lengths [2], device), counts zeroed beforehand.
+cudaError_t launch_transpose_planes(const uint4* planes, int64_t n, int w4, uint4* planes_t,
+                                    cudaStream_t stream);
+cudaError_t launch_sparse_t_count(const uint4* planes_t, int64_t n, const uint4* patient,
+                                  int wp4, const uint32_t* sup_list, const uint32_t* sup_len,
+                                  uint32_t* counts, int sms, cudaStream_t stream);
 
 // Arguments of the fused half-precision scan (per-query thresholds).
 struct ScanF16Args {

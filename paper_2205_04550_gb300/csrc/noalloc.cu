@@ -121,6 +121,7 @@ extern "C" int db_scan_packed_noalloc(const uint32_t* planes, const uint32_t* si
     a.sup_len = nullptr;
     a.group_lists = nullptr;
     a.tickets = nullptr;
+    a.counts_in = nullptr;
     const cudaError_t err = dbq::launch_scan_packed(a, grid, s);
     if (err != cudaSuccess) return noalloc_fail(DBQ_ECUDA, cudaGetErrorString(err));
     return DBQ_OK;

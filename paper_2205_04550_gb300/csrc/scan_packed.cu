@@ -76,11 +76,14 @@ scan_packed_kernel(const ScanPackedArgs a)
         if (!kSparse && mine) E = ecount2[g0 + tid];
         if (kSparse && mine) asm volatile("prefetch.global.L2 [%0];" ::"l"(ecount2 + g0 + tid));
         __syncthreads();
-        if (warp_mode)
+        if (a.counts_in) {
+            for (int i = tid; i < 2 * gn; i += kThreads) icnt[i] = a.counts_in[2 * g0 + i];
+        } else if (warp_mode) {
             count_group_warps(a.planes, a.wp4, nullptr, g0, gn, icnt, cache, next);
-        else
+        } else {
             count_group<U, EPI, kSparse>(a.planes, a.wp4, a.chunk4, a.nchunks, a.patient,
                                          nullptr, g0, gn, icnt, sup);
+        }
         __syncthreads();   // the group's counters are complete
         for (int i = tid; i < gn; i += kThreads) {
             const int64_t e = g0 + i;

@@ -39,13 +39,14 @@ def _sparse_patient(shape, seed, frac=0.1):
     return p
 
 
+@pytest.mark.parametrize("mode", [1, 2])
 @pytest.mark.parametrize("shape,n,k", CASES)
-def test_sparse_equals_oracle(torch, shape, n, k):
+def test_sparse_equals_oracle(torch, shape, n, k, mode):
     vols, _ = random_db(shape, n, seed=n)
     with Database(shape, n, DBQ_STORE_BITS, T1, T2) as db:
         db.load(0, vols)
         db.build()
-        db.set_sparse(True)
+        db.set_sparse(mode)
         for seed in range(3):
             patient = _sparse_patient(shape, seed)
             ref = oracle.query(vols, patient, T1, T2, k)
@@ -55,7 +56,8 @@ def test_sparse_equals_oracle(torch, shape, n, k):
             assert_hits_equal(hits, ref, k)
 
 
-def test_sparse_empty_and_full_patients(torch):
+@pytest.mark.parametrize("mode", [1, 2])
+def test_sparse_empty_and_full_patients(torch, mode):
     shape = (32, 16, 8)
     vols, _ = random_db(shape, 200, seed=4)
     vols[17] = 0.0
@@ -63,7 +65,7 @@ def test_sparse_empty_and_full_patients(torch):
     with Database(shape, 200, DBQ_STORE_BITS, T1, T2) as db:
         db.load(0, vols)
         db.build()
-        db.set_sparse(True)
+        db.set_sparse(mode)
         for patient in (np.zeros(shape[::-1], np.float32), np.ones(shape[::-1], np.float32)):
             ref = oracle.query(vols, patient, T1, T2, 20)
             hits, _ = db.query(patient, 20)
@@ -77,6 +79,49 @@ def test_sparse_empty_and_full_patients(torch):
         # an empty patient against empty entries: Dice 1 for both, lowest index first
         hits, _ = db.query(np.zeros(shape[::-1], np.float32), 2)
         assert list(hits["index"]) == [17, 18] and hits["score"][0] == 1.0
+
+
+def test_word_major_copy_follows_reloads(torch):
+    """The word-major copy is rebuilt after entries are reloaded; every
+    count and hit follows the new volumes (oracle), in every mode."""
+    shape = (64, 32, 24)
+    n = 3000                                    # 12 CTAs of counts, several slices
+    vols, _ = random_db(shape, n, seed=31)
+    pats = [_sparse_patient(shape, s, frac=f) for s, f in ((1, 0.05), (2, 0.3))]
+    with Database(shape, n, DBQ_STORE_BITS, T1, T2) as db:
+        db.load(0, vols)
+        db.build()
+        db.set_sparse(2)
+        for p in pats:
+            ref = oracle.query(vols, p, T1, T2, 40)
+            hits, _ = db.query(p, 40)
+            assert_hits_equal(hits, ref, 40)
+        new, _ = random_db(shape, 500, seed=32)
+        vols[1000:1500] = new
+        vols[2999] = pats[1]                    # planted: must rank first
+        db.load(1000, new)
+        db.load(2999, pats[1][None])
+        db.build()
+        for p in pats:
+            ref = oracle.query(vols, p, T1, T2, 40)
+            counts, _ = db.scan_counts(p)
+            np.testing.assert_array_equal(counts, ref["all_counts"])
+            for mode in (2, 1, 0, 2):
+                db.set_sparse(mode)
+                hits, _ = db.query(p, 40)
+                assert_hits_equal(hits, ref, 40)
+        assert hits["index"][0] == 2999
+
+
+def test_word_major_option_errors(torch):
+    from paper_2205_04550_gb300 import DBQ_STORE_F16, DbqError
+    with Database((8, 8, 8), 4, DBQ_STORE_F16) as db:
+        with pytest.raises(DbqError, match="EINVAL"):
+            _dbq.db_set_option(db.handle, _dbq.DBQ_OPT_SPARSE, 2)
+    with Database((8, 8, 8), 4, DBQ_STORE_BITS, T1, T2) as db:
+        for bad in (-1, 3):
+            with pytest.raises(DbqError, match="EINVAL"):
+                _dbq.db_set_option(db.handle, _dbq.DBQ_OPT_SPARSE, bad)
 
 
 def test_sparse_toggle_and_surrogate(torch):
