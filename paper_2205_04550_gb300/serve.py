@@ -31,7 +31,7 @@ from __future__ import annotations
 import queue
 import threading
 import time
-from concurrent.futures import Future
+from concurrent.futures import Future, ThreadPoolExecutor
 
 import numpy as np
 
@@ -92,11 +92,12 @@ class Server:
                 the batch size from which a batch's queries of that database
                 are scanned together on the tensor cores, and use it on every
                 lane; otherwise the plans' default threshold applies.
+    copy_threads host threads copying a batch's patients into pinned staging.
     """
 
     def __init__(self, databases, mode: str = "exact", k: int = 10, n_candidates: int = 512,
                  max_batch: int = 128, lanes: int = 2, budget: int | None = None,
-                 max_wait_s: float = 0.002, tune: bool = True):
+                 max_wait_s: float = 0.002, tune: bool = True, copy_threads: int = 8):
         import torch
         self.torch = torch
         self.databases = list(databases)
@@ -113,6 +114,10 @@ class Server:
         self.budget = int(0.9 * free) if budget is None else int(budget)
         self.reserved = 0
         self._lanes = [_Lane(torch, self.databases, max_batch, k, max_vox) for _ in range(lanes)]
+        # host copies of the patients into the lanes' pinned staging run on a
+        # pool (numpy releases the GIL while copying): a batch of 128 patients
+        # is hundreds of MB, more than one thread copies in a plan's time
+        self._copy_pool = ThreadPoolExecutor(max_workers=copy_threads)
         self.tc_min = {}
         if tune and self.mode == DBQ_MODE_EXACT:
             self._tune_crossovers()
@@ -191,6 +196,7 @@ class Server:
         self.torch.cuda.synchronize()
         for lane in self._lanes:
             lane.close()
+        self._copy_pool.shutdown(wait=True)
 
     # ------------------------------------------------------------ internals
     def _tune_crossovers(self):
@@ -280,8 +286,13 @@ class Server:
             ev1 = torch.cuda.Event(enable_timing=True)
             with torch.cuda.stream(lane.stream):
                 ev0.record(lane.stream)
+                rows = lane.pinned.numpy()
+
+                def stage(i):
+                    rows[i, :batch[i].patient.size] = batch[i].patient
+
+                list(self._copy_pool.map(stage, range(n)))
                 for i, r in enumerate(batch):
-                    lane.pinned[i, :r.patient.size].numpy()[:] = r.patient
                     lane.slots[i, :r.patient.size].copy_(lane.pinned[i, :r.patient.size],
                                                          non_blocking=True)
                 which = [r.db for r in batch]
