@@ -30,7 +30,9 @@
  *     failure of the device itself (DBQ_ECUDA, DBQ_ETIMEOUT) can leave
  *     partial results in device-memory outputs that kernels write directly.
  *   * "host or device" pointers are classified with cudaPointerGetAttributes;
- *     host memory may be pageable or pinned.
+ *     host memory may be pageable or pinned.  A pinned (page-locked), 16-byte
+ *     aligned host patient is read in place by the packing kernel over the
+ *     host link; other host patients are first copied to device staging.
  *   * `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
  *     whose outputs are host memory return only after their work is complete.
  *     The *_async calls only enqueue work on `stream`.

@@ -71,6 +71,22 @@ bool is_device_ptr(const void* p)
     return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
 }
 
+// The device address of page-locked host memory (readable by kernels over the
+// host link), if p points into such memory and is 16-byte aligned (the
+// packing kernels read 16 bytes at a time); else NULL.
+const void* pinned_device_view(const void* p)
+{
+    if (!p || reinterpret_cast<uintptr_t>(p) % 16 != 0) return nullptr;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+    if (reinterpret_cast<uintptr_t>(at.devicePointer) % 16 != 0) return nullptr;
+    return at.devicePointer;
+}
+
 bool threshold_ok(float t) { return std::isfinite(t) && t > 0.0f && t <= 1.0f; }
 
 constexpr int kMaxK = 1024;
@@ -274,7 +290,10 @@ int prepare_patient(dbq_db* db, const void* patient, int kind, float t1, float t
     else
         return fail(DBQ_EINVAL, "unknown patient kind %d", kind);
     const void* src = patient;
-    if (!on_dev) {
+    const void* view = on_dev ? nullptr : pinned_device_view(patient);
+    if (view) {
+        src = view;     // page-locked host memory: the packing kernel reads it in place
+    } else if (!on_dev) {
         int rc = ensure_stage(db, bytes);
         if (rc) return rc;
         DBQ_CUDA(cudaMemcpyAsync(db->stage, patient, bytes, cudaMemcpyHostToDevice, s));

@@ -112,6 +112,37 @@ def test_patient_kinds_f32_f16_bits_host_and_device(torch):
             assert_hits_equal(hits, ref, 9)
 
 
+def test_pinned_host_patients_read_in_place(torch):
+    """Page-locked host patients (read by the packing kernel in place) and an
+    unaligned view into one (staged instead) give the oracle's hits."""
+    shape = (33, 31, 30)
+    vols, patient = random_db(shape, 400, seed=77, plant=(5,))
+    ref = oracle.query(vols, patient, T1, T2, 12)
+    with _db_from(vols, torch=torch) as db:
+        pinned = torch.from_numpy(patient).pin_memory()
+        hits, _ = db.query(pinned.numpy(), 12)
+        assert_hits_equal(hits, ref, 12)
+        counts, pcount = db.scan_counts(pinned.numpy())
+        np.testing.assert_array_equal(counts, ref["all_counts"])
+        np.testing.assert_array_equal(pcount, ref["pcount"])
+        # f32 patient one element into a pinned buffer: 4-byte aligned only
+        buf = torch.zeros(patient.size + 1, dtype=torch.float32).pin_memory()
+        buf[1:] = torch.from_numpy(patient.reshape(-1))
+        hits_u, _ = db.query(buf.numpy()[1:].reshape(patient.shape), 12)
+        assert hits_u.tobytes() == hits.tobytes()
+        # f16 and bit-plane patients from pinned memory
+        p16 = torch.from_numpy(patient.astype(np.float16).view(np.int16)).pin_memory()
+        ref16 = oracle.query(vols, patient.astype(np.float16).astype(np.float32), T1, T2, 12)
+        hits16, _ = db.query(p16.numpy().view(np.uint16), 12, kind=DBQ_F16)
+        assert_hits_equal(hits16, ref16, 12)
+        bits = pack_bits_np(oracle.threshold(patient, T1, T2))
+        refb = oracle.query(vols, patient, T1, T2, 12,
+                            patient_mask=oracle.unpack_planes(bits, patient.size))
+        pb = torch.from_numpy(bits.view(np.int32)).pin_memory()
+        hitsb, _ = db.query(pb.numpy().view(np.uint32), 12)
+        assert_hits_equal(hitsb, refb, 12)
+
+
 def test_bits_patient_ignores_bits_past_last_voxel(torch):
     shape = (9, 10, 11)     # 990 voxels: the last word has 30 used bits
     vols, patient = random_db(shape, 50, seed=5)
