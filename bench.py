@@ -11,8 +11,12 @@ Prints one JSON line.  ``value`` is database entries scanned per second over
 all ranks (device-timed with CUDA events, inputs resident in HBM; the 26 GB
 database is far larger than the 129 MB L2, so no L2 flush is needed);
 ``e2e`` is the same metric through db_query with a pinned host patient and
-host results.  ``--impl reference`` times the CPU oracle on a bounded sample
-of the same workload instead.
+host results.  The default line also carries the batched embedding +
+re-rank record (``batched``), the sparse scans of the same queries and, run
+in child processes, the exact scan on the other configurations
+(``other_configs``: 1,024 x 64^3 bit-packed, 100,000 x 64^3 binary16).
+``--impl reference`` times the CPU oracle on a bounded sample of the same
+workload instead.
 """
 from __future__ import annotations
 
@@ -605,6 +609,34 @@ def measure_embed(wl, torch, steps, warmup, workload):
     return line
 
 
+def other_configs_record(steps: int, warmup: int):
+    """The exact scan on the other configurations (1,024 x 64^3 bit-packed with
+    the L2 flushed before every step; 100,000 x 64^3 binary16 with per-query
+    thresholds), each measured by this script in a child process (its own
+    CUDA context and memory), condensed into the default line."""
+    import subprocess
+    out = {}
+    for name, st, wu in (("exact_packed_1k_64", max(steps, 20), max(warmup, 5)),
+                         ("f16_100k_64", min(steps, 10), warmup)):
+        cmd = [sys.executable, os.path.abspath(__file__), "--workload", name, "--steps", str(st),
+               "--warmup", str(wu), "--no-cpu-baseline"]
+        try:
+            res = subprocess.run(cmd, capture_output=True, text=True, timeout=900, check=True)
+            full = json.loads([l for l in res.stdout.splitlines() if l.startswith("{")][-1])
+        except Exception as exc:   # report, do not fail the headline line
+            out[name] = {"error": str(exc)[:200]}
+            continue
+        r = full["roofline"]
+        out[name] = {"desc": full["config"]["desc"], "value": full["value"], "unit": full["unit"],
+                     "ms_per_step": full["ms_per_step"], "steps": st, "warmup": wu,
+                     "l2": full["config"]["l2"], "e2e": full["e2e"],
+                     "roofline": {k: r[k] for k in ("kernel", "achieved", "peak", "unit", "frac",
+                                                    "traffic", "kernel_ms", "frac_of_nominal")
+                                  if k in r},
+                     "clocks": full["clocks"]}
+    return out
+
+
 def batched_record(torch, steps: int, warmup: int):
     """The second half of the metric, "batched queries/s at top-1 match", on
     its own configuration (100,000 x 128^3 bit-packed with 2 x 4096-d bf16
@@ -1008,6 +1040,8 @@ def main(argv=None):
     ap.add_argument("--cpu-sample", type=int, default=32)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-other-configs", action="store_true",
+                    help="leave out the other configurations' records of the default line")
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched (embedding + re-rank) record of the default line")
     args = ap.parse_args(argv)
@@ -1236,6 +1270,8 @@ def main(argv=None):
     db.close()
     if args.workload == DEFAULT_WORKLOAD and not args.no_batched:
         line["batched"] = batched_record(torch, steps=min(args.steps, 10), warmup=3)
+    if args.workload == DEFAULT_WORKLOAD and not args.no_other_configs and world == 1:
+        line["other_configs"] = other_configs_record(args.steps, args.warmup)
     if dist:
         dist.destroy_process_group()
     if rank == 0:
