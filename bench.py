@@ -40,6 +40,11 @@ WORKLOADS = {
     "exact_packed_2k_128": dict(shape=(128, 128, 128), n=2000, k=64, t1=0.6, t2=0.25,
                                 desc="2,000 x 128^3 bit-packed (1.05 GB, profiling size), "
                                      "t=(0.6,0.25), top-64"),
+    # the largest bench patient's support over 4,000 entries (158 MB) exceeds the
+    # L2, so the sparse scans' DRAM counters mean something at profiling size
+    "exact_packed_4k_128": dict(shape=(128, 128, 128), n=4000, k=64, t1=0.6, t2=0.25,
+                                desc="4,000 x 128^3 bit-packed (2.1 GB, profiling size), "
+                                     "t=(0.6,0.25), top-64"),
     "f16_100k_64": dict(shape=(64, 64, 64), n=100_000, k=16, t1=0.6, t2=0.25, storage="f16",
                         desc="100,000 x 64^3 binary16 (52.4 GB), per-query thresholds "
                              "t1~U(0.5,0.8), t2~U(0.15,0.35), top-16"),
