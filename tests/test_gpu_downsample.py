@@ -58,6 +58,11 @@ def test_downsampled_masks_and_query(torch, shape, f):
             ds.set_sparse(True)
             hits_s, _ = ds.query(torch.from_numpy(patient).cuda(), k)
             assert hits_s.tobytes() == hits.tobytes()
+            ds.set_sparse(2)                    # the word-major copy of the coarse planes
+            hits_t, _ = ds.query(patient, k)
+            assert hits_t.tobytes() == hits.tobytes()
+            counts_t, _ = ds.scan_counts(patient)
+            np.testing.assert_array_equal(counts_t, cnt)
         finally:
             ds.close()
 
