@@ -349,9 +349,12 @@ int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int 
  * db_scan_counts) over a word-major copy of the planes ([2 wp][n] 16-byte
  * words: each support word of every entry is one contiguous run), which
  * the library allocates here (DBQ_ENOMEM if the device lacks room: N x 2 x
- * words-per-plane x 4 bytes plus N x 8) and rebuilds at the first such scan
- * after db_build_masks; the other paths treat 2 as 1.  DBQ_EINVAL for 2 on
- * half-precision storage or for any value outside 0..2.
+ * words-per-plane x 4 bytes plus N x 8) and builds in db_build_masks (or
+ * here, if the database is already built).  Plans use
+ * the copy too, for a database's queries that do not go to the tensor-core
+ * contraction: the counts of all of them over the copy, then the
+ * contraction's per-query selection.  The other paths treat 2 as 1.
+ * DBQ_EINVAL for 2 on half-precision storage or for any value outside 0..2.
  */
 int db_set_option(dbq_db* db, int option, int64_t value);
 

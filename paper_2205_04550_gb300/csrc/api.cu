@@ -362,8 +362,8 @@ int launch_query(dbq_db* db, int k, dbq::Hit* hits, uint32_t* counts_out, cudaSt
             }
             DBQ_CUDA(cudaMemsetAsync(db->tcounts, 0, (size_t)db->n * 2 * sizeof(uint32_t), s));
             cudaError_t err = dbq::launch_sparse_t_count(
-                db->planes_t, db->n, reinterpret_cast<const uint4*>(db->pplanes), (int)db->wp4,
-                db->plist, db->plen, db->tcounts, db->grid, s);
+                db->planes_t, db->n, 1, reinterpret_cast<const uint4*>(db->pplanes),
+                (int)db->wp4, db->plist, db->plen, db->tcounts, 0, 2, 1, db->grid, s);
             if (err != cudaSuccess) return cuda_fail(err, "word-major sparse count launch");
         }
         dbq::ScanPackedArgs a;
@@ -971,9 +971,15 @@ int db_build_masks(dbq_db* db, void* stream)
                                              db->codes, db->codes8, db->code_norm, s);
         if (err != cudaSuccess) return cuda_fail(err, "sketch launch");
     }
+    db->planes_t_valid = false;
+    if (db->sparse_mode == 2) {     // the word-major copy follows the planes
+        cudaError_t err = dbq::launch_transpose_planes(reinterpret_cast<const uint4*>(db->planes),
+                                                       db->n, 2 * (int)db->wp4, db->planes_t, s);
+        if (err != cudaSuccess) return cuda_fail(err, "word-major copy launch");
+        db->planes_t_valid = true;
+    }
     DBQ_CUDA(cudaStreamSynchronize(s));
     db->built = true;
-    db->planes_t_valid = false;     // rebuilt before the next word-major sparse scan
     return DBQ_OK;
 }
 
@@ -1386,6 +1392,16 @@ int db_set_option(dbq_db* db, int option, int64_t value)
                 }
                 db->planes_t_valid = false;
             }
+            if (db->built && !db->planes_t_valid) {   // built now, not at the first scan
+                DeviceGuard guard(db->device);
+                if (!guard.ok) return fail(DBQ_ECUDA, "cannot select device %d", db->device);
+                cudaError_t err = dbq::launch_transpose_planes(
+                    reinterpret_cast<const uint4*>(db->planes), db->n, 2 * (int)db->wp4,
+                    db->planes_t, nullptr);
+                if (err == cudaSuccess) err = cudaStreamSynchronize(nullptr);
+                if (err != cudaSuccess) return cuda_fail(err, "word-major copy");
+                db->planes_t_valid = true;
+            }
         }
         db->sparse = value != 0;
         db->sparse_mode = (int)value;
@@ -1594,11 +1610,20 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
         use_tc[d] = p->tc_rows > 0 && thr > 0 && per_db[d] >= thr &&
                     db->v <= ((int64_t)1 << 24) && db->wp >= dbq::tc_scan_min_words();
     }
+    // databases with a word-major copy (DBQ_OPT_SPARSE 2) whose queries stay off
+    // the contraction: counts of all their queries over the copy, then the
+    // contraction's per-query selection on those counts
+    std::vector<char> use_wm((size_t)ndb, 0);
+    for (int d = 0; d < ndb; ++d) {
+        const dbq_db* db = p->dbs[d];
+        use_wm[d] = !use_tc[d] && p->tc_rows > 0 && db->sparse_mode == 2 && db->planes_t &&
+                    db->planes_t_valid && db->v <= ((int64_t)1 << 24);
+    }
     // work-item budget: items_per_sm * SMs, shared in proportion to bytes
     double total = 0;
     for (int q = 0; q < nq; ++q) {
         const dbq_db* db = p->dbs[db_of_query[q]];
-        if (!use_tc[db_of_query[q]]) total += (double)db->n * db->wp4;
+        if (!use_tc[db_of_query[q]] && !use_wm[db_of_query[q]]) total += (double)db->n * db->wp4;
     }
     struct TcGroup {
         const dbq_db* db;
@@ -1606,6 +1631,14 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
         const uint32_t* qplanes;
     };
     std::vector<TcGroup> tc_groups;
+    struct WmGroup {
+        const dbq_db* db;
+        int slot, cnt;
+        const uint32_t* qplanes;
+        const uint32_t* sup;
+        const uint32_t* len;
+    };
+    std::vector<WmGroup> wm_groups;
     const double budget = (double)p->items_per_sm * p->sms;
     int nitems = 0;
     size_t word_off = 0, sup_off = 0;
@@ -1653,7 +1686,7 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
             t.nchunks = db->nchunks;
             t.k = p->k;
             int sl = 1;
-            if (!use_tc[d] && total > 0)
+            if (!use_tc[d] && !use_wm[d] && total > 0)
                 sl = (int)std::lround(budget * ((double)db->n * db->wp4) / total);
             sl = std::max(1, std::min(sl, p->max_slices));
             if ((int64_t)sl > db->n) sl = (int)db->n;
@@ -1670,6 +1703,10 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
             // no work items: the group runs as a contraction after the scan
             for (int i = 0; i < cnt; ++i) p->tasks_host[slot + i].slices = 0;
             tc_groups.push_back({db, slot, cnt, gplanes});
+        } else if (use_wm[d]) {
+            // no work items: counts over the word-major copy after the scan
+            for (int i = 0; i < cnt; ++i) p->tasks_host[slot + i].slices = 0;
+            wm_groups.push_back({db, slot, cnt, gplanes, gsup, glen});
         } else {
             // slice-major: the same entry slice of every query of this
             // database in consecutive items, so CTAs that run them at the
@@ -1715,6 +1752,22 @@ int db_plan_query(dbq_plan* p, const int* db_of_query, int nq, const void* const
             err = dbq::launch_tc_select(p->tasks_dev, tg.slot + c0, nqc, p->tc_counts, tg.db->n,
                                         ta.stride, s);
             if (err != cudaSuccess) return cuda_fail(err, "tensor-core selection launch");
+        }
+    }
+    for (const WmGroup& wg : wm_groups) {
+        const int64_t stride = dbq::tc_counts_stride(wg.db->n);
+        for (int c0 = 0; c0 < wg.cnt; c0 += p->tc_rows) {
+            const int nqc = std::min(p->tc_rows, wg.cnt - c0);
+            DBQ_CUDA(cudaMemsetAsync(p->tc_counts, 0, (size_t)2 * nqc * stride * 4, s));
+            err = dbq::launch_sparse_t_count(
+                wg.db->planes_t, wg.db->n, nqc,
+                reinterpret_cast<const uint4*>(wg.qplanes + (size_t)c0 * 2 * wg.db->wp),
+                (int)wg.db->wp4, wg.sup + (size_t)c0 * 2 * wg.db->wp4, wg.len + 2 * c0,
+                p->tc_counts, stride, 1, (int64_t)nqc * stride, p->sms, s);
+            if (err != cudaSuccess) return cuda_fail(err, "word-major sparse count launch");
+            err = dbq::launch_tc_select(p->tasks_dev, wg.slot + c0, nqc, p->tc_counts, wg.db->n,
+                                        stride, s);
+            if (err != cudaSuccess) return cuda_fail(err, "selection launch");
         }
     }
     return DBQ_OK;

@@ -68,14 +68,17 @@ void scan_packed_chunking(int wp4, int* chunk4, int* nchunks);
 cudaError_t launch_scan_packed(const ScanPackedArgs& a, int grid, cudaStream_t stream);
 
 // Word-major copy of the planes: planes [n][w4] -> planes_t [w4][n] (16-byte
-// words; w4 = 2 wp4), and the sparse counts over it: counts [n][2] += the
-// intersections of every entry with the patient over its support lists
-// ([2][wp4] and lengths [2], device), counts zeroed beforehand.
+// words; w4 = 2 wp4), and the sparse counts over it for nq patients
+// (patients [nq][2][wp4], support lists [nq][2][wp4] and lengths [nq][2],
+// device): the intersections of entry e with patient q are added to
+// counts[q qstride + e estride] (plane 1) and to that + poff (plane 2), which
+// the caller zeroes beforehand.
 cudaError_t launch_transpose_planes(const uint4* planes, int64_t n, int w4, uint4* planes_t,
                                     cudaStream_t stream);
-cudaError_t launch_sparse_t_count(const uint4* planes_t, int64_t n, const uint4* patient,
-                                  int wp4, const uint32_t* sup_list, const uint32_t* sup_len,
-                                  uint32_t* counts, int sms, cudaStream_t stream);
+cudaError_t launch_sparse_t_count(const uint4* planes_t, int64_t n, int nq, const uint4* patients,
+                                  int wp4, const uint32_t* sup_lists, const uint32_t* sup_lens,
+                                  uint32_t* counts, int64_t qstride, int64_t estride,
+                                  int64_t poff, int sms, cudaStream_t stream);
 
 // Arguments of the fused half-precision scan (per-query thresholds).
 struct ScanF16Args {

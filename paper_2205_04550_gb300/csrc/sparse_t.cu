@@ -12,8 +12,8 @@
 // (transpose_planes_kernel) after the database changes.
 //
 // Counting: a CTA of kCountThreads threads owns kCountThreads consecutive
-// entries (one per thread) and one of `splits` slices of the patient's
-// support positions, streams those words of its entries (twelve 16-byte loads
+// entries (one per thread) of one patient and one of `splits` slices of that
+// patient's support positions, streams those words of its entries (twelve 16-byte loads
 // in flight per thread, 64 registers: four CTAs per SM; eight loads measured
 // 7 % slower) and adds its partial counts into the per-entry
 // counters with one atomic per entry and plane.  The fused scan
@@ -57,22 +57,31 @@ transpose_planes_kernel(const uint4* __restrict__ planes, int64_t n, int w4,
     }
 }
 
-// Partial counts of entries [blockIdx.x * kCountThreads, +kCountThreads) over
-// support slice blockIdx.y of gridDim.y: positions p of the concatenated
-// support (plane 1's list, then plane 2's), word off(p) of the entry-major
-// layout = row off(p) of planes_t.
+// Partial counts of entries [blockIdx.y * kCountThreads, +kCountThreads) of
+// query blockIdx.x (the fastest grid index, so CTAs running together read the
+// same entries for different patients) over support slice blockIdx.z of
+// gridDim.z: positions p of the query's concatenated support (plane 1's list,
+// then plane 2's), word off(p) of the entry-major layout = row off(p) of
+// planes_t.  Query q's patient is patient + q * 2 wp4, its lists sup_list +
+// q * 2 wp4 and lengths sup_len + 2 q; entry e's counters are
+// counts[q * qstride + e * estride] (plane 1) and the same + poff (plane 2).
 __global__ void __launch_bounds__(kCountThreads, 4)
-sparse_t_count_kernel(const uint4* __restrict__ planes_t, int64_t n, const uint4* __restrict__ patient,
-                      int wp4, const uint32_t* __restrict__ sup_list,
-                      const uint32_t* __restrict__ sup_len, uint32_t* __restrict__ counts)
+sparse_t_count_kernel(const uint4* __restrict__ planes_t, int64_t n,
+                      const uint4* __restrict__ patients, int wp4,
+                      const uint32_t* __restrict__ sup_lists,
+                      const uint32_t* __restrict__ sup_lens, uint32_t* __restrict__ counts,
+                      int64_t qstride, int64_t estride, int64_t poff)
 {
     __shared__ uint32_t s_off[kCountChunk];
     __shared__ uint4 s_pw[kCountChunk];
-    const int l1 = (int)sup_len[0], l2 = (int)sup_len[1];
+    const int q = blockIdx.x;
+    const uint4* patient = patients + (int64_t)q * 2 * wp4;
+    const uint32_t* sup_list = sup_lists + (int64_t)q * 2 * wp4;
+    const int l1 = (int)sup_lens[2 * q], l2 = (int)sup_lens[2 * q + 1];
     const int total = l1 + l2;
-    const int p0 = (int)((int64_t)total * blockIdx.y / gridDim.y);
-    const int p1 = (int)((int64_t)total * (blockIdx.y + 1) / gridDim.y);
-    const int64_t e = (int64_t)blockIdx.x * kCountThreads + threadIdx.x;
+    const int p0 = (int)((int64_t)total * blockIdx.z / gridDim.z);
+    const int p1 = (int)((int64_t)total * (blockIdx.z + 1) / gridDim.z);
+    const int64_t e = (int64_t)blockIdx.y * kCountThreads + threadIdx.x;
     const bool live = e < n;
     const uint4* col = planes_t + (live ? e : 0);
     uint32_t a1 = 0, a2 = 0;
@@ -103,8 +112,9 @@ sparse_t_count_kernel(const uint4* __restrict__ planes_t, int64_t n, const uint4
         }
     }
     if (live) {
-        if (a1) atomicAdd(&counts[2 * e], a1);
-        if (a2) atomicAdd(&counts[2 * e + 1], a2);
+        uint32_t* c = counts + (int64_t)q * qstride + e * estride;
+        if (a1) atomicAdd(c, a1);
+        if (a2) atomicAdd(c + poff, a2);
     }
 }
 
@@ -122,19 +132,21 @@ cudaError_t launch_transpose_planes(const uint4* planes, int64_t n, int w4, uint
     return cudaGetLastError();
 }
 
-cudaError_t launch_sparse_t_count(const uint4* planes_t, int64_t n, const uint4* patient,
-                                  int wp4, const uint32_t* sup_list, const uint32_t* sup_len,
-                                  uint32_t* counts, int sms, cudaStream_t stream)
+cudaError_t launch_sparse_t_count(const uint4* planes_t, int64_t n, int nq, const uint4* patients,
+                                  int wp4, const uint32_t* sup_lists, const uint32_t* sup_lens,
+                                  uint32_t* counts, int64_t qstride, int64_t estride,
+                                  int64_t poff, int sms, cudaStream_t stream)
 {
-    if (n <= 0) return cudaSuccess;
-    const int64_t bx = (n + kCountThreads - 1) / kCountThreads;
+    if (n <= 0 || nq <= 0) return cudaSuccess;
+    const int64_t by = (n + kCountThreads - 1) / kCountThreads;
     // enough CTAs for about eight per SM (two waves of four)
-    int64_t splits = (8LL * sms + bx - 1) / bx;
+    int64_t splits = (8LL * sms + by * nq - 1) / (by * nq);
     if (splits < 1) splits = 1;
     if (splits > 64) splits = 64;
-    const dim3 grid((unsigned)bx, (unsigned)splits);
-    sparse_t_count_kernel<<<grid, kCountThreads, 0, stream>>>(planes_t, n, patient, wp4, sup_list,
-                                                              sup_len, counts);
+    const dim3 grid((unsigned)nq, (unsigned)by, (unsigned)splits);
+    sparse_t_count_kernel<<<grid, kCountThreads, 0, stream>>>(planes_t, n, patients, wp4,
+                                                              sup_lists, sup_lens, counts,
+                                                              qstride, estride, poff);
     return cudaGetLastError();
 }
 

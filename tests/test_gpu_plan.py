@@ -406,3 +406,57 @@ def test_plan_tensor_core_query_counts(torch, two_dbs, nq):
     assert tc.tobytes() == cc.tobytes()
     for q in sorted({0, nq // 2, nq - 1}):
         assert_hits_equal(tc[q], oracle.query(v1, pats[q], T1, T2, k), k)
+
+
+def test_plan_word_major_sparse_counts(torch, two_dbs):
+    """Queries of databases with a word-major copy (DBQ_OPT_SPARSE 2) that stay
+    off the contraction: the counts of all of them over the copy, then the
+    per-query selection -- the oracle's hits, bit-identical to the CUDA-core
+    loop; 140 queries of one database (two passes of 128), and graph replay."""
+    (d1, v1), (d2, v2) = two_dbs
+    rng = np.random.default_rng(41)
+    p1 = _patients(rng, v1, 5) + [_box_patient(rng, (64, 64, 64), f) for f in (0.01, 0.05, 0.2, 0.5)]
+    p2 = _patients(rng, v2, 60) + [_box_patient(rng, (32, 32, 32), 0.002 * (1 + i)) for i in range(78)]
+    p2 += [np.zeros_like(p2[0]), np.ones_like(p2[0])]
+    pats = p1 + p2
+    which = [0] * len(p1) + [1] * len(p2)
+    perm = rng.permutation(len(pats))
+    pats = [pats[i] for i in perm]
+    which = [which[i] for i in perm]
+    k = 12
+    cc = _run_plan(torch, [d1, d2], which, pats, k, tc_min=0)
+    d1.set_sparse(2)
+    d2.set_sparse(2)
+    try:
+        wm = _run_plan(torch, [d1, d2], which, pats, k, tc_min=0)
+        assert wm.tobytes() == cc.tobytes()
+        for q, (p, w) in enumerate(zip(pats, which)):
+            vols = v1 if w == 0 else v2
+            assert_hits_equal(wm[q], oracle.query(vols, p, T1, T2, k), k)
+        # captured once, replayed with new patients in the same device slots
+        dev = [torch.from_numpy(p).cuda() for p in pats]
+        hits = torch.zeros((len(pats), k * 40), dtype=torch.uint8, device="cuda")
+        with Plan([d1, d2], len(pats), k) as plan:
+            plan.set_tc_min_queries(0)
+            keep = []
+            plan.query(which, dev, hits, keep=keep)     # first call outside capture
+            torch.cuda.synchronize()
+            g = torch.cuda.CUDAGraph()
+            s = torch.cuda.Stream()
+            s.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    plan.query(which, dev, hits, keep=keep)
+            torch.cuda.synchronize()
+            new = [_box_patient(rng, (64, 64, 64) if w == 0 else (32, 32, 32), 0.05) for w in which]
+            for sl, p in zip(dev, new):
+                sl.copy_(torch.from_numpy(p))
+            g.replay()
+            torch.cuda.synchronize()
+            got = hits.cpu().numpy().view(_dbq.HIT_DTYPE)
+            for q in range(0, len(new), 7):
+                vols = v1 if which[q] == 0 else v2
+                assert_hits_equal(got[q], oracle.query(vols, new[q], T1, T2, k), k)
+    finally:
+        d1.set_sparse(False)
+        d2.set_sparse(False)
