@@ -835,11 +835,12 @@ def run_plan_mix(args, wl, torch):
     which, pats = _mix_patients(torch, wl, nq)
     hits = torch.zeros((nq, k * 40), dtype=torch.uint8, device="cuda")
     results = {}
-    for sparse in (False, True):
+    for mode in (0, 1, 2):
+        sparse = mode > 0
         for d in dbs:
-            d.set_sparse(sparse)
+            d.set_sparse(mode)
         with Plan(dbs, nq, k) as plan:
-            tuned = tune.tune_plan(plan, which, pats, hits, sparse_flags=sparse)
+            tuned = tune.tune_plan(plan, which, pats, hits, sparse_flags=mode)
             keep = []
             plan.query(which, pats, hits, keep=keep)
             torch.cuda.synchronize()
@@ -870,7 +871,7 @@ def run_plan_mix(args, wl, torch):
                 per = (16 * _support_granules(torch, pats[q], wl["t1"], wl["t2"]) if sparse
                        else 2 * ((nx * ny * nz + 31) // 32) * 4)
                 nbytes += part["n"] * (per + 8)
-            results["sparse" if sparse else "dense"] = {
+            results[("dense", "sparse", "sparse_word_major")[mode]] = {
                 "queries_per_s": world * args.steps * nq / el,
                 "ms_per_launch": 1000.0 * el / args.steps,
                 "bytes_per_launch": nbytes, "gbs": nbytes / (el / args.steps) / 1e9,
@@ -894,6 +895,7 @@ def run_plan_mix(args, wl, torch):
                                                                    * part["shape"][2] + 127) // 128)
                                                 for part in wl["mix"]) / 1e9)},
             "dense": dense, "sparse": results["sparse"],
+            "sparse_word_major": results["sparse_word_major"],
             # per dense launch: a patient-packing kernel per database, and for
             # each database past its tuned crossover the tensor-core
             # contraction and its selection kernel (both databases here)

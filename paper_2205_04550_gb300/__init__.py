@@ -80,6 +80,7 @@ class Database:
         nx, ny, nz = shape
         self.shape = (int(nx), int(ny), int(nz))
         self.sparse = False
+        self.sparse_mode = 0
         self.capacity = int(capacity)
         self.storage = storage
         self.t1, self.t2 = float(np.float32(t1)), float(np.float32(t2))
@@ -127,6 +128,8 @@ class Database:
         obj.t1, obj.t2 = self.t1, self.t2
         obj.n_params = self.n_params
         obj.embed = False
+        obj.sparse = False
+        obj.sparse_mode = 0
         obj.sketch = False
         obj.handle = db_create_downsampled(self.handle, factor)
         return obj
@@ -138,6 +141,7 @@ class Database:
         mode = 2 if on == 2 else (1 if on else 0)
         db_set_option(self.handle, DBQ_OPT_SPARSE, mode)
         self.sparse = bool(mode)
+        self.sparse_mode = mode
 
     def embeddings(self, first: int, count: int):
         """-> dict of bf16 bits [count,2,d] uint16, e4m3 codes [count,2,d] uint8,

@@ -211,7 +211,7 @@ class Server:
         for d, db in enumerate(self.databases):
             pats = [torch.zeros(self.voxels[d], dtype=torch.float32, device="cuda")]
             res = _tune.tune_crossover(plan, d, pats, self._lanes[0].hits,
-                                       sparse=getattr(db, "sparse", False))
+                                       sparse=getattr(db, "sparse_mode", 0))
             self.tc_min[d] = int(res["tc_min"])
             for lane in self._lanes:
                 lane.plan.set_tc_min_queries(self.tc_min[d], db=d)

@@ -75,7 +75,7 @@ def crossover_key(db, sparse=False) -> str:
     import torch
     props = torch.cuda.get_device_properties(torch.cuda.current_device())
     return json.dumps({"gpu": props.name, "sms": props.multi_processor_count,
-                       "crossover": [list(db.shape), db.capacity], "sparse": bool(sparse)},
+                       "crossover": [list(db.shape), db.capacity], "sparse": int(sparse)},
                       sort_keys=True)
 
 
@@ -133,8 +133,9 @@ def tune_plan(plan, which, patients_dev, hits_dev, candidates=CANDIDATES, reps: 
         for d, db in enumerate(plan.databases):
             mine = [patients_dev[q] for q in range(len(which)) if which[q] == d]
             if mine:
+                mode = getattr(db, "sparse_mode", 1 if sparse_flags else 0)
                 tc_min[str(d)] = tune_crossover(plan, d, mine, hits_dev, use_cache=use_cache,
-                                                sparse=bool(sparse_flags))["tc_min"]
+                                                sparse=mode)["tc_min"]
     key = workload_key(plan, which, sparse_flags)
     if use_cache:
         hit = _load_cache().get(key)
