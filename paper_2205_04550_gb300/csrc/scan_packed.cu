@@ -20,9 +20,12 @@
 //     counter.
 //   * When every chunk of a group of entries is done the CTA knows their
 //     exact I_1, I_2, computes the binary64 scores and keeps a running
-//     top-k in shared memory (bitonic sort, order: score desc, index asc).
+//     top-k in shared memory (topk.cuh; order: score desc, index asc).
 //   * Each CTA writes its list to scratch; the last CTA to finish (atomic
-//     ticket, no spinning) merges all lists and writes the k hits.
+//     ticket, no spinning; in groups of CTAs first for larger k) merges the
+//     lists and writes the k hits.
+//   * With counts_in (the word-major sparse scan) the counts come from
+//     memory instead of the planes; scoring and selection are the same.
 #include "kernels.h"
 #include "scan_core.cuh"
 #include "topk.cuh"

@@ -9,12 +9,16 @@
 //
 // Shared-memory protocol (all threads of the block take part in every call):
 //   * slots [0, k) hold the running top-k, best first, padded with sentinels;
-//   * topk_offer() appends a candidate at k + (atomic counter) when it beats
-//     the current k-th best -- at most kTopkCap - k offers between flushes;
-//   * topk_flush() bitonic-sorts the k + appended slots and keeps the first k.
+//   * topk_offer() appends a candidate at k + (a warp's share of an atomic
+//     counter) when it beats the current k-th best -- at most kTopkCap - k
+//     offers between flushes;
+//   * topk_flush() merges the appended candidates into the k best: by
+//     direct counts for small rounds, by a merge tree (k <= kTreeK) or a
+//     bitonic sort for large ones.
 // After the scan each CTA publishes its k slots to global scratch and the
 // last CTA to arrive (atomicInc ticket that wraps to zero, no spinning)
-// merges all of them with the same offer/flush rounds.
+// merges all of them (topk_merge_published: warp tournaments, merge trees or
+// ranks, else offer/flush rounds), directly or through groups of CTAs.
 #pragma once
 
 #include "common.cuh"
