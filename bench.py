@@ -129,11 +129,11 @@ DEFAULT_WORKLOAD = "exact_packed_50k_128"
 TRAFFIC = {
     "scan_packed_kernel": dict(files=("scan_packed.cu", "scan_core.cuh", "topk.cuh",
                                       "common.cuh", "dice.cuh"),
-                               sha="e32043bc771f7e1f", entries=2000, grid=(128, 128, 128),
+                               sha="38baec0056c291f0", entries=2000, grid=(128, 128, 128),
                                read_bytes=1049227264, write_bytes=3523328,
                                capture="profiles/scan_packed_2k_128_ncu_full.md"),
     "scan_f16_kernel": dict(files=("scan_f16.cu", "topk.cuh", "common.cuh", "dice.cuh"),
-                            sha="a39d7727a862e634", entries=4000, grid=(64, 64, 64),
+                            sha="7fd859a44601ab7f", entries=4000, grid=(64, 64, 64),
                             read_bytes=2097329408, write_bytes=3185152,
                             capture="profiles/scan_f16_4k_64_ncu_full.md"),
 }
