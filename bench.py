@@ -499,6 +499,21 @@ def measure_embed(wl, torch, steps, warmup, workload):
     wall1 = time.time()
     elapsed = t0.elapsed_time(t1) / 1000.0
     stages = {a: v / args.steps for a, v in stage_sum.items()}
+    # the same launches with the other dense re-rank pass (the library picks
+    # the deduplicated pass for groups of 160 queries or more, else per query)
+    dedupe = nq >= 160
+    db.set_rerank(1 if dedupe else 2)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    alt_ms = 0.0
+    for _ in range(args.steps):
+        alt_hits, _ = step()
+        alt_ms += _dbq.db_stage_times(h)["rerank"]
+    db.set_rerank(0)
+    alt_line = {"pass": "per query" if dedupe else "deduplicated",
+                "rerank_ms": alt_ms / args.steps,
+                "identical_hits": bool(alt_hits.tobytes() == hits.tobytes())}
     # the same launches with sparse re-ranking (patient support only)
     db.set_sparse(True)
     for _ in range(2):
@@ -555,7 +570,11 @@ def measure_embed(wl, torch, steps, warmup, workload):
     dist_error = None if wl.get("sketch") else _embed_distance_error(db, plist, mode, wl, stream)
     value = world * args.steps * nq / elapsed
     words = (nx * ny * nz + 31) // 32
-    rr_bytes = nq * c * (2 * words * 4 + 8)
+    # algorithmic bytes of the re-rank: the planes of every candidate entry
+    # the pass reads (each distinct one once when deduplicated) + 8 B of
+    # entry sizes per candidate
+    distinct = int(np.unique(pf_cand).size)
+    rr_bytes = (distinct if dedupe else nq * c) * 2 * words * 4 + nq * c * 8
     gemm_flops = 2.0 * nq * wl["n"] * 2 * dims
     gemm_bytes = wl["n"] * 2 * dims * (1 if mode == DBQ_MODE_EMBED_FP8 else 2) + nq * wl["n"] * 4
     peak, peak_kind = _peaks()
@@ -565,7 +584,8 @@ def measure_embed(wl, torch, steps, warmup, workload):
     dominant = "rerank" if stages["rerank"] >= stages["distances"] or mode == DBQ_MODE_HASH else "gemm"
     if dominant == "rerank":
         ach = rr_bytes / (stages["rerank"] / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": "rerank_kernel", "achieved": ach, "peak": peak,
+        roof = {"bound": "hbm", "kernel": "rr_count_kernel" if dedupe else "rerank_kernel",
+                "achieved": ach, "peak": peak,
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
                 "algorithmic_bytes_per_launch": rr_bytes, "kernel_ms": stages["rerank"]}
     else:
@@ -604,9 +624,14 @@ def measure_embed(wl, torch, steps, warmup, workload):
                      "note": "sign codes as E4M3 0/1 bytes on the tensor cores (FP8 GEMM), "
                              "|q|+|e|-2q.e exact"}
                     if mode == DBQ_MODE_HASH else None),
-        "rerank": {"gbs": rr_bytes / (stages["rerank"] / 1000.0) / 1e9,
-                   "bytes_per_launch": rr_bytes},
-        "gpu_launches": 5 * args.steps,   # per step: pack, embed, GEMM, select, re-rank
+        "rerank": {"pass": "deduplicated" if dedupe else "per query",
+                   "gbs": rr_bytes / (stages["rerank"] / 1000.0) / 1e9,
+                   "bytes_per_launch": rr_bytes, "candidate_pairs": nq * c,
+                   "distinct_candidates": distinct, "other_pass": alt_line},
+        # per step: pack, embed, GEMM, select, then the re-rank: one launch per
+        # query, or seven deduplicated (histogram, two prefix-sum passes,
+        # scatter, slice counts, sums, per-query top-k)
+        "gpu_launches": (11 if dedupe else 5) * args.steps,
         "roofline": roof,
         "clocks": clk,
     }
@@ -655,6 +680,7 @@ def batched_record(torch, steps: int, warmup: int):
         "value": full["value"], "unit": "queries/s",
         "ms_per_launch": full["ms_per_step"], "steps": steps, "warmup": warmup,
         "sparse_rerank_queries_per_s": full["sparse_rerank"]["queries_per_s"],
+        "rerank": full["rerank"],
         "agreement_vs_exact_gpu_scan": full["agreement_vs_exact_gpu_scan"],
         "prefilter_ranking_vs_exact": full["prefilter_ranking_vs_exact"],
         "distance_error_vs_fp64": full["distance_error_vs_fp64"],

@@ -86,11 +86,16 @@ enum dbq_storage {
 
 /* Options of db_set_option. */
 enum dbq_option {
-    DBQ_OPT_SPARSE = 1   /* 1: exact scans of a bit-packed database read only the
+    DBQ_OPT_SPARSE = 1,  /* 1: exact scans of a bit-packed database read only the
                             words where the patient's mask is non-zero (exact
                             counts, fewer bytes); 2: the same from a word-major
                             copy of the planes (faster, twice the planes' memory);
                             0 (default): read every word */
+    DBQ_OPT_RERANK = 2   /* re-ranking of db_query_batch's embedding modes on a
+                            dense bit-packed database: 2 reads each distinct
+                            candidate entry of a batch once, 1 reads every
+                            (query, candidate) pair's entry, 0 (default) takes
+                            2 for batches of 160 queries or more, else 1 */
 };
 
 /* Query modes of db_query_batch. */
@@ -355,6 +360,15 @@ int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int 
  * contraction: the counts of all of them over the copy, then the
  * contraction's per-query selection.  The other paths treat 2 as 1.
  * DBQ_EINVAL for 2 on half-precision storage or for any value outside 0..2.
+ * DBQ_OPT_RERANK: how db_query_batch re-ranks the prefilter's candidates
+ * when DBQ_OPT_SPARSE is 0.  The queries of a batch share candidates, so
+ * with 2 the candidate pairs are sorted by entry and every distinct entry
+ * is read once, slice by slice, against the slices of all the queries that
+ * picked it (held in shared memory); with 1 each query reads its own
+ * candidates; 0 (default) takes 2 for a group of 160 queries or more of one
+ * database, else 1.  The hits are the same.  A sparse database always
+ * re-ranks per query, reading only the patient's support.  DBQ_EINVAL
+ * outside 0..2.
  */
 int db_set_option(dbq_db* db, int option, int64_t value);
 

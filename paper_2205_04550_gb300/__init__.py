@@ -17,7 +17,7 @@ from ._dbq import (DBQ_BITS, DBQ_F16, DBQ_F32, DBQ_FLAG_EMBED, DBQ_FLAG_SKETCH,
                    db_get_masks, db_info, db_last_error, db_load_volumes, db_prefilter,
                    db_prepare_patient, db_query, db_query_async, db_query_batch,
                    db_query_prepared, db_scan_counts, db_scan_packed_noalloc, db_set_option,
-                   db_stage_times, DBQ_OPT_SPARSE, DBQ_PLAN_ITEMS_PER_SM, DBQ_PLAN_TC_MIN_QUERIES,
+                   db_stage_times, DBQ_OPT_SPARSE, DBQ_OPT_RERANK, DBQ_PLAN_ITEMS_PER_SM, DBQ_PLAN_TC_MIN_QUERIES,
                    db_plan_create, db_plan_set, db_plan_query, db_plan_status, db_plan_destroy,
                    db_create_downsampled)
 
@@ -26,7 +26,7 @@ __all__ = ["Database", "ForwardModel", "DbqError", "HIT_DTYPE", "DBQ_F32", "DBQ_
            "DBQ_MODE_EXACT", "DBQ_MODE_EMBED_BF16", "DBQ_MODE_EMBED_FP8", "DBQ_MODE_HASH",
            "SKETCH_DIMS", "db_get_codes", "db_query_batch", "db_prefilter",
            "db_get_embeddings", "db_scan_packed_noalloc", "db_set_option", "db_stage_times",
-           "DBQ_OPT_SPARSE", "DBQ_PLAN_ITEMS_PER_SM", "DBQ_PLAN_TC_MIN_QUERIES", "Plan",
+           "DBQ_OPT_SPARSE", "DBQ_OPT_RERANK", "DBQ_PLAN_ITEMS_PER_SM", "DBQ_PLAN_TC_MIN_QUERIES", "Plan",
            "db_plan_create", "db_plan_set", "db_plan_query", "db_plan_status", "db_plan_destroy", "db_create_downsampled", "db_create", "db_load_volumes",
            "db_build_masks", "db_query", "db_query_async", "db_prepare_patient",
            "db_query_prepared", "db_scan_counts", "db_get_masks",
@@ -142,6 +142,13 @@ class Database:
         db_set_option(self.handle, DBQ_OPT_SPARSE, mode)
         self.sparse = bool(mode)
         self.sparse_mode = mode
+
+    def set_rerank(self, mode):
+        """How embedding batches re-rank their candidates on a dense database:
+        2 reads each distinct candidate entry of the batch once, 1 reads each
+        query's candidates separately, 0 (default) takes 2 for batches of 160
+        queries or more, else 1 (the same hits)."""
+        db_set_option(self.handle, DBQ_OPT_RERANK, int(mode))
 
     def embeddings(self, first: int, count: int):
         """-> dict of bf16 bits [count,2,d] uint16, e4m3 codes [count,2,d] uint8,

@@ -36,6 +36,7 @@ DBQ_FLAG_SKETCH = 2
 SKETCH_DIMS = 4096
 
 DBQ_OPT_SPARSE = 1
+DBQ_OPT_RERANK = 2
 
 DBQ_PLAN_ITEMS_PER_SM = 1
 DBQ_PLAN_TC_MIN_QUERIES = 2

@@ -160,6 +160,8 @@ struct dbq_db {
     float* bdist = nullptr;         // [bq][n]
     int32_t* bcand = nullptr;       // [bq][1024]
     dbq::Cand* brr = nullptr;       // [bq][slices][bk]
+    dbq::RerankDedupeWork rrd = {}; // deduplicated re-rank (partial grows with the pairs)
+    int rerank_mode = 0;            // DBQ_OPT_RERANK: 0 automatic, 1 per query, 2 deduplicated
     unsigned int* btickets = nullptr;
     dbq::Hit* bhits = nullptr;      // [bq][bk] device
     dbq::Hit* bhits_host = nullptr; // pinned
@@ -225,6 +227,16 @@ struct dbq_db {
         cudaFree(bdist);
         cudaFree(bcand);
         cudaFree(brr);
+        cudaFree(rrd.hist);
+        cudaFree(rrd.tiles);
+        cudaFree(rrd.start);
+        cudaFree(rrd.uniq);
+        cudaFree(rrd.ubeg);
+        cudaFree(rrd.nuniq);
+        cudaFree(rrd.qof);
+        cudaFree(rrd.posof);
+        cudaFree(rrd.partial);
+        cudaFree(rrd.cnt);
         cudaFree(btickets);
         cudaFree(bhits);
         cudaFreeHost(bhits_host);
@@ -417,6 +429,7 @@ namespace {
 
 constexpr int kBatchQ = 256;      // queries per prefilter group (tensor-core N)
 constexpr int kRerankSlices = 4;
+constexpr int kRerankDedupeMinQ = 160;   // automatic deduplicated re-rank from this batch size
 
 size_t patient_bytes(const dbq_db* db, int kind)
 {
@@ -465,6 +478,18 @@ int ensure_batch(dbq_db* db, int k)
             if (!rc) rc = grow(db, &db->bcand, q * 1024 * 4, "prefilter candidates");
             if (!rc) rc = grow(db, &db->brr, q * kRerankSlices * kMaxK * sizeof(dbq::Cand),
                                "re-rank lists");
+            const size_t n = (size_t)db->n, pairs = q * 1024;
+            dbq::RerankDedupeWork& w = db->rrd;
+            if (!rc) rc = grow(db, &w.hist, n * 4, "re-rank histogram");
+            if (!rc) rc = grow(db, &w.tiles, (size_t)dbq::rerank_dedupe_tiles(db->n) * sizeof(uint2),
+                               "re-rank tile sums");
+            if (!rc) rc = grow(db, &w.start, (n + 1) * 4, "re-rank entry starts");
+            if (!rc) rc = grow(db, &w.uniq, n * 4, "re-rank distinct entries");
+            if (!rc) rc = grow(db, &w.ubeg, (n + 1) * 4, "re-rank distinct starts");
+            if (!rc) rc = grow(db, &w.nuniq, 4, "re-rank distinct count");
+            if (!rc) rc = grow(db, &w.qof, pairs * 2, "re-rank pair queries");
+            if (!rc) rc = grow(db, &w.posof, pairs * 4, "re-rank pair positions");
+            if (!rc) rc = grow(db, &w.cnt, 2 * pairs * 4, "re-rank pair counts");
         }
         if (!rc && !db->bhits_host) {
             cudaError_t err = cudaMallocHost(reinterpret_cast<void**>(&db->bhits_host),
@@ -478,6 +503,8 @@ int ensure_batch(dbq_db* db, int k)
         if (!rc) {
             cudaError_t err = cudaMemset(db->btickets, 0, (q + 1) * sizeof(unsigned int));
             if (err == cudaSuccess) err = cudaMemset(db->bstatus, 0, 16);
+            if (err == cudaSuccess && db->rrd.hist)
+                err = cudaMemset(db->rrd.hist, 0, (size_t)db->n * 4);
             if (err == cudaSuccess) err = cudaDeviceSynchronize();
             if (err != cudaSuccess) rc = cuda_fail(err, "batch workspace initialisation");
         }
@@ -486,6 +513,40 @@ int ensure_batch(dbq_db* db, int k)
     }
     (void)k;
     return DBQ_OK;
+}
+
+// Work items per query of the per-query re-rank: every item of a dense
+// batch costs the same, so the launch takes ceil(nq x slices / grid) rounds
+// of items of c / slices candidates; the count of slices (at least
+// kRerankSlices, items of at least 4 candidates, lists [nq][slices][k]
+// within the scratch of kBatchQ x kRerankSlices lists) that minimises
+// rounds / slices, the smallest of those within 2 %.
+int rerank_slices(int nq, int c, int grid)
+{
+    const int cap = std::max(kRerankSlices, std::min(c / 4, kBatchQ * kRerankSlices / nq));
+    int best = kRerankSlices;
+    double best_cost = 1e300;
+    for (int s = kRerankSlices; s <= cap; ++s) {
+        const double cost = (double)(((int64_t)nq * s + grid - 1) / grid) / s;
+        if (cost < 0.98 * best_cost) {
+            best_cost = cost;
+            best = s;
+        }
+    }
+    return std::min(best, c);
+}
+
+// Slice counts of the deduplicated re-rank for npairs pairs.
+int ensure_rerank_partial(dbq_db* db, int64_t npairs)
+{
+    const int64_t need =
+        (int64_t)2 * dbq::rerank_dedupe_slices((int)db->wp4) * dbq::rerank_dedupe_pstride(npairs);
+    if (db->rrd.partial_elems >= need) return DBQ_OK;
+    if (db->rrd.partial) db->bytes_held -= (size_t)db->rrd.partial_elems * 2;
+    db->rrd.partial_elems = 0;
+    int rc = grow(db, &db->rrd.partial, (size_t)need * 2, "re-rank slice counts");
+    if (!rc) db->rrd.partial_elems = need;
+    return rc;
 }
 
 // Threshold (or import) nq patients into bplanes / bpcount.
@@ -1325,14 +1386,25 @@ int db_query_batch(dbq_db* const* dbs, const int* db_of_query, int nq,
                 r.nq = gn;
                 r.c = n_candidates;
                 r.k = k;
-                r.slices = std::min(kRerankSlices, n_candidates);
+                r.slices = rerank_slices(gn, n_candidates, db->grid);
                 r.scratch = db->brr;
                 r.tickets = db->btickets;
                 r.hits = db->bhits;
                 r.sup_lists = db->sparse ? db->bsup : nullptr;
                 r.sup_lens = db->sparse ? db->bsuplen : nullptr;
                 r.sched = db->sparse ? db->btickets + kBatchQ : nullptr;
-                cudaError_t err = dbq::launch_rerank(r, s);
+                // a dense batch of kRerankDedupeMinQ queries or more reads each
+                // distinct candidate once (DBQ_OPT_RERANK 2: every dense batch;
+                // 1: none)
+                const bool dedupe =
+                    !db->sparse && (db->rerank_mode == 2 ||
+                                    (db->rerank_mode == 0 && gn >= kRerankDedupeMinQ));
+                if (dedupe) {
+                    rc = ensure_rerank_partial(db, (int64_t)gn * n_candidates);
+                    if (rc) return rc;
+                }
+                cudaError_t err = dedupe ? dbq::launch_rerank_dedupe(r, db->rrd, s)
+                                         : dbq::launch_rerank(r, s);
                 if (err != cudaSuccess) return cuda_fail(err, "re-rank launch");
                 mark(db, 5, s);
                 db->ev_valid = db->ev[0] != nullptr;
@@ -1406,6 +1478,11 @@ int db_set_option(dbq_db* db, int option, int64_t value)
         db->sparse = value != 0;
         db->sparse_mode = (int)value;
         db->prepared = false;   // a prepared patient has no support lists yet
+        return DBQ_OK;
+    }
+    if (option == DBQ_OPT_RERANK) {
+        if (value < 0 || value > 2) return fail(DBQ_EINVAL, "DBQ_OPT_RERANK takes 0, 1 or 2");
+        db->rerank_mode = (int)value;
         return DBQ_OK;
     }
     return fail(DBQ_EINVAL, "unknown option %d", option);

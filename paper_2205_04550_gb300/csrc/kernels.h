@@ -210,6 +210,30 @@ struct RerankArgs {
 };
 cudaError_t launch_rerank(const RerankArgs& a, cudaStream_t stream);
 
+// The same hits for a dense batch, each distinct candidate entry read once
+// (rerank_dedupe.cu): the pairs sorted by entry, slice counts against the
+// patients' slices in shared memory, their sums, a top-k per query.
+// sup_lists must be null; nq <= kRerankDedupeMaxQ, c <= 1024.
+constexpr int kRerankDedupeMaxQ = 256;
+struct RerankDedupeWork {
+    uint32_t* hist;             // [n], zero between launches (the launch leaves it zero)
+    uint2* tiles;               // [rerank_dedupe_tiles(n)]
+    uint32_t* start;            // [n + 1]
+    int32_t* uniq;              // [n]
+    uint32_t* ubeg;             // [n + 1]
+    uint32_t* nuniq;            // [1]
+    uint16_t* qof;              // [nq * c]
+    uint32_t* posof;            // [nq * c]
+    uint16_t* partial;          // [2 * rerank_dedupe_slices(wp4)][rerank_dedupe_pstride(nq * c)]
+    int64_t partial_elems;
+    uint32_t* cnt;              // [2][nq * c]
+};
+int rerank_dedupe_slices(int wp4);
+int64_t rerank_dedupe_pstride(int64_t npairs);
+int64_t rerank_dedupe_tiles(int64_t n);
+cudaError_t launch_rerank_dedupe(const RerankArgs& a, const RerankDedupeWork& w,
+                                 cudaStream_t stream);
+
 // ---- many exact queries in one persistent launch
 struct QueryTask {
     const uint4* planes;        // database planes [n][2][wp4]
