@@ -230,12 +230,27 @@ rr_count_kernel(const uint4* __restrict__ planes, int wp4, const uint4* __restri
     const int64_t estride = 2 * (int64_t)wp4;
     uint16_t* out = partial + (int64_t)x * pstride;
     // batches of kEntryBatch entries: the pieces of a batch are loaded
-    // together (kEntryBatch x 512 bytes in flight per warp), then counted
+    // together (kEntryBatch x 512 bytes in flight per warp), then counted.
+    // The next batch's entry ids and pair bounds are loaded while this one
+    // is counted, so a batch waits on one memory latency, not two.
+    auto batch_len = [&](int u) { return u_end - u < kEntryBatch ? u_end - u : kEntryBatch; };
+    uint32_t bn = 0;   // lanes 0..nb: the first pair of entry u0 + lane (lane nb: the end)
+    int32_t en = 0;    // lanes 0..nb-1: the entries
+    if (u_begin < u_end) {
+        const int nb = batch_len(u_begin);
+        bn = ubeg[u_begin + (lane < nb ? lane : nb)];
+        en = uniq[u_begin + (lane < nb - 1 ? lane : nb - 1)];
+    }
     for (int u0 = u_begin; u0 < u_end; u0 += kEntryBatch) {
-        const int nb = u_end - u0 < kEntryBatch ? u_end - u0 : kEntryBatch;
-        // lanes 0..nb: the first pair of entry u0 + lane (lane nb: the end)
-        const uint32_t b = ubeg[u0 + (lane < nb ? lane : nb)];
-        const int32_t e = uniq[u0 + (lane < nb - 1 ? lane : nb - 1)];
+        const int nb = batch_len(u0);
+        const uint32_t b = bn;
+        const int32_t e = en;
+        const int u1 = u0 + kEntryBatch;
+        if (u1 < u_end) {
+            const int nb1 = batch_len(u1);
+            bn = ubeg[u1 + (lane < nb1 ? lane : nb1)];
+            en = uniq[u1 + (lane < nb1 - 1 ? lane : nb1 - 1)];
+        }
         uint4 ev[kEntryBatch];
 #pragma unroll
         for (int j = 0; j < kEntryBatch; ++j) {
