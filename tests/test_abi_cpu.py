@@ -38,3 +38,20 @@ def test_binding_loads_and_reports_no_error():
     assert rc == _dbq.DBQ_EINVAL and h.value is None
     assert b"grid" in lib.db_last_error()
     assert lib.db_destroy(None) == 0
+
+
+def test_binding_constants_match_the_header():
+    """Every enumerator and DBQ_ flag of include/dbq.h has the same value in the
+    binding (an option or mode renumbered on one side would be passed through
+    silently as another)."""
+    text = open(os.path.join(ROOT, "include", "dbq.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    consts = {m.group(1): int(m.group(2))
+              for m in re.finditer(r"\b(DBQ_[A-Z0-9_]+)\s*=\s*(-?\d+)", text)}
+    consts.update({m.group(1): int(m.group(2))
+                   for m in re.finditer(r"#define\s+(DBQ_[A-Z0-9_]+)\s+(\d+)u?\b", text)})
+    for name in ("DBQ_OK", "DBQ_ETIMEOUT", "DBQ_OPT_SPARSE", "DBQ_OPT_RERANK",
+                 "DBQ_MODE_HASH", "DBQ_FLAG_SKETCH", "DBQ_PLAN_TC_MIN_QUERIES"):
+        assert name in consts, name
+    for name, value in sorted(consts.items()):
+        assert getattr(_dbq, name) == value, name
