@@ -21,10 +21,12 @@
 //      top-k with the shared top-k code -- the hits of rerank.cu, bit for bit,
 //      because the counts are exact and the ranking is a total order.
 //
-// The CTAs that own neighbouring slices of one plane read neighbouring
-// 512-byte pieces of each entry at about the same time (every CTA walks the
-// same entry list), so DRAM sees long runs.  The histogram returns to zero in
-// the scatter, so only its allocation clears it.
+// Every (distinct entry, slice) costs a warp a few instructions besides its
+// pairs' intersections, and at 1,024 slices per 128^3 entry the kernel is
+// bound by instruction issue and the shared-memory pipe rather than by its
+// DRAM reads (a copy of the planes in which each CTA's pieces are contiguous
+// was measured no faster).  The histogram returns to zero in the scatter, so
+// only its allocation clears it.
 #include "kernels.h"
 #include "topk.cuh"
 
