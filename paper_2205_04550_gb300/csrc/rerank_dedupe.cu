@@ -21,12 +21,11 @@
 //      top-k with the shared top-k code -- the hits of rerank.cu, bit for bit,
 //      because the counts are exact and the ranking is a total order.
 //
-// Every (distinct entry, slice) costs a warp a few instructions besides its
-// pairs' intersections, and at 1,024 slices per 128^3 entry the kernel is
-// bound by instruction issue and the shared-memory pipe rather than by its
-// DRAM reads (a copy of the planes in which each CTA's pieces are contiguous
-// was measured no faster).  The histogram returns to zero in the scatter, so
-// only its allocation clears it.
+// A tumour fills a small part of the grid, so most queries' patient slices
+// are empty: those pairs intersect nothing in the slice and only their zero
+// count is written, which leaves the warps mostly streaming the entries'
+// pieces (every word of every distinct entry is still read).  The histogram
+// returns to zero in the scatter, so only its allocation clears it.
 #include "kernels.h"
 #include "topk.cuh"
 
@@ -208,15 +207,26 @@ rr_count_kernel(const uint4* __restrict__ planes, int wp4, const uint4* __restri
                 const uint32_t* __restrict__ nuniq, const uint16_t* __restrict__ qof, int nslice,
                 int64_t pstride, uint16_t* __restrict__ partial)
 {
-    extern __shared__ uint4 spat[];   // [nq][kSliceW], then [warps][32][32] bytes
+    // [nq][kSliceW] patient slices, [warps][32][32] staging bytes, [nq] flags
+    extern __shared__ uint4 spat[];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint8_t* stage = reinterpret_cast<uint8_t*>(spat + nq * kSliceW) + warp * 1024;
+    uint8_t* nonzero = reinterpret_cast<uint8_t*>(spat + nq * kSliceW) +
+                       (kCountThreads / 32) * 1024;
     const int x = blockIdx.x;
     const int plane = x / nslice;
     const int w0 = (x - plane * nslice) * kSliceW;
+    // a warp loads whole slices (kSliceW = 32 lanes, blockDim a multiple of
+    // 32) and flags the queries whose slice has a set bit: a pair whose
+    // query's slice is empty intersects nothing here, so only its zero count
+    // is written
     for (int i = threadIdx.x; i < nq * kSliceW; i += blockDim.x) {
         const int q = i / kSliceW, w = w0 + i % kSliceW;
-        spat[i] = w < wp4 ? patients[((int64_t)q * 2 + plane) * wp4 + w] : make_uint4(0, 0, 0, 0);
+        const uint4 v =
+            w < wp4 ? patients[((int64_t)q * 2 + plane) * wp4 + w] : make_uint4(0, 0, 0, 0);
+        spat[i] = v;
+        const bool any = __any_sync(0xffffffffu, (v.x | v.y | v.z | v.w) != 0u);
+        if (lane == 0) nonzero[q] = any ? 1 : 0;
     }
     __syncthreads();
     // entry indices are int32, so the distinct entries number below 2^31
@@ -268,28 +278,38 @@ rr_count_kernel(const uint4* __restrict__ planes, int wp4, const uint4* __restri
         // and lane i sums row i
         for (uint32_t wbase = s_first; wbase < s_last; wbase += 32u) {
             const int wn = s_last - wbase < 32u ? (int)(s_last - wbase) : 32;
-            const uint32_t qoff = (lane < wn ? (uint32_t)qof[wbase + lane] : 0u) * (uint32_t)kSliceW;
+            const uint32_t q = lane < wn ? (uint32_t)qof[wbase + lane] : 0u;
+            const bool counted = lane < wn && nonzero[q];
+            const uint32_t qoff = q * (uint32_t)kSliceW;
+            // positions of the window whose query's slice is not empty
+            const unsigned act = __ballot_sync(0xffffffffu, counted);
 #pragma unroll
             for (int j = 0; j < kEntryBatch; ++j) {
                 if (j < nb) {
                     const int p0 = (int)__shfl_sync(0xffffffffu, b, j) - (int)wbase;
                     const int p1 = (int)__shfl_sync(0xffffffffu, b, j + 1) - (int)wbase;
-                    int i = p0 > 0 ? p0 : 0;
-                    const int iend = p1 < wn ? p1 : wn;
-                    for (; i + 1 < iend; i += 2) {   // two independent chains
-                        const uint4 pa = spat[__shfl_sync(0xffffffffu, qoff, i) + lane];
-                        const uint4 pb = spat[__shfl_sync(0xffffffffu, qoff, i + 1) + lane];
-                        stage[i * 32 + lane] = (uint8_t)and_popc4(ev[j], pa);
-                        stage[(i + 1) * 32 + lane] = (uint8_t)and_popc4(ev[j], pb);
-                    }
-                    if (i < iend) {
-                        const uint4 pa = spat[__shfl_sync(0xffffffffu, qoff, i) + lane];
-                        stage[i * 32 + lane] = (uint8_t)and_popc4(ev[j], pa);
+                    const int i0 = p0 > 0 ? p0 : 0;
+                    const int i1 = p1 < wn ? p1 : wn;
+                    unsigned m = 0u;
+                    if (i0 < i1)   // bits [i0, i1); i0 < 32
+                        m = act & (i1 >= 32 ? 0xffffffffu : (1u << i1) - 1u) & ~((1u << i0) - 1u);
+                    while (m) {
+                        const int ia = __ffs(m) - 1;
+                        m &= m - 1u;
+                        const uint4 pa = spat[__shfl_sync(0xffffffffu, qoff, ia) + lane];
+                        if (m) {   // two independent chains
+                            const int ib = __ffs(m) - 1;
+                            m &= m - 1u;
+                            const uint4 pb = spat[__shfl_sync(0xffffffffu, qoff, ib) + lane];
+                            stage[ib * 32 + lane] = (uint8_t)and_popc4(ev[j], pb);
+                        }
+                        stage[ia * 32 + lane] = (uint8_t)and_popc4(ev[j], pa);
                     }
                 }
             }
             __syncwarp();
-            if (lane < wn) {
+            if (lane < wn && !counted) out[wbase + lane] = 0;
+            if (counted) {
                 const uint4* row = reinterpret_cast<const uint4*>(stage + lane * 32);
                 const uint4 r0 = row[0], r1 = row[1];
                 uint32_t t = 0;
@@ -398,7 +418,8 @@ cudaError_t launch_rerank_dedupe(const RerankArgs& a, const RerankDedupeWork& w,
     if (w.partial_elems < (int64_t)2 * nslice * pstride) return cudaErrorInvalidValue;
     // attributes first: once the histogram is built, every launch must follow
     // (the scatter returns it to zero)
-    const size_t csmem = (size_t)a.nq * kSliceW * sizeof(uint4) + (kCountThreads / 32) * 1024;
+    const size_t csmem =
+        (size_t)a.nq * kSliceW * sizeof(uint4) + (kCountThreads / 32) * 1024 + a.nq;
     const size_t ssmem = topk_smem_bytes();
     cudaError_t err = cudaFuncSetAttribute(rr_count_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
