@@ -500,8 +500,8 @@ def measure_embed(wl, torch, steps, warmup, workload):
     elapsed = t0.elapsed_time(t1) / 1000.0
     stages = {a: v / args.steps for a, v in stage_sum.items()}
     # the same launches with the other dense re-rank pass (the library picks
-    # the deduplicated pass for groups of 160 queries or more, else per query)
-    dedupe = nq >= 160
+    # the deduplicated pass for groups of 32 queries or more, else per query)
+    dedupe = nq >= 32
     db.set_rerank(1 if dedupe else 2)
     for _ in range(2):
         step()

@@ -95,7 +95,7 @@ enum dbq_option {
                             dense bit-packed database: 2 reads each distinct
                             candidate entry of a batch once, 1 reads every
                             (query, candidate) pair's entry, 0 (default) takes
-                            2 for batches of 160 queries or more, else 1 */
+                            2 for batches of 32 queries or more, else 1 */
 };
 
 /* Query modes of db_query_batch. */
@@ -365,7 +365,7 @@ int db_prefilter(dbq_db* db, int nq, const void* const* patients, int kind, int 
  * with 2 the candidate pairs are sorted by entry and every distinct entry
  * is read once, slice by slice, against the slices of all the queries that
  * picked it (held in shared memory); with 1 each query reads its own
- * candidates; 0 (default) takes 2 for a group of 160 queries or more of one
+ * candidates; 0 (default) takes 2 for a group of 32 queries or more of one
  * database, else 1.  The hits are the same.  A sparse database always
  * re-ranks per query, reading only the patient's support.  DBQ_EINVAL
  * outside 0..2.

@@ -146,7 +146,7 @@ class Database:
     def set_rerank(self, mode):
         """How embedding batches re-rank their candidates on a dense database:
         2 reads each distinct candidate entry of the batch once, 1 reads each
-        query's candidates separately, 0 (default) takes 2 for batches of 160
+        query's candidates separately, 0 (default) takes 2 for batches of 32
         queries or more, else 1 (the same hits)."""
         db_set_option(self.handle, DBQ_OPT_RERANK, int(mode))
 

@@ -429,7 +429,7 @@ namespace {
 
 constexpr int kBatchQ = 256;      // queries per prefilter group (tensor-core N)
 constexpr int kRerankSlices = 4;
-constexpr int kRerankDedupeMinQ = 160;   // automatic deduplicated re-rank from this batch size
+constexpr int kRerankDedupeMinQ = 32;    // automatic deduplicated re-rank from this batch size
 
 size_t patient_bytes(const dbq_db* db, int kind)
 {
