@@ -137,6 +137,11 @@ TRAFFIC = {
                             read_bytes=2097329408, write_bytes=3185152,
                             capture="profiles/scan_f16_4k_64_ncu_full.md"),
 }
+# DRAM traffic of the deduplicated re-rank's count kernel, from one full-size
+# one-pass capture (profiles/rerank_dedupe_100k_launches.md): valid only for
+# that workload and while the kernel's source hashes to the captured version.
+TRAFFIC_RERANK = dict(files=("rerank_dedupe.cu",), sha="5ba8ffe13de930b5",
+                      workload="embed_100k_128", read_bytes=37125778944, write_bytes=220821248)
 METRIC = "DB entries/s per query (HBM GB/s vs peak); batched queries/s at top-1 match"
 FALLBACK_HBM_GBS = 6800.0
 NOMINAL_HBM_GBS = 7900.0              # GB300 HBM3e, nominal
@@ -153,17 +158,29 @@ def _traffic(kernel: str, n_entries: int, grid):
     """Scaled DRAM bytes per launch, or None if the kernel changed since the
     capture or the workload's grid is not the captured one (bytes per entry
     differ)."""
-    import hashlib
     t = TRAFFIC.get(kernel)
-    if t is None or tuple(grid) != tuple(t["grid"]):
-        return None
-    h = hashlib.sha256()
-    for f in t["files"]:
-        with open(os.path.join(ROOT, "paper_2205_04550_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    if h.hexdigest()[:16] != t["sha"]:
+    if t is None or tuple(grid) != tuple(t["grid"]) or _sources_sha(t["files"]) != t["sha"]:
         return None
     return t["read_bytes"] / t["entries"] * n_entries + t["write_bytes"]
+
+
+def _sources_sha(files) -> str:
+    """First 16 hex digits of the SHA-256 of the named kernel sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2205_04550_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _rerank_traffic(workload: str):
+    """DRAM bytes of one count-kernel launch of the deduplicated re-rank, or
+    None when the workload or the kernel's source is not the captured one."""
+    t = TRAFFIC_RERANK
+    if workload != t["workload"] or _sources_sha(t["files"]) != t["sha"]:
+        return None
+    return t["read_bytes"] + t["write_bytes"]
 
 
 def max_over_ranks(value: float, dist=None, device=None) -> float:
@@ -586,7 +603,8 @@ def measure_embed(wl, torch, steps, warmup, workload):
         ach = rr_bytes / (stages["rerank"] / 1000.0) / 1e9
         roof = {"bound": "hbm", "kernel": "rr_count_kernel" if dedupe else "rerank_kernel",
                 "achieved": ach, "peak": peak,
-                "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                "traffic": _rerank_traffic(args.workload) if dedupe else None,
                 "algorithmic_bytes_per_launch": rr_bytes, "kernel_ms": stages["rerank"]}
     else:
         ach = gemm_flops / (stages["distances"] / 1000.0) / 1e12
