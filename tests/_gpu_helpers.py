@@ -54,7 +54,8 @@ def oracle_query(db, patient, t1, t2, k, patient_mask=None):
     return oracle.query(db, patient, t1, t2, k, patient_mask=patient_mask)
 
 
-def stream_oracle_counts(shape, n, queries, dtype="float32", chunk=256, seed=synth.DB_SEED):
+def stream_oracle_counts(shape, n, queries, dtype="float32", chunk=256, seed=synth.DB_SEED,
+                         entries=None):
     """The oracle's per-entry counts over a whole surrogate database that is
     too large to hold on the host: the same seeded volumes the database was
     built from are generated on the GPU chunk by chunk, copied into pinned
@@ -62,8 +63,10 @@ def stream_oracle_counts(shape, n, queries, dtype="float32", chunk=256, seed=syn
     worker thread while the next chunk is generated and copied (ctypes
     releases the GIL during the oracle's C call).
 
-    queries: list of (patient mask [2][V] uint8, t1, t2).
-    Returns one [n, 4] uint32 array (I1, I2, E1, E2) per query.
+    queries: list of (patient mask [2][V] uint8, t1, t2).  entries: the entry
+    ids counted (default 0 .. n-1; n is then len(entries)).
+    Returns one [n, 4] uint32 array (I1, I2, E1, E2) per query, row i for the
+    i-th entry.
     """
     import queue
     import threading
@@ -72,7 +75,9 @@ def stream_oracle_counts(shape, n, queries, dtype="float32", chunk=256, seed=syn
 
     nx, ny, nz = shape
     tdt = torch.float16 if dtype == "float16" else torch.float32
-    gen = synth.DeviceGenerator(shape, seed, np.arange(n))
+    if entries is not None:
+        n = len(entries)
+    gen = synth.DeviceGenerator(shape, seed, np.arange(n) if entries is None else entries)
     dev = torch.empty((chunk, nz, ny, nx), dtype=tdt, device="cuda")
     host = [torch.empty((chunk, nz, ny, nx), dtype=tdt, pin_memory=True) for _ in range(2)]
     free = [threading.Semaphore(1) for _ in range(2)]     # host buffer not in use by the oracle

@@ -8,12 +8,16 @@ benchmark times.
   entry from the same volumes (streamed from the GPU generator through host
   memory in chunks); every count, the patient's sizes, the top-64 order and
   the hits' score bits must equal the oracle's own ranking of its own scores.
+* The embedding batch at 100,000 entries of 128^3 (256 queries, 512
+  candidates, top-10): the deduplicated and the per-query re-ranks give
+  byte-identical hits, and for three queries the oracle counts every
+  candidate from its volume and its top-10 of them equals the GPU's.
 """
 import numpy as np
 import pytest
 
 import oracle
-from paper_2205_04550_gb300 import DBQ_STORE_BITS, Database, synth
+from paper_2205_04550_gb300 import DBQ_MODE_EMBED_BF16, DBQ_STORE_BITS, Database, synth
 from tests._gpu_helpers import assert_hits_equal, stream_oracle_counts
 
 pytestmark = pytest.mark.gpu
@@ -29,8 +33,8 @@ def torch():
     return _t
 
 
-def _build_db_on_device(torch, shape, n, chunk, n_params=8):
-    db = Database(shape, n, DBQ_STORE_BITS, T1, T2, n_params)
+def _build_db_on_device(torch, shape, n, chunk, n_params=8, embed=False):
+    db = Database(shape, n, DBQ_STORE_BITS, T1, T2, n_params, embed=embed)
     nx, ny, nz = shape
     gen = synth.DeviceGenerator(shape, synth.DB_SEED, np.arange(n))
     buf = torch.empty((chunk, nz, ny, nx), dtype=torch.float32, device="cuda")
@@ -90,5 +94,36 @@ def test_exact_query_50000_entries_128cube_every_entry(torch):
         db.set_sparse(False)
         assert s_hits.tobytes() == hits.tobytes()
         np.testing.assert_array_equal(s_counts, counts)
+    finally:
+        db.close()
+
+
+def test_embedding_batch_100000_entries_128cube(torch):
+    shape = (128, 128, 128)
+    nx, ny, nz = shape
+    n, nq, c, k = 100_000, 256, 512, 10
+    db = _build_db_on_device(torch, shape, n, chunk=8, embed=True)
+    try:
+        pgen = synth.DeviceGenerator(shape, synth.DB_SEED,
+                                     synth.PATIENT_BASE + np.arange(1, nq + 1, dtype=np.uint64))
+        pats = torch.empty((nq, nz, ny, nx), dtype=torch.float32, device="cuda")
+        pgen.fill(0, nq, pats)
+        plist = [pats[q] for q in range(nq)]
+        _, cand = db.prefilter(plist, DBQ_MODE_EMBED_BF16, c)
+        out = []
+        for mode in (1, 2, 0):
+            db.set_rerank(mode)
+            out.append(db.query_batch(plist, k, DBQ_MODE_EMBED_BF16, c)[0])
+        assert out[1].tobytes() == out[0].tobytes() and out[2].tobytes() == out[0].tobytes()
+        hits = out[2]
+        for q in (0, 100, 255):
+            pm = oracle.threshold(pats[q].cpu().numpy(), T1, T2)
+            psize = pm.sum(axis=1).astype(np.uint32)
+            ents = np.sort(cand[q]).astype(np.int64)
+            (ref_counts,) = stream_oracle_counts(shape, c, [(pm, T1, T2)], chunk=64, entries=ents)
+            idx, val = oracle.rank(oracle.scores(ref_counts, psize), k)
+            ref = {"index": ents[idx], "score": val,
+                   "counts": np.concatenate([ref_counts[idx], np.tile(psize, (k, 1))], axis=1)}
+            assert_hits_equal(hits[q], ref, k)
     finally:
         db.close()
